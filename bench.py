@@ -1,0 +1,414 @@
+"""Benchmark of the streaming connectivity push on GB300.
+
+Default workload (one pushed trial per step): large all-to-all source space, 5124 nodes,
+window W = 100 trials x 500 samples at 1 kHz, Hann taper, 40 bins (4-44 Hz, nfft 1000),
+the 7 spectral metrics, streaming mode with resident accumulators (27.8 GB, larger than
+L2, so no L2 flush is needed between steps). A step = one fc_push_trial of a new trial
+through taper + band spectrum, per-node PSD sums, the streaming add/subtract update with
+fused finalize and band average (plus the periodic re-sum when it falls due).
+
+Metric: pair-bin updates/s = P * B / (time per push), P = n(n-1)/2 pairs, B bins.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs an independent session (weak scaling, no collective on
+the data path); rank 0 prints one JSON line with the max-over-ranks time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "large_stream": dict(n=5124, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=100,
+                         desc="large all-to-all source space, streaming push: 5124 nodes, "
+                              "W=100 trials x 500 samples @1 kHz, Hann, 40 bins (4-44 Hz, nfft 1000), "
+                              "7 spectral metrics, FP32 terms + double-float accumulators"),
+    "source_stream": dict(n=2000, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=50,
+                          desc="source space streaming push: 2000 nodes, W=50 trials x 500 samples, "
+                               "40 bins (4-44 Hz), 7 spectral metrics"),
+}
+METRIC = "pair-bin updates/s per pushed trial"
+UNIT = "pair-bin updates/s"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------- environment
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def stream_kernel_hash():
+    h = hashlib.sha256()
+    for f in ("k_pairs.cu", "df32.cuh", "terms.cuh", "fc_internal.h"):
+        with open(os.path.join(ROOT, "paper_2303_03279_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_hash, workload):
+    """DRAM bytes per launch of the streaming kernel from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "k_stream_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload)
+    if not e or e.get("kernel_hash") != kernel_hash:
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+# ----------------------------------------------------------------- trial pool
+
+
+def make_trials(w, count, seed=42):
+    from synth import ar2_source_model, ar2_source_trials
+    model = ar2_source_model(seed, w["n"], fs=w["fs"])
+    return ar2_source_trials(model, 0, count, w["N"])
+
+
+# ----------------------------------------------------------------- CPU oracle leg
+
+
+def _oracle_sample_job(args):
+    """One full-window oracle evaluation on a node subset (runs in a spawned process)."""
+    n_sub, N, fs, band, W, seed = args
+    import numpy as np  # noqa: F811
+    import oracle as O
+    from synth import ar2_source_model, ar2_source_trials
+    model = ar2_source_model(seed, n_sub, fs=fs)
+    x = ar2_source_trials(model, 0, W, N)
+    bins = O.band_bins(fs, band[2], band[0], band[1])
+    t0 = time.perf_counter()
+    X = O.spectra(x, bins, band[2], "hann")
+    nets = O.spectral_networks_dense(X)
+    dt = time.perf_counter() - t0
+    assert np.isfinite(nets["COH"]).all()
+    P = n_sub * (n_sub - 1) // 2
+    return dt, P * len(bins)
+
+
+def cpu_oracle_time(w, n_sub, reps=1):
+    """Time the oracle, single-threaded (BLAS threads pinned to 1), in a spawned process."""
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(1) as pool:
+            res = [pool.apply(_oracle_sample_job, ((n_sub, w["N"], w["fs"], w["band"], w["W"], 7 + r),))
+                   for r in range(reps)]
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return res
+
+
+def run_reference(args, w, wname):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    n_sub = args.ref_nodes
+    for _ in range(args.warmup):
+        cpu_oracle_time(w, n_sub)
+    times, units = [], 0
+    for _ in range(args.steps):
+        (dt, pb), = cpu_oracle_time(w, n_sub)
+        times.append(dt)
+        units = pb
+    ms = 1000.0 * sum(times) / len(times)
+    value = units / (ms / 1000.0)
+    sample = (f"{n_sub}-node subset of the {w['n']}-node workload: one full-window oracle evaluation "
+              f"per step (FP64 DFT of W={w['W']} trials, pair sums, 7 spectral metrics)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wname, "description": w["desc"], "oracle_nodes": n_sub},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU leg
+
+
+def run_ours(args, w, wname):
+    import torch
+    from paper_2303_03279_gb300 import fc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    fc.load()
+    n, N, W, B_band = w["n"], w["N"], w["W"], w["band"]
+    steps, warmup = args.steps, args.warmup
+    pool_n = min(W + warmup + steps, args.pool)
+    t0 = time.time()
+    host = make_trials(w, pool_n, seed=42 + rank)
+    log(f"[rank {rank}] generated {pool_n} trials in {time.time() - t0:.1f}s")
+    dev = torch.from_numpy(host).cuda()
+    stream = torch.cuda.Stream()
+    mask = fc.FC_SPECTRAL_METRICS
+    sess = fc.Session(n, N, w["fs"], B_band, "hann", mask, W, mode=fc.FC_MODE_STREAM,
+                      stream=stream.cuda_stream, resum_period=args.resum_period)
+    P, B = sess.P, sess.B
+    units = P * B
+    torch.cuda.synchronize()
+
+    def trial(k):
+        return dev[k % pool_n]
+
+    # fill the window (bulk push: one re-sum from the stored spectra), then warm up
+    fc.fc_push_trials(sess.handle, dev[:W].contiguous() if pool_n >= W else dev, W)
+    fc.fc_sync(sess.handle)
+    for k in range(warmup):
+        fc.fc_push_trial(sess.handle, trial(W + k))
+    fc.fc_sync(sess.handle)
+
+    # timed region: device-resident inputs
+    fc.fc_set_profiling(sess.handle, True)
+    fc.fc_kernel_times(sess.handle, reset=True)
+    launches0 = fc.fc_launch_count(sess.handle)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(steps):
+            ev[k][0].record(stream)
+            fc.fc_push_trial(sess.handle, trial(W + warmup + k))
+            ev[k][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    fc.fc_sync(sess.handle)
+    launches = fc.fc_launch_count(sess.handle) - launches0
+    ktimes = fc.fc_kernel_times(sess.handle, reset=True)
+    fc.fc_set_profiling(sess.handle, False)
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / steps
+    lat = sorted(a.elapsed_time(b) for a, b in ev)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
+    value = world * units / (ms_per_step / 1000.0)
+
+    # roofline of the dominant kernel (streaming update)
+    launches_k, tot_k = ktimes["stream"]
+    hbm, peak_kind = measured_peaks()
+    roofline = None
+    if launches_k:
+        avg_ms = tot_k / launches_k
+        alg_bytes = 104.0 * units + 28.0 * P  # state read + write, 7 network planes written
+        achieved = alg_bytes / (avg_ms / 1000.0) / 1e9
+        roofline = {"kernel": "k_stream", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "peak_source": peak_kind, "avg_launch_ms": avg_ms,
+                    "algorithmic_bytes_per_launch": alg_bytes,
+                    "traffic": ncu_traffic(stream_kernel_hash(), wname)}
+    kernel_share = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in ktimes.items() if v[0]}
+
+    # e2e: host trial in (pinned), one metric's network out, through the public API
+    e2e = None
+    if not args.no_e2e:
+        pinned_in = torch.from_numpy(host[: min(pool_n, 8)].copy()).pin_memory()
+        out = torch.empty(P, dtype=torch.float32).pin_memory()
+        out_np = out.numpy()
+        e2e_steps = max(3, min(steps, args.e2e_steps))
+        fc.fc_sync(sess.handle)
+        tt = []
+        for k in range(e2e_steps + 2):
+            a = time.perf_counter()
+            fc.fc_push_trial(sess.handle, pinned_in[k % pinned_in.shape[0]].numpy())
+            fc.fc_get_network(sess.handle, fc.FC_COH, 1, out_np)
+            if k >= 2:
+                tt.append(time.perf_counter() - a)
+        e2e_ms = 1000.0 * sum(tt) / len(tt)
+        e2e = {"value": world * units / (e2e_ms / 1000.0), "unit": UNIT, "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": n * N * 4, "d2h_bytes_per_step": P * 4,
+               "latency_ms": {"p50": sorted(tt)[len(tt) // 2] * 1000.0, "max": max(tt) * 1000.0},
+               "steps": e2e_steps}
+    sess.close()
+    del sess
+    torch.cuda.synchronize()
+
+    # plain FP32 comparator: CUDA-core full-window recompute per push, no accumulators
+    plain = None
+    if not args.no_plain:
+        ps = fc.Session(n, N, w["fs"], B_band, "hann", mask, W, mode=fc.FC_MODE_FULL, stream=stream.cuda_stream)
+        fc.fc_push_trials(ps.handle, dev[:W].contiguous(), W)
+        fc.fc_sync(ps.handle)
+        pst = max(2, min(args.plain_steps, steps))
+        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(pst)]
+        for k in range(pst):
+            pev[k][0].record(stream)
+            fc.fc_push_trial(ps.handle, trial(W + k))
+            pev[k][1].record(stream)
+        torch.cuda.synchronize()
+        pl = sorted(a.elapsed_time(b) for a, b in pev)
+        pms = sum(pl) / len(pl)
+        plain = {"value": world * units / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
+                 "latency_ms": {"p50": pl[len(pl) // 2], "p99": pl[-1]}, "steps": pst,
+                 "path": "CUDA-core full-window recompute per push (FC_MODE_FULL), FP32"}
+        ps.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        res = cpu_oracle_time(w, args.cpu_nodes)
+        dt, pb = res[0]
+        cpu = {"value": pb / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_nodes}-node subset of the workload, one full-window FP64 oracle "
+                         f"evaluation (W={W} trials, {B} bins, 7 spectral metrics); the oracle has no "
+                         f"streaming form, so one push costs a full window", "seconds": dt}
+
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded AR(2) alpha sources + 200-edge coupling graph)",
+        "config": {"workload": wname, "description": w["desc"], "n_nodes": n, "n_samples": N,
+                   "window": W, "n_bins": B, "pairs": P, "pair_bins_per_push": units,
+                   "resum_period": args.resum_period or W, "metrics": "COH,IMAGCOHY,PLV,PLI,USPLI,WPLI,DSWPLI",
+                   "l2": "inputs larger than L2 (27.8 GB resident state), no flush",
+                   "parallelism": f"{world} independent session(s), one per GPU"},
+        "latency_ms": {"p50": p50, "p99": p99, "what": "device time from push enqueue to network ready"},
+        "plain_fp32": plain, "roofline": roofline, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
+        "clocks": clocks.summary(), "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default="large_stream", choices=sorted(WORKLOADS))
+    ap.add_argument("--resum-period", type=int, default=0)
+    ap.add_argument("--pool", type=int, default=128)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--cpu-nodes", type=int, default=512)
+    ap.add_argument("--ref-nodes", type=int, default=96)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w, args.workload)
+    return run_ours(args, w, args.workload)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

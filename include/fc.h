@@ -1,0 +1,241 @@
+/*
+ * fc.h - C ABI of the GB300 (sm_103a) online all-to-all functional connectivity library.
+ *
+ * The library follows the statement of the problem in Esch et al., "Online functional
+ * connectivity analysis of large all-to-all networks" (arXiv 2303.03279):
+ *   - trials arrive as node x sample matrices (Methods 2.4, 2.5; Results 3.2.3: 265 x 250);
+ *   - per trial, a spectrum per node, then the cross-spectral density CSD_xy = x y* and the
+ *     power spectral density PSD_x = A_x^2 (Supplementary Information 1, Frequency Domain);
+ *   - running sums of those over the trials being averaged (Methods 2.4: "the sums of CSD
+ *     and PSD over all trials are directly computed"), only one half of the edge weights
+ *     (Methods 2.4: undirected metrics);
+ *   - the user sets the number of trials to average, and each new trial is added to the
+ *     network (Methods 2.5; Results 3.2.3), with stored per-trial intermediates reused
+ *     (Methods 2.4 storage mode; Discussion);
+ *   - metrics COR, XCOR, COH, IMAGCOHY, PLV, PLI, USPLI, WPLI, DSWPLI (Methods 2.1,
+ *     Supplementary Information 1), band-averaged over the selected frequency bins
+ *     (Results 3.2.1, 3.2.3), returned as a network of nodes and weighted edges.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an fc_status and never throws or aborts. On failure,
+ *     fc_last_error() returns a thread-local, library-owned message.
+ *   - The library owns only the session handle and the device memory it allocates for
+ *     the session. Every input and output buffer belongs to the caller; the library
+ *     copies inputs and never keeps a caller pointer past the call.
+ *   - Work is enqueued on the session's CUDA stream (fc_config.stream, or a stream the
+ *     library creates). Calls returning data into host memory synchronize that stream;
+ *     calls with device outputs do not.
+ *   - Pointers marked "host or device" are interpreted according to the *_on_device flag.
+ *   - Node pairs are (i, j) with i < j. "Packed upper" layout: pair (i, j) at index
+ *     p = i*n - i*(i+1)/2 + (j - i - 1), P = n*(n-1)/2 entries.
+ *   - There is no CPU fallback: a session can only be created when a CUDA device is
+ *     present; otherwise fc_session_create returns FC_ERR_CUDA.
+ */
+#ifndef FC_H
+#define FC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fc_session fc_session; /* opaque, library-owned */
+
+typedef enum {
+    FC_OK = 0,
+    FC_ERR_INVALID_ARG = -1,   /* a null pointer, a size out of range, a bad flag */
+    FC_ERR_OUT_OF_MEMORY = -2, /* device or host allocation failed; nothing was changed */
+    FC_ERR_CUDA = -3,          /* a CUDA runtime error (message in fc_last_error) */
+    FC_ERR_NOT_READY = -4,     /* no trial has been accepted yet */
+    FC_ERR_TIMEOUT = -5,       /* a bounded device-side wait ran out */
+    FC_ERR_ADMISSION = -6,     /* a server refused a session: HBM budget exhausted */
+    FC_ERR_NONFINITE = -7,     /* a pushed trial held NaN/Inf and was rejected */
+    FC_ERR_UNSUPPORTED = -8    /* a valid request this build does not implement */
+} fc_status;
+
+/* Metric bits (Methods 2.1 list; definitions in Supplementary Information 1). */
+enum {
+    FC_COR = 1u << 0,      /* Pearson correlation, mean over trials */
+    FC_XCOR = 1u << 1,     /* maximum normalised cross-correlation, mean over trials */
+    FC_COH = 1u << 2,      /* |COHY| */
+    FC_IMAGCOHY = 1u << 3, /* Im(COHY), antisymmetric: (j,i) = -(i,j) */
+    FC_PLV = 1u << 4,      /* |mean of e^{i(Phi_x - Phi_y)}| */
+    FC_PLI = 1u << 5,      /* |mean of sign(Im CSD)| */
+    FC_USPLI = 1u << 6,    /* (K PLI^2 - 1)/(K - 1); NaN for K < 2 */
+    FC_WPLI = 1u << 7,     /* |mean Im CSD| / mean |Im CSD| */
+    FC_DSWPLI = 1u << 8    /* ((sum Im)^2 - sum Im^2)/((sum |Im|)^2 - sum Im^2) */
+};
+#define FC_SPECTRAL_METRICS (FC_COH | FC_IMAGCOHY | FC_PLV | FC_PLI | FC_USPLI | FC_WPLI | FC_DSWPLI)
+#define FC_ALL_METRICS (FC_COR | FC_XCOR | FC_SPECTRAL_METRICS)
+
+typedef enum {
+    FC_TAPER_NONE = 0,
+    FC_TAPER_HANN = 1,    /* periodic Hann, w(t) = 0.5 - 0.5 cos(2 pi t / N) */
+    FC_TAPER_HANN_SYM = 2 /* symmetric Hann, w(t) = 0.5 - 0.5 cos(2 pi t / (N - 1)) */
+} fc_taper;
+
+/* Frequency band: every bin k (0 <= k <= nfft/2) with f_lo <= k*fs/nfft < f_hi.
+ * nfft >= n_samples (the trial is zero-padded to nfft). */
+typedef struct {
+    double f_lo;
+    double f_hi;
+    int nfft;
+} fc_band;
+
+typedef enum {
+    FC_PREC_FP32 = 0, /* every sum from exactly rounded FP32 terms, FP64-class accumulation */
+    FC_PREC_TF32 = 1, /* full-window linear sums on tensor cores, TF32 operands, FP32 accumulate */
+    FC_PREC_BF16 = 2, /* same with BF16 operands */
+    FC_PREC_FP16 = 3  /* same with FP16 operands */
+} fc_precision;
+
+typedef enum {
+    FC_MODE_STREAM = 0, /* resident accumulators; each push adds the new trial and
+                           subtracts the one leaving the window (Methods 2.4 storage mode) */
+    FC_MODE_FULL = 1    /* no accumulators; each push recomputes the window from the stored
+                           spectra (the storage-off comparison of Results 3.1) */
+} fc_mode;
+
+typedef struct {
+    fc_precision precision;
+    fc_mode mode;
+    void* stream;     /* cudaStream_t to enqueue on; NULL: the library creates one */
+    int resum_period; /* stream mode: pushes between re-sums of the accumulators from the
+                         stored spectra (drift reset); 0 = the window length; -1 = never */
+    /* Optional device allocator (e.g. a framework's caching allocator). Both NULL: cudaMalloc. */
+    void* (*dev_alloc)(size_t bytes, void* ctx);
+    void (*dev_free)(void* ptr, void* ctx);
+    void* alloc_ctx;
+} fc_config;
+
+typedef struct {
+    int n_nodes, n_samples, n_bins, first_bin, nfft;
+    int window;           /* W (0 = cumulative) */
+    int k_used;           /* trials in the current window (after completed work) */
+    long long pushes;     /* accepted pushes */
+    long long rejected;   /* pushes rejected as non-finite */
+    long long pairs;      /* P = n (n - 1) / 2 */
+    size_t device_bytes;  /* device memory held by the session */
+    uint32_t metric_mask;
+    fc_mode mode;
+    fc_precision precision;
+} fc_info;
+
+/* Fill *cfg with the defaults: FP32, stream mode, library stream, resum_period 0, cudaMalloc. */
+fc_status fc_config_default(fc_config* cfg);
+
+/* Create a session (Methods 2.4/2.5 settings: nodes, samples, sampling rate, band, taper,
+ * metrics, number of trials to average).
+ *   n_nodes >= 2, 1 <= n_samples <= band.nfft, fs > 0, the band selects >= 1 bin;
+ *   metric_mask: nonzero subset of FC_ALL_METRICS;
+ *   window: W >= 0 trials (0 = cumulative; FC_MODE_FULL needs W >= 1);
+ *   cfg: NULL for defaults. *out receives the handle; on failure *out is NULL and nothing
+ *   stays allocated. Errors: FC_ERR_INVALID_ARG, FC_ERR_OUT_OF_MEMORY, FC_ERR_CUDA. */
+fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band, fc_taper taper,
+                            uint32_t metric_mask, int window, const fc_config* cfg,
+                            fc_session** out);
+
+/* Synchronize the session's stream and free everything it holds. NULL is accepted. */
+fc_status fc_session_destroy(fc_session* s);
+
+/* Push one trial x[n_nodes][n_samples] (float32, row-major, host or device). The trial is
+ * copied; a pageable host buffer may be reused on return, a page-locked one or a device
+ * buffer once the session's stream has passed this call (fc_sync). A trial holding NaN or
+ * Inf is rejected on the device and leaves the state unchanged; the next synchronizing
+ * call (fc_sync, fc_get_network, fc_session_info) then reports FC_ERR_NONFINITE once. */
+fc_status fc_push_trial(fc_session* s, const float* x, int x_on_device);
+
+/* Push `count` trials x[count][n_nodes][n_samples] (host or device) and update the network
+ * once at the end. Same copying and rejection rules as fc_push_trial, per trial. */
+fc_status fc_push_trials(fc_session* s, const float* x, int count, int x_on_device);
+
+/* Band-averaged network of one metric (a single bit of the session's mask).
+ *   packed_upper = 1: out[P] in the packed upper layout; 0: out[n][n] dense, diagonal 0,
+ *   symmetric except IMAGCOHY (antisymmetric). out_len: element capacity of out.
+ *   k_used (nullable) receives the number of trials the network averages.
+ * Errors: FC_ERR_NOT_READY before the first accepted trial, FC_ERR_INVALID_ARG. */
+fc_status fc_get_network(fc_session* s, uint32_t metric, int packed_upper, float* out,
+                         size_t out_len, int out_on_device, int* k_used);
+
+/* Per-bin values of one spectral metric, out[n_bins][P] (packed upper per bin). */
+fc_status fc_get_network_bins(fc_session* s, uint32_t metric, float* out, size_t out_len,
+                              int out_on_device);
+
+/* Argmax lags of XCOR for the most recent trial, out[P] (int32, packed upper): for pair
+ * (i, j) the lag tau of max_tau sum_t x_i(t + tau) x_j(t). Needs FC_XCOR in the mask. */
+fc_status fc_get_xcor_lags(fc_session* s, int32_t* out, size_t out_len, int out_on_device);
+
+/* Switch the set of finalized metrics (Results 3.2.3: metrics switched on the fly). The
+ * accumulators are shared, so a switch recomputes only the networks. Time-domain bits
+ * (COR, XCOR) can only be kept or removed, not added after creation. */
+fc_status fc_set_metric_mask(fc_session* s, uint32_t metric_mask);
+
+/* Wait for the session's stream; reports a pending FC_ERR_NONFINITE. */
+fc_status fc_sync(fc_session* s);
+
+/* Session facts (synchronizes). */
+fc_status fc_session_info(fc_session* s, fc_info* info);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* fc_last_error(void);
+
+/* ---- measurement hooks ------------------------------------------------------------ */
+
+/* Kernel ids reported by fc_kernel_times. */
+typedef enum {
+    FC_K_SPECTRUM = 0, /* taper + band DFT of one or more trials */
+    FC_K_CALIBRATE,    /* one-time power-of-two prescale of the spectra */
+    FC_K_NODE,         /* per-node PSD sums */
+    FC_K_STREAM,       /* streaming add/subtract update with fused finalize */
+    FC_K_WINDOW,       /* CUDA-core full-window sums (all terms) with fused finalize */
+    FC_K_HERK_TC,      /* tensor-core Hermitian rank-K linear sums */
+    FC_K_BAND_REDUCE,  /* band average of per-bin-group partial sums */
+    FC_K_COR,          /* correlation products */
+    FC_K_XCOR,         /* cross-correlation via FFT */
+    FC_K_OTHER,
+    FC_K_COUNT
+} fc_kernel_id;
+
+typedef struct {
+    int launches;
+    double total_ms;
+} fc_kernel_time;
+
+/* Enable (1) or disable (0) per-launch CUDA-event timing on the session's stream. */
+fc_status fc_set_profiling(fc_session* s, int enable);
+
+/* Accumulated per-kernel timings since profiling was enabled or reset (synchronizes).
+ * out[FC_K_COUNT]. reset = 1 clears the counters after reading. */
+fc_status fc_kernel_times(fc_session* s, fc_kernel_time* out, int reset);
+
+/* Total kernel launches this session has enqueued. */
+long long fc_launch_count(const fc_session* s);
+
+/* The session's CUDA stream (cudaStream_t), e.g. to record events on it. */
+void* fc_session_stream(const fc_session* s);
+
+/* ---- test hooks ------------------------------------------------------------------- */
+
+/* Spectra of the trial pushed `age` accepted pushes ago (0 = newest), as the kernels hold
+ * them (after the session's power-of-two prescale): out[n_bins][n_nodes][2] (re, im). */
+fc_status fc_debug_get_spectra(fc_session* s, int age, float* out, size_t out_len);
+
+/* The power-of-two factor the spectra were multiplied by (all metrics are invariant). */
+fc_status fc_debug_get_scale(fc_session* s, float* scale);
+
+/* Accumulator fields (stream mode), each out[n_bins][P] in double (hi + lo of the
+ * double-float pairs); FC_ACC_PSD gives out[n_bins][n_nodes]. */
+typedef enum {
+    FC_ACC_CSD_RE = 0, FC_ACC_CSD_IM, FC_ACC_U_RE, FC_ACC_U_IM, FC_ACC_ABS, FC_ACC_SQ,
+    FC_ACC_SIGN, FC_ACC_PSD, FC_ACC_COR, FC_ACC_XCOR
+} fc_acc_field;
+fc_status fc_debug_get_accumulators(fc_session* s, fc_acc_field field, double* out,
+                                    size_t out_len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FC_H */

@@ -1,0 +1,779 @@
+// fc_api.cu - the C ABI (include/fc.h): sessions, device state, push sequencing.
+//
+// A push enqueues, on the session's stream and without waiting for the device:
+//   validate  -> taper + band spectrum into the ring slot of the new trial
+//   -> (first pushes) power-of-two calibration of the spectra
+//   -> per-node PSD sums -> pair update (streaming add/subtract, or a full re-sum of the
+//      window every `resum_period` pushes, or the full-window recompute in FC_MODE_FULL)
+//   -> band reduction (small sessions) -> COR / XCOR -> commit.
+// The window position lives in a device control block, so a rejected (non-finite) trial
+// is skipped by every kernel and the host never synchronizes inside a push.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "fc_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+fc_status fail(fc_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(FC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+
+const double kPi = 3.14159265358979323846;
+
+int metric_index(uint32_t bit) {
+    for (int i = 0; i < FC_NMETRIC; ++i)
+        if (bit == (1u << i)) return i;
+    return -1;
+}
+
+fc_status dev_alloc(fc_session* s, size_t bytes, void** out) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (s->cfg.dev_alloc) {
+        p = s->cfg.dev_alloc(bytes, s->cfg.alloc_ctx);
+        if (!p) return fail(FC_ERR_OUT_OF_MEMORY, "device allocator returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FC_ERR_OUT_OF_MEMORY, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    s->allocations.push_back(p);
+    s->device_bytes += bytes;
+    *out = p;
+    return FC_OK;
+}
+
+template <class T>
+fc_status alloc_zero(fc_session* s, size_t count, T** out) {
+    void* p;
+    fc_status st = dev_alloc(s, count * sizeof(T), &p);
+    if (st != FC_OK) return st;
+    CK(cudaMemsetAsync(p, 0, count * sizeof(T), s->stream));
+    *out = static_cast<T*>(p);
+    return FC_OK;
+}
+
+void free_all(fc_session* s) {
+    for (void* p : s->allocations) {
+        if (s->cfg.dev_free)
+            s->cfg.dev_free(p, s->cfg.alloc_ctx);
+        else if (!s->cfg.dev_alloc)
+            cudaFree(p);
+    }
+    s->allocations.clear();
+}
+
+// -------------------------------------------------------------- profiling wrapper
+std::vector<cudaEvent_t>& event_pool() {
+    static thread_local std::vector<cudaEvent_t> pool;
+    return pool;
+}
+
+cudaEvent_t get_event() {
+    auto& pool = event_pool();
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+template <class F>
+fc_status launch(fc_session* s, int kid, F&& f) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (s->profiling) {
+        e0 = get_event();
+        e1 = get_event();
+        cudaEventRecord(e0, s->stream);
+    }
+    cudaError_t e = f();
+    s->launches++;
+    if (s->profiling) {
+        cudaEventRecord(e1, s->stream);
+        s->pending.push_back({kid, e0, e1});
+    }
+    if (e != cudaSuccess) return fail(FC_ERR_CUDA, "kernel %d launch failed: %s", kid, cudaGetErrorString(e));
+    return FC_OK;
+}
+
+#define LAUNCH(kid, expr)                                              \
+    do {                                                               \
+        fc_status st_ = launch(s, (kid), [&]() { return (expr); });    \
+        if (st_ != FC_OK) return st_;                                  \
+    } while (0)
+
+fc_status drain_timings(fc_session* s) {
+    for (auto& p : s->pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, p.start, p.stop);
+        if (e == cudaSuccess) {
+            s->ktime[p.kernel].launches += 1;
+            s->ktime[p.kernel].total_ms += ms;
+        }
+        event_pool().push_back(p.start);
+        event_pool().push_back(p.stop);
+    }
+    s->pending.clear();
+    return FC_OK;
+}
+
+// ------------------------------------------------------------------ argument packs
+PairArgs pair_args(fc_session* s, bool stream_kernel, int count) {
+    PairArgs a{};
+    a.ring = s->ring;
+    a.inv_psd = s->inv_psd;
+    a.acc = s->acc;
+    a.tile_a = s->tile_a;
+    a.tile_b = s->tile_b;
+    a.net = s->net;
+    a.partial = s->partial;
+    a.slots = s->slots;
+    a.n = s->n;
+    a.B = s->B;
+    a.W = s->W;
+    a.ntp = s->ntp;
+    a.P = s->P;
+    a.groups = stream_kernel ? s->stream_groups : s->groups;
+    a.group_bins = stream_kernel ? s->stream_group_bins : s->group_bins;
+    a.mask = s->mask;
+    a.finalize = 1;
+    a.update = 1;
+    a.write_acc = 0;
+    a.count = count;
+    a.ctrl = s->ctrl;
+    return a;
+}
+
+SpectrumArgs spectrum_args(fc_session* s, const float* x, int count, int write_from) {
+    SpectrumArgs a{};
+    a.x = x;
+    a.count = count;
+    a.write_from = write_from;
+    a.twiddle = s->twiddle;
+    a.ring = s->ring;
+    a.slots = s->slots;
+    a.n = s->n;
+    a.N = s->N;
+    a.B = s->B;
+    a.ctrl = s->ctrl;
+    return a;
+}
+
+CorArgs cor_args(fc_session* s, const float* x, int count, int write_from, int mode) {
+    CorArgs a{};
+    a.x = x;
+    a.count = count;
+    a.write_from = write_from;
+    a.zring = s->zring;
+    a.cor_acc = s->cor_acc;
+    a.net = s->net + (size_t)MI_COR * s->P;
+    a.slots = s->slots;
+    a.n = s->n;
+    a.N = s->N;
+    a.W = s->W;
+    a.P = s->P;
+    a.mode = mode;
+    a.finalize = (s->mask & FC_COR) ? 1 : 0;
+    a.ctrl = s->ctrl;
+    return a;
+}
+
+XcorArgs xcor_args(fc_session* s, const float* x, int count, int write_from, int mode) {
+    XcorArgs a{};
+    a.x = x;
+    a.count = count;
+    a.write_from = write_from;
+    a.n = s->n;
+    a.N = s->N;
+    a.L = s->xcor_L;
+    a.W = s->W;
+    a.slots = s->slots;
+    a.P = s->P;
+    a.tw = s->xcor_tw;
+    a.spec = s->xcor_spec;
+    a.energy = s->xcor_energy;
+    a.vals = s->xcor_vals;
+    a.lag = s->xcor_lag;
+    a.acc = s->xcor_acc;
+    a.net = s->net + (size_t)MI_XCOR * s->P;
+    a.mode = mode;
+    a.finalize = (s->mask & FC_XCOR) ? 1 : 0;
+    a.ctrl = s->ctrl;
+    return a;
+}
+
+// ------------------------------------------------------------------ push stages
+fc_status stage_spectra(fc_session* s, const float* x, int count, int write_from) {
+    SpectrumArgs sa = spectrum_args(s, x, count, write_from);
+    LAUNCH(FC_K_SPECTRUM, launch_spectrum(sa, s->stream));
+    if (!s->calibrated) {
+        for (int ph = 0; ph < 3; ++ph) LAUNCH(FC_K_CALIBRATE, launch_calibrate(sa, s->stream, ph));
+    }
+    return FC_OK;
+}
+
+fc_status stage_time_metrics(fc_session* s, const float* x, int count, int write_from, int mode) {
+    if (s->time_mask & FC_COR) {
+        CorArgs ca = cor_args(s, x, count, write_from, mode);
+        LAUNCH(FC_K_COR, launch_cor_normalize(ca, s->stream));
+        LAUNCH(FC_K_COR, launch_cor_update(ca, s->stream));
+    }
+    if (s->time_mask & FC_XCOR) {
+        XcorArgs xa = xcor_args(s, x, count, write_from, mode);
+        LAUNCH(FC_K_XCOR, launch_xcor_spectra(xa, s->stream));
+        LAUNCH(FC_K_XCOR, launch_xcor_pairs(xa, s->stream));
+        LAUNCH(FC_K_XCOR, launch_xcor_update(xa, s->stream));
+    }
+    return FC_OK;
+}
+
+// Spectral pair sums over the whole window (bulk push, re-sum, full mode).
+fc_status stage_window(fc_session* s, int count, bool write_acc) {
+    NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, 1, s->ctrl, count};
+    LAUNCH(FC_K_NODE, launch_node(na, s->stream));
+    PairArgs pa = pair_args(s, false, count);
+    pa.write_acc = write_acc ? 1 : 0;
+    pa.finalize = (s->mask & FC_SPECTRAL_METRICS) ? 1 : 0;
+    LAUNCH(FC_K_WINDOW, launch_window_sums(pa, s->stream));
+    if (pa.finalize && pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
+    return FC_OK;
+}
+
+// One trial through the streaming path: x points at one [n][N] trial on the device.
+fc_status push_one_stream(fc_session* s, const float* x, bool finalize) {
+    const long long nx = (long long)s->n * s->N;
+    LAUNCH(FC_K_OTHER, launch_validate(x, nx, s->ctrl, s->stream));
+    fc_status st = stage_spectra(s, x, 1, 0);
+    if (st != FC_OK) return st;
+    const bool resum = s->W > 0 && s->cfg.resum_period >= 0 &&
+                       s->since_resum + 1 >= (s->cfg.resum_period > 0 ? s->cfg.resum_period : s->W);
+    if (resum) {
+        st = stage_window(s, 1, true);
+        if (st != FC_OK) return st;
+        s->since_resum = 0;
+    } else {
+        NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, 0, s->ctrl, 1};
+        LAUNCH(FC_K_NODE, launch_node(na, s->stream));
+        PairArgs pa = pair_args(s, true, 1);
+        pa.finalize = (finalize && (s->mask & FC_SPECTRAL_METRICS)) ? 1 : 0;
+        LAUNCH(FC_K_STREAM, launch_stream_update(pa, s->stream));
+        if (pa.finalize && pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
+        s->since_resum++;
+    }
+    st = stage_time_metrics(s, x, 1, 0, 0);
+    if (st != FC_OK) return st;
+    CommitArgs ca{s->ctrl, 1};
+    LAUNCH(FC_K_OTHER, launch_commit(ca, s->stream));
+    s->enqueued += 1;
+    return FC_OK;
+}
+
+// Many trials at once, then one window computation (stream bulk or full mode).
+fc_status push_bulk(fc_session* s, const float* x, int count, bool write_acc) {
+    const long long nx = (long long)s->n * s->N;
+    LAUNCH(FC_K_OTHER, launch_validate(x, nx * count, s->ctrl, s->stream));
+    const int keep = s->W > 0 ? std::min(count, s->W) : count;
+    const int write_from = count - keep;
+    fc_status st = stage_spectra(s, x, count, write_from);
+    if (st != FC_OK) return st;
+    st = stage_window(s, count, write_acc);
+    if (st != FC_OK) return st;
+    st = stage_time_metrics(s, x, count, write_from, 1);
+    if (st != FC_OK) return st;
+    CommitArgs ca{s->ctrl, count};
+    LAUNCH(FC_K_OTHER, launch_commit(ca, s->stream));
+    s->enqueued += count;
+    if (write_acc) s->since_resum = 0;
+    return FC_OK;
+}
+
+fc_status ensure_stage(fc_session* s, int count) {
+    if (count <= s->stage_trials) return FC_OK;
+    void* p;
+    fc_status st = dev_alloc(s, (size_t)count * s->n * s->N * sizeof(float), &p);
+    if (st != FC_OK) return st;
+    s->x_stage = static_cast<float*>(p);
+    s->stage_trials = count;
+    return FC_OK;
+}
+
+fc_status read_ctrl(fc_session* s, FcCtrl* h) {
+    CK(cudaMemcpyAsync(h, s->ctrl, sizeof(FcCtrl), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (h->scale != 0.f) s->calibrated = true;
+    return FC_OK;
+}
+
+fc_status check_latched(fc_session* s, FcCtrl* h) {
+    fc_status st = read_ctrl(s, h);
+    if (st != FC_OK) return st;
+    if (h->bad_latched) {
+        CK(cudaMemsetAsync(&s->ctrl->bad_latched, 0, sizeof(int), s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        return fail(FC_ERR_NONFINITE, "a pushed trial held NaN or Inf and was rejected (%lld rejected so far)",
+                    h->rejected);
+    }
+    return FC_OK;
+}
+
+}  // namespace
+
+// ====================================================================== public API
+extern "C" {
+
+const char* fc_last_error(void) { return g_err.c_str(); }
+
+fc_status fc_config_default(fc_config* cfg) {
+    if (!cfg) return fail(FC_ERR_INVALID_ARG, "cfg is NULL");
+    memset(cfg, 0, sizeof *cfg);
+    cfg->precision = FC_PREC_FP32;
+    cfg->mode = FC_MODE_STREAM;
+    cfg->resum_period = 0;
+    return FC_OK;
+}
+
+fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band, fc_taper taper,
+                            uint32_t metric_mask, int window, const fc_config* cfg_in,
+                            fc_session** out) {
+    if (!out) return fail(FC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    fc_config cfg;
+    if (cfg_in) cfg = *cfg_in; else fc_config_default(&cfg);
+    if (n_nodes < 2 || n_nodes > 65535 * FC_T) return fail(FC_ERR_INVALID_ARG, "n_nodes %d out of range", n_nodes);
+    if (n_samples < 1) return fail(FC_ERR_INVALID_ARG, "n_samples %d < 1", n_samples);
+    if (!(fs > 0.0) || !std::isfinite(fs)) return fail(FC_ERR_INVALID_ARG, "fs must be positive");
+    if (band.nfft < n_samples) return fail(FC_ERR_INVALID_ARG, "nfft %d < n_samples %d", band.nfft, n_samples);
+    if (!(band.f_lo < band.f_hi)) return fail(FC_ERR_INVALID_ARG, "band f_lo must be < f_hi");
+    if (taper < FC_TAPER_NONE || taper > FC_TAPER_HANN_SYM) return fail(FC_ERR_INVALID_ARG, "bad taper");
+    if (metric_mask == 0 || (metric_mask & ~(uint32_t)FC_ALL_METRICS))
+        return fail(FC_ERR_INVALID_ARG, "bad metric mask 0x%x", metric_mask);
+    if (window < 0) return fail(FC_ERR_INVALID_ARG, "window must be >= 0");
+    if (cfg.mode != FC_MODE_STREAM && cfg.mode != FC_MODE_FULL) return fail(FC_ERR_INVALID_ARG, "bad mode");
+    if (cfg.mode == FC_MODE_FULL && window < 1) return fail(FC_ERR_INVALID_ARG, "full mode needs window >= 1");
+    if (cfg.precision < FC_PREC_FP32 || cfg.precision > FC_PREC_FP16) return fail(FC_ERR_INVALID_ARG, "bad precision");
+    if (cfg.precision != FC_PREC_FP32)
+        return fail(FC_ERR_UNSUPPORTED, "tensor-core precisions are not available in this build");
+    if ((cfg.dev_alloc == nullptr) != (cfg.dev_free == nullptr))
+        return fail(FC_ERR_INVALID_ARG, "dev_alloc and dev_free must be given together");
+    // band bins: f_lo <= k fs / nfft < f_hi
+    int first = -1, B = 0;
+    for (int k = 0; k <= band.nfft / 2; ++k) {
+        const double kf = (double)k * fs;
+        if (kf >= band.f_lo * band.nfft && kf < band.f_hi * band.nfft) {
+            if (first < 0) first = k;
+            ++B;
+        }
+    }
+    if (B == 0) return fail(FC_ERR_INVALID_ARG, "the band selects no bin");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(FC_ERR_CUDA, "no CUDA device: this library has no CPU path");
+    }
+
+    fc_session* s = new (std::nothrow) fc_session();
+    if (!s) return fail(FC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    s->n = n_nodes;
+    s->N = n_samples;
+    s->B = B;
+    s->first_bin = first;
+    s->nfft = band.nfft;
+    s->W = window;
+    s->fs = fs;
+    s->band = band;
+    s->taper = taper;
+    s->mask = metric_mask;
+    s->time_mask = metric_mask & (FC_COR | FC_XCOR);
+    s->cfg = cfg;
+    s->nt = (n_nodes + FC_T - 1) / FC_T;
+    s->ntp = s->nt * (s->nt + 1) / 2;
+    s->P = (long long)n_nodes * (n_nodes - 1) / 2;
+    s->slots = cfg.mode == FC_MODE_FULL ? window : (window > 0 ? window + 1 : 1);
+    cudaGetDevice(&s->device);
+
+    auto cleanup = [&](fc_status st) {
+        if (s->stream) cudaStreamSynchronize(s->stream);
+        free_all(s);
+        if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+        delete s;
+        return st;
+    };
+
+    if (cfg.stream) {
+        s->stream = static_cast<cudaStream_t>(cfg.stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cleanup(fail(FC_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+        s->own_stream = true;
+    }
+
+    // work split: enough CTAs to fill 152 SMs twice over
+    const int target = 152 * 4;
+    s->groups = std::min(B, std::max(1, (target + s->ntp - 1) / s->ntp));
+    s->group_bins = (B + s->groups - 1) / s->groups;
+    s->groups = (B + s->group_bins - 1) / s->group_bins;
+    s->stream_groups = s->groups;
+    s->stream_group_bins = s->group_bins;
+    const int max_groups = std::max(s->groups, s->stream_groups);
+
+    fc_status st;
+#define TRY(x) do { st = (x); if (st != FC_OK) return cleanup(st); } while (0)
+    TRY(alloc_zero(s, 1, &s->ctrl));
+    // taper-folded DFT factors, FP64 on the host with exact angle reduction
+    {
+        std::vector<float2> tw((size_t)n_samples * B);
+        for (int t = 0; t < n_samples; ++t) {
+            double w = 1.0;
+            if (taper == FC_TAPER_HANN) w = 0.5 - 0.5 * std::cos(2.0 * kPi * t / n_samples);
+            if (taper == FC_TAPER_HANN_SYM) w = n_samples > 1 ? 0.5 - 0.5 * std::cos(2.0 * kPi * t / (n_samples - 1)) : 1.0;
+            for (int b = 0; b < B; ++b) {
+                const long long m = ((long long)(first + b) * t) % band.nfft;
+                const double ang = 2.0 * kPi * (double)m / band.nfft;
+                tw[(size_t)t * B + b] = make_float2((float)(w * std::cos(ang)), (float)(-w * std::sin(ang)));
+            }
+        }
+        TRY(alloc_zero(s, tw.size(), &s->twiddle));
+        cudaError_t e = cudaMemcpyAsync(s->twiddle, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) return cleanup(fail(FC_ERR_CUDA, "twiddle upload: %s", cudaGetErrorString(e)));
+        cudaStreamSynchronize(s->stream);
+    }
+    TRY(alloc_zero(s, (size_t)s->slots * B * n_nodes, &s->ring));
+    TRY(alloc_zero(s, (size_t)B * n_nodes, &s->psd));
+    TRY(alloc_zero(s, (size_t)B * n_nodes, &s->inv_psd));
+    {
+        std::vector<unsigned short> ta, tb;
+        for (int a = 0; a < s->nt; ++a)
+            for (int b = a; b < s->nt; ++b) {
+                ta.push_back((unsigned short)a);
+                tb.push_back((unsigned short)b);
+            }
+        TRY(alloc_zero(s, ta.size(), &s->tile_a));
+        TRY(alloc_zero(s, tb.size(), &s->tile_b));
+        cudaMemcpy(s->tile_a, ta.data(), ta.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
+        cudaMemcpy(s->tile_b, tb.data(), tb.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
+    }
+    if (cfg.mode == FC_MODE_STREAM) TRY(alloc_zero(s, (size_t)s->ntp * B * FC_BLOCK_WORDS, &s->acc));
+    TRY(alloc_zero(s, (size_t)FC_NMETRIC * s->P, &s->net));
+    if (max_groups > 1) TRY(alloc_zero(s, (size_t)max_groups * 7 * s->P, &s->partial));
+    if (s->time_mask & FC_COR) {
+        TRY(alloc_zero(s, (size_t)s->slots * n_nodes * n_samples, &s->zring));
+        TRY(alloc_zero(s, (size_t)2 * s->P, &s->cor_acc));
+    }
+    if (s->time_mask & FC_XCOR) {
+        int L = 1;
+        while (L < 2 * n_samples - 1) L *= 2;
+        if (L < 64) L = 64;
+        s->xcor_L = L;
+        if (L > 8192) return cleanup(fail(FC_ERR_UNSUPPORTED, "XCOR supports n_samples <= 4096"));
+        const int M = L / 2;
+        std::vector<float2> xt(M);
+        for (int k = 0; k < M; ++k) {
+            const double ang = 2.0 * kPi * k / L;
+            xt[k] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
+        }
+        TRY(alloc_zero(s, (size_t)M, &s->xcor_tw));
+        cudaMemcpy(s->xcor_tw, xt.data(), M * sizeof(float2), cudaMemcpyHostToDevice);
+        TRY(alloc_zero(s, (size_t)s->slots * n_nodes * (M + 1), &s->xcor_spec));
+        TRY(alloc_zero(s, (size_t)s->slots * n_nodes, &s->xcor_energy));
+        TRY(alloc_zero(s, (size_t)s->slots * s->P, &s->xcor_vals));
+        TRY(alloc_zero(s, (size_t)s->P, &s->xcor_lag));
+        TRY(alloc_zero(s, (size_t)2 * s->P, &s->xcor_acc));
+    }
+    TRY(ensure_stage(s, 1));
+#undef TRY
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cleanup(fail(FC_ERR_CUDA, "session init: %s", cudaGetErrorString(e)));
+    *out = s;
+    return FC_OK;
+}
+
+fc_status fc_session_destroy(fc_session* s) {
+    if (!s) return FC_OK;
+    cudaSetDevice(s->device);
+    cudaStreamSynchronize(s->stream);
+    drain_timings(s);
+    free_all(s);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    if (s->dense_scratch) cudaFree(s->dense_scratch);
+    delete s;
+    return FC_OK;
+}
+
+fc_status fc_push_trials(fc_session* s, const float* x, int count, int x_on_device) {
+    if (!s || !x) return fail(FC_ERR_INVALID_ARG, "NULL session or trial pointer");
+    if (count < 1) return fail(FC_ERR_INVALID_ARG, "count must be >= 1");
+    CK(cudaSetDevice(s->device));
+    const float* xd = x;
+    const size_t per = (size_t)s->n * s->N;
+    if (!x_on_device) {
+        fc_status st = ensure_stage(s, count);
+        if (st != FC_OK) return st;
+        CK(cudaMemcpyAsync(s->x_stage, x, per * count * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+        xd = s->x_stage;
+    }
+    if (s->cfg.mode == FC_MODE_FULL) return push_bulk(s, xd, count, false);
+    const bool bulk = s->W > 0 && count >= std::max(2, s->W / 4);
+    if (bulk) return push_bulk(s, xd, count, true);
+    for (int u = 0; u < count; ++u) {
+        fc_status st = push_one_stream(s, xd + per * u, u == count - 1);
+        if (st != FC_OK) return st;
+    }
+    return FC_OK;
+}
+
+fc_status fc_push_trial(fc_session* s, const float* x, int x_on_device) {
+    return fc_push_trials(s, x, 1, x_on_device);
+}
+
+fc_status fc_sync(fc_session* s) {
+    if (!s) return fail(FC_ERR_INVALID_ARG, "NULL session");
+    CK(cudaSetDevice(s->device));
+    FcCtrl h;
+    return check_latched(s, &h);
+}
+
+fc_status fc_get_network(fc_session* s, uint32_t metric, int packed_upper, float* out, size_t out_len,
+                         int out_on_device, int* k_used) {
+    if (!s || !out) return fail(FC_ERR_INVALID_ARG, "NULL session or output");
+    const int mi = metric_index(metric);
+    if (mi < 0) return fail(FC_ERR_INVALID_ARG, "metric must be a single FC_* bit");
+    if (!(s->mask & metric)) return fail(FC_ERR_INVALID_ARG, "metric 0x%x is not in the session mask", metric);
+    const size_t need = packed_upper ? (size_t)s->P : (size_t)s->n * s->n;
+    if (out_len < need) return fail(FC_ERR_INVALID_ARG, "out_len %zu < %zu", out_len, need);
+    CK(cudaSetDevice(s->device));
+    if (s->enqueued == 0) return fail(FC_ERR_NOT_READY, "no trial has been pushed");
+    if (!out_on_device || k_used) {
+        FcCtrl h;
+        fc_status st = check_latched(s, &h);
+        if (st != FC_OK) return st;
+        if (h.pushed == 0) return fail(FC_ERR_NOT_READY, "no trial has been accepted");
+        if (k_used) *k_used = (int)((s->W > 0 && h.pushed > s->W) ? s->W : h.pushed);
+    }
+    const float* src = s->net + (size_t)mi * s->P;
+    if (packed_upper) {
+        CK(cudaMemcpyAsync(out, src, need * sizeof(float),
+                           out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+    } else {
+        float* dst = out;
+        if (!out_on_device) {
+            if (s->dense_scratch_len < need) {
+                if (s->dense_scratch) cudaFree(s->dense_scratch);
+                s->dense_scratch = nullptr;
+                s->dense_scratch_len = 0;
+                CK(cudaMalloc(&s->dense_scratch, need * sizeof(float)));
+                s->dense_scratch_len = need;
+            }
+            dst = s->dense_scratch;
+        }
+        LAUNCH(FC_K_OTHER, launch_expand_dense(src, dst, s->n, mi == MI_IMAGCOHY, s->stream));
+        if (!out_on_device) CK(cudaMemcpyAsync(out, dst, need * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    }
+    if (!out_on_device) CK(cudaStreamSynchronize(s->stream));
+    return FC_OK;
+}
+
+fc_status fc_get_network_bins(fc_session* s, uint32_t metric, float* out, size_t out_len, int out_on_device) {
+    if (!s || !out) return fail(FC_ERR_INVALID_ARG, "NULL session or output");
+    const int mi = metric_index(metric);
+    if (mi < MI_COH) return fail(FC_ERR_INVALID_ARG, "per-bin values exist for spectral metrics only");
+    const size_t need = (size_t)s->B * s->P;
+    if (out_len < need) return fail(FC_ERR_INVALID_ARG, "out_len %zu < %zu", out_len, need);
+    CK(cudaSetDevice(s->device));
+    FcCtrl h;
+    fc_status st = check_latched(s, &h);
+    if (st != FC_OK) return st;
+    if (h.pushed == 0) return fail(FC_ERR_NOT_READY, "no trial has been accepted");
+    float* dst = out;
+    float* tmp = nullptr;
+    if (!out_on_device) {
+        CK(cudaMalloc(&tmp, need * sizeof(float)));
+        dst = tmp;
+    }
+    if (s->cfg.mode == FC_MODE_STREAM) {
+        PairArgs pa = pair_args(s, true, 0);
+        LAUNCH(FC_K_OTHER, launch_bins_from_acc(pa, mi, dst, s->stream));
+    } else {
+        PairArgs pa = pair_args(s, false, 0);
+        LAUNCH(FC_K_OTHER, launch_bins_window(pa, mi, dst, s->stream));
+    }
+    if (!out_on_device) {
+        cudaError_t e = cudaMemcpyAsync(out, dst, need * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        cudaFree(tmp);
+        if (e != cudaSuccess) return fail(FC_ERR_CUDA, "per-bin copy: %s", cudaGetErrorString(e));
+    }
+    return FC_OK;
+}
+
+fc_status fc_get_xcor_lags(fc_session* s, int32_t* out, size_t out_len, int out_on_device) {
+    if (!s || !out) return fail(FC_ERR_INVALID_ARG, "NULL session or output");
+    if (!(s->time_mask & FC_XCOR)) return fail(FC_ERR_INVALID_ARG, "XCOR is not in the session");
+    if (out_len < (size_t)s->P) return fail(FC_ERR_INVALID_ARG, "out_len too small");
+    CK(cudaSetDevice(s->device));
+    FcCtrl h;
+    fc_status st = check_latched(s, &h);
+    if (st != FC_OK) return st;
+    if (h.pushed == 0) return fail(FC_ERR_NOT_READY, "no trial has been accepted");
+    CK(cudaMemcpyAsync(out, s->xcor_lag, s->P * sizeof(int32_t),
+                       out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return FC_OK;
+}
+
+fc_status fc_set_metric_mask(fc_session* s, uint32_t metric_mask) {
+    if (!s) return fail(FC_ERR_INVALID_ARG, "NULL session");
+    if (metric_mask == 0 || (metric_mask & ~(uint32_t)FC_ALL_METRICS))
+        return fail(FC_ERR_INVALID_ARG, "bad metric mask 0x%x", metric_mask);
+    if ((metric_mask & (FC_COR | FC_XCOR)) & ~s->time_mask)
+        return fail(FC_ERR_INVALID_ARG, "COR/XCOR can only be kept, not added after creation");
+    CK(cudaSetDevice(s->device));
+    const uint32_t added = metric_mask & ~s->mask & FC_SPECTRAL_METRICS;
+    s->mask = metric_mask;
+    if (added && s->enqueued > 0) {
+        // recompute the spectral networks from the shared sums (no trial is reprocessed)
+        if (s->cfg.mode == FC_MODE_STREAM) {
+            PairArgs pa = pair_args(s, true, 0);
+            pa.finalize = 1;
+            pa.update = 0;
+            LAUNCH(FC_K_STREAM, launch_stream_update(pa, s->stream));
+            if (pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
+        } else {
+            PairArgs pa = pair_args(s, false, 0);
+            LAUNCH(FC_K_WINDOW, launch_window_sums(pa, s->stream));
+            if (pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
+        }
+    }
+    return FC_OK;
+}
+
+fc_status fc_session_info(fc_session* s, fc_info* info) {
+    if (!s || !info) return fail(FC_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaSetDevice(s->device));
+    FcCtrl h;
+    fc_status st = read_ctrl(s, &h);
+    if (st != FC_OK) return st;
+    memset(info, 0, sizeof *info);
+    info->n_nodes = s->n;
+    info->n_samples = s->N;
+    info->n_bins = s->B;
+    info->first_bin = s->first_bin;
+    info->nfft = s->nfft;
+    info->window = s->W;
+    info->k_used = (int)((s->W > 0 && h.pushed > s->W) ? s->W : h.pushed);
+    info->pushes = h.pushed;
+    info->rejected = h.rejected;
+    info->pairs = s->P;
+    info->device_bytes = s->device_bytes;
+    info->metric_mask = s->mask;
+    info->mode = s->cfg.mode;
+    info->precision = s->cfg.precision;
+    if (h.bad_latched) return check_latched(s, &h);
+    return FC_OK;
+}
+
+fc_status fc_set_profiling(fc_session* s, int enable) {
+    if (!s) return fail(FC_ERR_INVALID_ARG, "NULL session");
+    s->profiling = enable != 0;
+    return FC_OK;
+}
+
+fc_status fc_kernel_times(fc_session* s, fc_kernel_time* out, int reset) {
+    if (!s || !out) return fail(FC_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaSetDevice(s->device));
+    CK(cudaStreamSynchronize(s->stream));
+    drain_timings(s);
+    for (int k = 0; k < FC_K_COUNT; ++k) out[k] = s->ktime[k];
+    if (reset)
+        for (int k = 0; k < FC_K_COUNT; ++k) s->ktime[k] = fc_kernel_time{0, 0.0};
+    return FC_OK;
+}
+
+long long fc_launch_count(const fc_session* s) { return s ? s->launches : 0; }
+
+void* fc_session_stream(const fc_session* s) { return s ? (void*)s->stream : nullptr; }
+
+fc_status fc_debug_get_spectra(fc_session* s, int age, float* out, size_t out_len) {
+    if (!s || !out) return fail(FC_ERR_INVALID_ARG, "NULL argument");
+    const size_t need = (size_t)2 * s->B * s->n;
+    if (out_len < need) return fail(FC_ERR_INVALID_ARG, "out_len too small");
+    CK(cudaSetDevice(s->device));
+    FcCtrl h;
+    fc_status st = read_ctrl(s, &h);
+    if (st != FC_OK) return st;
+    const long long kept = s->W > 0 ? std::min<long long>(h.pushed, s->W) : std::min<long long>(h.pushed, 1);
+    if (age < 0 || age >= kept) return fail(FC_ERR_INVALID_ARG, "no stored trial of age %d", age);
+    const long long g = h.pushed - 1 - age;
+    CK(cudaMemcpy(out, s->ring + (size_t)(g % s->slots) * s->B * s->n, need * sizeof(float), cudaMemcpyDeviceToHost));
+    return FC_OK;
+}
+
+fc_status fc_debug_get_scale(fc_session* s, float* scale) {
+    if (!s || !scale) return fail(FC_ERR_INVALID_ARG, "NULL argument");
+    FcCtrl h;
+    fc_status st = read_ctrl(s, &h);
+    if (st != FC_OK) return st;
+    *scale = h.scale == 0.f ? 1.f : h.scale;
+    return FC_OK;
+}
+
+fc_status fc_debug_get_accumulators(fc_session* s, fc_acc_field field, double* out, size_t out_len) {
+    if (!s || !out) return fail(FC_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaSetDevice(s->device));
+    CK(cudaStreamSynchronize(s->stream));
+    size_t need;
+    if (field == FC_ACC_PSD) need = (size_t)s->B * s->n;
+    else if (field == FC_ACC_COR || field == FC_ACC_XCOR) need = (size_t)s->P;
+    else if (field >= FC_ACC_CSD_RE && field <= FC_ACC_SIGN) need = (size_t)s->B * s->P;
+    else return fail(FC_ERR_INVALID_ARG, "bad field");
+    if (out_len < need) return fail(FC_ERR_INVALID_ARG, "out_len too small");
+    if (field == FC_ACC_PSD) {
+        CK(cudaMemcpy(out, s->psd, need * sizeof(double), cudaMemcpyDeviceToHost));
+        return FC_OK;
+    }
+    const float* planes = nullptr;
+    if (field == FC_ACC_COR) planes = s->cor_acc;
+    if (field == FC_ACC_XCOR) planes = s->xcor_acc;
+    if ((field == FC_ACC_COR || field == FC_ACC_XCOR) && !planes)
+        return fail(FC_ERR_INVALID_ARG, "metric not in the session");
+    if (field <= FC_ACC_SIGN && !s->acc) return fail(FC_ERR_INVALID_ARG, "no accumulators in full mode");
+    double* tmp = nullptr;
+    CK(cudaMalloc(&tmp, need * sizeof(double)));
+    cudaError_t e;
+    if (planes)
+        e = launch_df_planes_to_double(planes, s->P, tmp, s->stream);
+    else
+        e = launch_acc_field(s->acc, s->tile_a, s->tile_b, s->ntp, s->B, s->n, (int)field, tmp, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, need * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(FC_ERR_CUDA, "accumulator read: %s", cudaGetErrorString(e));
+    return FC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,216 @@
+// fc_internal.h - session state, device layout and kernel launchers (library-internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fc.h"
+
+// ---------------------------------------------------------------------------------
+// Device layout
+//
+// Nodes are grouped in tiles of FC_T = 32. The pair space is covered by the upper
+// triangle of tile pairs (a <= b), enumerated row by row; a diagonal tile pair (a == a)
+// holds only its pairs with i < j.
+//
+// Spectral accumulators, one block per (tile pair, bin), tile-pair major, bins inside:
+//   block = 13 planes of FC_T*FC_T 32-bit words, pair (li, lj) at word li*32 + lj:
+//     planes 2k, 2k+1 = hi, lo floats of double-float field k:
+//       k = 0 CSD re, 1 CSD im (= sum Im, also used by WPLI/DSWPLI), 2 phasor re,
+//           3 phasor im, 4 sum |Im|, 5 sum Im^2
+//     plane 12      = int32 sign count
+//   53,248 bytes per (tile pair, bin): 52 B per pair-bin of state.
+// Ring of spectra: slots x [n_bins][n_nodes] float2 (re, im), a slot per stored trial.
+// Per-node: psd [n_bins][n_nodes] double; inv_sqrt_psd [n_bins][n_nodes] float.
+// Networks: [FC_NMETRIC][P] float, packed upper (pair (i,j), i<j).
+// Time-domain accumulators (COR, XCOR): double-float [2][P] (hi plane, lo plane).
+// ---------------------------------------------------------------------------------
+
+#define FC_T 32
+#define FC_TT (FC_T * FC_T)
+#define FC_NFIELD 6
+#define FC_BLOCK_WORDS (13 * FC_TT)
+#define FC_NMETRIC 9
+
+// metric bit index (log2 of the FC_* bit)
+enum { MI_COR = 0, MI_XCOR, MI_COH, MI_IMAGCOHY, MI_PLV, MI_PLI, MI_USPLI, MI_WPLI, MI_DSWPLI };
+
+// Device-resident control block: the state of the window lives on the device so that a
+// push never waits for the host (rejections are decided on the device).
+struct FcCtrl {
+    long long pushed;      // accepted trials
+    long long rejected;    // rejected trials
+    int bad;               // the push in flight held a non-finite value
+    int bad_latched;       // a rejection happened since the host last looked
+    unsigned int max_bits; // calibration: max |re|,|im| of the first spectra (float bits)
+    float scale;           // power-of-two prescale of all spectra (0 = not calibrated)
+};
+
+struct FcPendingTiming {
+    int kernel;
+    cudaEvent_t start, stop;
+};
+
+struct fc_session {
+    // settings
+    int n, N, B, first_bin, nfft, W, slots;
+    double fs;
+    fc_band band;
+    fc_taper taper;
+    uint32_t mask;      // metrics finalized each push
+    uint32_t time_mask; // COR/XCOR state allocated at creation
+    fc_config cfg;
+    bool own_stream;
+    cudaStream_t stream;
+    int device;
+
+    // derived sizes
+    int nt;             // node tiles
+    int ntp;            // tile pairs
+    long long P;        // pairs
+    int groups;         // bin groups for the full-window kernel
+    int group_bins;     // bins per group
+    int stream_groups;  // bin groups for the streaming kernel
+    int stream_group_bins;
+    int xcor_L;         // XCOR transform length (power of two >= 2N - 1)
+
+    // host mirror of the enqueued push count (scheduling only; the device count rules)
+    long long enqueued;
+    long long since_resum;
+    bool calibrated;        // the device prescale is known to be set
+
+    float* dense_scratch;   // n x n staging for dense host outputs
+    size_t dense_scratch_len;
+
+    // device buffers
+    FcCtrl* ctrl;
+    float* x_stage;         // [stage_trials][n][N]
+    int stage_trials;
+    float2* twiddle;        // [N][B] taper-folded DFT factors
+    float2* ring;           // [slots][B][n]
+    double* psd;            // [B][n]
+    float* inv_psd;         // [B][n]
+    float* acc;             // [ntp][B][13][1024] (stream mode)
+    unsigned short* tile_a; // [ntp]
+    unsigned short* tile_b; // [ntp]
+    float* net;             // [FC_NMETRIC][P]
+    float* partial;         // [groups][7][P] band partial sums (when groups > 1)
+    float* zring;           // COR: [slots][n][N] normalized trials
+    float* cor_acc;         // COR: [2][P] double-float
+    float* xcor_vals;       // XCOR: [slots][P] per-trial values
+    int* xcor_lag;          // XCOR: [P] lags of the newest trial
+    float* xcor_acc;        // XCOR: [2][P]
+    float2* xcor_tw;        // XCOR FFT twiddles [L/2]
+    float2* xcor_spec;      // XCOR spectra of the trials in flight [count][n][L/2+1]
+    float* xcor_energy;     // XCOR [count][n]
+    int xcor_spec_trials;
+    size_t device_bytes;
+
+    // measurement
+    long long launches;
+    bool profiling;
+    std::vector<FcPendingTiming> pending;
+    fc_kernel_time ktime[FC_K_COUNT];
+    std::vector<void*> allocations;
+};
+
+// ---------------------------------------------------------------------------------
+// Launchers (each returns the cudaError_t of the launch)
+
+struct SpectrumArgs {
+    const float* x;        // [count][n][N]
+    int count;             // trials in x
+    int write_from;        // first trial of x written to the ring (earlier ones are skipped)
+    const float2* twiddle; // [N][B]
+    float2* ring;
+    int slots, n, N, B;
+    FcCtrl* ctrl;
+};
+cudaError_t launch_validate(const float* x, long long count, FcCtrl* ctrl, cudaStream_t st);
+cudaError_t launch_spectrum(const SpectrumArgs& a, cudaStream_t st);
+cudaError_t launch_calibrate(const SpectrumArgs& a, cudaStream_t st, int phase);
+
+struct NodeArgs {
+    const float2* ring;
+    double* psd;
+    float* inv_psd;
+    int slots, n, B, W;
+    int mode;   // 0 = add newest / subtract leaving, 1 = recompute from the window
+    FcCtrl* ctrl;
+    int count;  // trials pushed by this call (mode 1: the window ends at pushed + count)
+};
+cudaError_t launch_node(const NodeArgs& a, cudaStream_t st);
+
+struct PairArgs {
+    const float2* ring;
+    const float* inv_psd;
+    float* acc;
+    const unsigned short* tile_a;
+    const unsigned short* tile_b;
+    float* net;        // [FC_NMETRIC][P]
+    float* partial;    // [groups][7][P]
+    int slots, n, B, W, ntp;
+    long long P;
+    int groups, group_bins;
+    uint32_t mask;     // metrics to finalize
+    int finalize;      // write networks / partials
+    int update;        // stream kernel: 1 = add/subtract the trials, 0 = finalize only
+    int write_acc;     // window kernel: store accumulators (re-sum)
+    int count;         // trials pushed by this call (window end = pushed + count)
+    const FcCtrl* ctrl;
+};
+cudaError_t launch_stream_update(const PairArgs& a, cudaStream_t st);
+cudaError_t launch_window_sums(const PairArgs& a, cudaStream_t st);
+cudaError_t launch_band_reduce(const PairArgs& a, cudaStream_t st);
+cudaError_t launch_bins_from_acc(const PairArgs& a, int metric_index, float* out, cudaStream_t st);
+cudaError_t launch_bins_window(const PairArgs& a, int metric_index, float* out, cudaStream_t st);
+
+struct CommitArgs {
+    FcCtrl* ctrl;
+    int count;
+};
+cudaError_t launch_commit(const CommitArgs& a, cudaStream_t st);
+
+// time-domain metrics
+struct CorArgs {
+    const float* x;     // [count][n][N] raw trials
+    int count, write_from;
+    float* zring;       // [slots][n][N]
+    float* cor_acc;     // [2][P]
+    float* net;         // network plane for COR
+    int slots, n, N, W;
+    long long P;
+    int mode;           // 0 = stream add/subtract, 1 = full recompute of the window
+    int finalize;
+    const FcCtrl* ctrl;
+};
+cudaError_t launch_cor_normalize(const CorArgs& a, cudaStream_t st);
+cudaError_t launch_cor_update(const CorArgs& a, cudaStream_t st);
+
+struct XcorArgs {
+    const float* x;     // [count][n][N]
+    int count, write_from;
+    int n, N, L, W, slots;
+    long long P;
+    const float2* tw;   // [L/2] twiddles e^{-2 pi i k / L}
+    float2* spec;       // [count][n][L/2+1]
+    float* energy;      // [count][n]
+    float* vals;        // [slots][P]
+    int* lag;           // [P]
+    float* acc;         // [2][P]
+    float* net;
+    int mode, finalize;
+    const FcCtrl* ctrl;
+};
+cudaError_t launch_xcor_spectra(const XcorArgs& a, cudaStream_t st);
+cudaError_t launch_xcor_pairs(const XcorArgs& a, cudaStream_t st);
+cudaError_t launch_xcor_update(const XcorArgs& a, cudaStream_t st);
+
+cudaError_t launch_expand_dense(const float* packed, float* dense, int n, int antisym,
+                                cudaStream_t st);
+cudaError_t launch_acc_field(const float* acc, const unsigned short* ta, const unsigned short* tb,
+                             int ntp, int B, int n, int field, double* out, cudaStream_t st);
+cudaError_t launch_df_planes_to_double(const float* acc2, long long P, double* out, cudaStream_t st);

@@ -1,0 +1,257 @@
+// k_xcor.cu - cross-correlation (XCOR), Supplementary Information 1 (Time Domain) and
+// Methods 2.4: "an FFT convolution, which consists of the creation of the signal spectra,
+// multiplication of these spectra, and the transformation of the product back to the time
+// domain. Subsequently, the highest correlation value and its index are returned."
+//
+// Per trial k and node i: x~_i = x_i - mean, energy E_i = sum x~_i^2, and the length-L
+// real spectrum Z_i of x~_i zero-padded to L (power of two >= 2N - 1, so the circular
+// correlation equals the linear one for |tau| <= N - 1). Per pair (i, j):
+//   R(tau) = irfft(Z_i Z_j*)[tau mod L] = sum_t x~_i(t + tau) x~_j(t),
+//   XCOR_k(i, j) = max_{|tau| <= N-1} R(tau) / sqrt(E_i E_j)   (0 if E_i E_j = 0),
+// ties to the smallest |tau|, then the negative tau. The network is the mean over trials.
+//
+// Transforms are hand-written radix-2 FFTs in shared memory, one warp per signal: a real
+// length-L transform is done as a complex length-M = L/2 transform plus the standard
+// even/odd split (forward) or merge (inverse). Twiddles come from a host-built FP64 table
+// rounded to FP32 (tw[k] = exp(-2 pi i k / L), k < L/2).
+#include "df32.cuh"
+#include "fc_internal.h"
+
+namespace {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// Pair (i, j), i < j, of packed index p (row r starts at r*n - r(r+1)/2).
+__device__ __forceinline__ void unpack_pair(long long p, int n, int& i, int& j) {
+    const double b = 2.0 * n - 1.0;
+    int r = (int)floor((b - sqrt(b * b - 8.0 * (double)p)) * 0.5);
+    if (r < 0) r = 0;
+    if (r > n - 2) r = n - 2;
+    while (r > 0 && (long long)r * n - (long long)r * (r + 1) / 2 > p) --r;
+    while (r < n - 2 && (long long)(r + 1) * n - (long long)(r + 1) * (r + 2) / 2 <= p) ++r;
+    i = r;
+    j = (int)(p - ((long long)r * n - (long long)r * (r + 1) / 2)) + r + 1;
+}
+
+__device__ __forceinline__ int bitrev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
+
+// In-place radix-2 decimation-in-time FFT of buf[0..M) (already in bit-reversed order),
+// executed by one warp. sign = -1: forward (exp(-i...)), +1: inverse (no 1/M scaling).
+__device__ void warp_fft(float2* buf, int M, const float2* __restrict__ tw, int L, int sign) {
+    const int lane = threadIdx.x & 31;
+    for (int s = 1; s < M; s <<= 1) {
+        const int step = L / (2 * s);
+        for (int b = lane; b < M / 2; b += 32) {
+            const int j = b & (s - 1);
+            const int i0 = ((b - j) << 1) + j, i1 = i0 + s;
+            float2 w = tw[j * step];
+            if (sign > 0) w.y = -w.y;
+            const float2 u = buf[i0], v = cmul(buf[i1], w);
+            buf[i0] = cadd(u, v);
+            buf[i1] = csub(u, v);
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ node spectra
+// One warp per (trial, node). Shared memory: M float2 per warp.
+__global__ void k_xcor_spectra(XcorArgs a) {
+    const FcCtrl* c = a.ctrl;
+    if (c->bad) return;
+    extern __shared__ float2 smem[];
+    const int M = a.L / 2;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* buf = smem + (size_t)wib * M;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+    const int ntr = a.count - a.write_from;
+    if (warp >= ntr * a.n) return;
+    const int tr = a.write_from + warp / a.n, node = warp % a.n;
+    const float* x = a.x + ((size_t)tr * a.n + node) * a.N;
+    double s = 0.0;
+    for (int t = lane; t < a.N; t += 32) s += (double)x[t];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double mean = s / a.N;
+    double q = 0.0;
+    for (int t = lane; t < a.N; t += 32) {
+        const double d = (double)x[t] - mean;
+        q += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    const float fmean = (float)mean;
+    int bits = 0;
+    while ((1 << bits) < M) ++bits;
+    for (int m = lane; m < M; m += 32) {
+        const int t0 = 2 * m, t1 = 2 * m + 1;
+        const float v0 = t0 < a.N ? __fsub_rn(x[t0], fmean) : 0.f;
+        const float v1 = t1 < a.N ? __fsub_rn(x[t1], fmean) : 0.f;
+        buf[bitrev(m, bits)] = make_float2(v0, v1);
+    }
+    __syncwarp();
+    warp_fft(buf, M, a.tw, a.L, -1);
+    const long long g = c->pushed + tr;
+    const int slot = (int)(g % a.slots);
+    float2* out = a.spec + ((size_t)slot * a.n + node) * (M + 1);
+    for (int k = lane; k <= M; k += 32) {
+        const float2 zk = buf[k == M ? 0 : k];
+        const float2 zc = cconj(buf[k == 0 ? 0 : M - k]);
+        const float2 e = make_float2(0.5f * __fadd_rn(zk.x, zc.x), 0.5f * __fadd_rn(zk.y, zc.y));
+        const float2 d = csub(zk, zc);  // 2i O[k]
+        const float2 o = make_float2(0.5f * d.y, -0.5f * d.x);  // d / (2i)
+        const float2 w = (k < M) ? a.tw[k] : make_float2(-1.f, 0.f);
+        out[k] = cadd(e, cmul(w, o));
+    }
+    if (lane == 0) a.energy[(size_t)slot * a.n + node] = (float)q;
+}
+
+// ------------------------------------------------------------------ pair correlations
+// One warp per (pair, trial). Trials: the window (full mode) or the newest (stream mode).
+__device__ __forceinline__ bool better(float v1, int t1, float v2, int t2) {
+    if (v1 != v2) return v1 > v2;
+    const int a1 = abs(t1), a2 = abs(t2);
+    if (a1 != a2) return a1 < a2;
+    return t1 < t2;
+}
+
+__global__ void k_xcor_pairs(XcorArgs a, long long n_items, long long first_trial, int n_trials) {
+    const FcCtrl* c = a.ctrl;
+    if (c->bad) return;
+    extern __shared__ float2 smem[];
+    const int M = a.L / 2;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* buf = smem + (size_t)wib * M;
+    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (item >= n_items) return;
+    const long long p = item / n_trials;
+    const long long trial = c->pushed + first_trial + item % n_trials;
+    if (trial < 0) return;  // window not yet full
+    int i, j;
+    unpack_pair(p, a.n, i, j);
+    {
+        const int slot = (int)(trial % a.slots);
+        const float2* Zi = a.spec + ((size_t)slot * a.n + i) * (M + 1);
+        const float2* Zj = a.spec + ((size_t)slot * a.n + j) * (M + 1);
+        int bits = 0;
+        while ((1 << bits) < M) ++bits;
+        // Y[k] = E[k] + i O[k], E = (P[k] + conj P[M-k]) / 2, O = (P[k] - conj P[M-k]) e^{+2 pi i k/L} / 2
+        for (int k = lane; k < M; k += 32) {
+            const float2 pk = cmul(Zi[k], cconj(Zj[k]));
+            const float2 pm = cconj(cmul(Zi[M - k], cconj(Zj[M - k])));
+            const float2 e = make_float2(0.5f * __fadd_rn(pk.x, pm.x), 0.5f * __fadd_rn(pk.y, pm.y));
+            const float2 dd = csub(pk, pm);
+            float2 w = a.tw[k];
+            w.y = -w.y;  // e^{+2 pi i k / L}
+            const float2 o = cmul(make_float2(0.5f * dd.x, 0.5f * dd.y), w);
+            buf[bitrev(k, bits)] = make_float2(__fsub_rn(e.x, o.y), __fadd_rn(e.y, o.x));  // e + i o
+        }
+        __syncwarp();
+        warp_fft(buf, M, a.tw, a.L, +1);
+        // r[2m] = Re y[m] / M, r[2m+1] = Im y[m] / M; scan lags |tau| <= N-1
+        float best = -INFINITY;
+        int best_tau = 0;
+        const float invM = 1.0f / (float)M;
+        for (int tau = -(a.N - 1) + lane; tau <= a.N - 1; tau += 32) {
+            const int idx = tau >= 0 ? tau : a.L + tau;
+            const float2 y = buf[idx >> 1];
+            const float r = __fmul_rn((idx & 1) ? y.y : y.x, invM);
+            if (better(r, tau, best, best_tau)) {
+                best = r;
+                best_tau = tau;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int ot = __shfl_xor_sync(0xffffffffu, best_tau, o);
+            if (better(ov, ot, best, best_tau)) {
+                best = ov;
+                best_tau = ot;
+            }
+        }
+        if (lane == 0) {
+            const float ei = a.energy[(size_t)slot * a.n + i], ej = a.energy[(size_t)slot * a.n + j];
+            const float den = __fmul_rn(sqrtf(ei), sqrtf(ej));
+            float v = 0.f;
+            int lag = 0;
+            if (den > 0.f) {
+                v = __fdiv_rn(best, den);
+                lag = best_tau;
+            }
+            a.vals[(size_t)slot * a.P + p] = v;
+            if (trial == c->pushed + a.count - 1) a.lag[p] = lag;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ network update
+__global__ void k_xcor_update(XcorArgs a) {
+    const FcCtrl* c = a.ctrl;
+    if (c->bad) return;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.P) return;
+    const long long end = c->pushed + a.count;
+    const long long start = (a.W > 0 && end > a.W) ? end - a.W : 0;
+    const int K = (int)(end - start);
+    df32 acc;
+    if (a.mode == 0) {
+        acc = df_make(a.acc[p], a.acc[a.P + p]);
+        const long long tn = end - 1;
+        acc = df_add_f(acc, a.vals[(size_t)(tn % a.slots) * a.P + p]);
+        if (a.W > 0 && tn >= a.W) acc = df_add_f(acc, -a.vals[(size_t)((tn - a.W) % a.slots) * a.P + p]);
+    } else {
+        acc = df_make(0.f, 0.f);
+        for (long long k = start; k < end; ++k) acc = df_add_f(acc, a.vals[(size_t)(k % a.slots) * a.P + p]);
+    }
+    a.acc[p] = acc.hi;
+    a.acc[a.P + p] = acc.lo;
+    if (a.finalize) a.net[p] = __fmul_rn(df_to_f(acc), 1.0f / (float)K);
+}
+
+}  // namespace
+
+cudaError_t launch_xcor_spectra(const XcorArgs& a, cudaStream_t st) {
+    const long long warps = (long long)(a.count - a.write_from) * a.n;
+    if (warps <= 0) return cudaSuccess;
+    const int wpb = 4;
+    const size_t sm = (size_t)wpb * (a.L / 2) * sizeof(float2);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_xcor_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    k_xcor_spectra<<<(unsigned)((warps + wpb - 1) / wpb), wpb * 32, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+// mode 1: every trial of the window; mode 0: the newest trial only.
+cudaError_t launch_xcor_pairs(const XcorArgs& a, cudaStream_t st) {
+    // trials relative to ctrl->pushed: newest = count - 1; window = [count - K, count)
+    int n_trials;
+    long long first;
+    if (a.mode == 0) {
+        n_trials = 1;
+        first = a.count - 1;
+    } else {
+        n_trials = a.W;  // full mode always has W >= 1; the kernel clamps below
+        first = a.count - a.W;
+    }
+    const long long items = a.P * n_trials;
+    const int wpb = 4;
+    const size_t sm = (size_t)wpb * (a.L / 2) * sizeof(float2);
+    const int M = a.L / 2;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_xcor_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    (void)M;
+    k_xcor_pairs<<<(unsigned)((items + wpb - 1) / wpb), wpb * 32, sm, st>>>(a, items, first, n_trials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xcor_update(const XcorArgs& a, cudaStream_t st) {
+    k_xcor_update<<<(unsigned)((a.P + 255) / 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}

@@ -41,6 +41,10 @@ WORKLOADS = {
     "source_stream": dict(n=2000, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=50,
                           desc="source space streaming push: 2000 nodes, W=50 trials x 500 samples, "
                                "40 bins (4-44 Hz), 7 spectral metrics"),
+    # profiling case: same kernel shapes, 1.1 GB of state (> L2) so that an ncu capture stays small
+    "profile_stream": dict(n=1024, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=20,
+                           desc="profiling case: 1024 nodes, W=20 trials x 500 samples, 40 bins, "
+                                "7 spectral metrics (1.1 GB of accumulators)"),
 }
 METRIC = "pair-bin updates/s per pushed trial"
 UNIT = "pair-bin updates/s"

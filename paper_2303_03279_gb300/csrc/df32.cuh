@@ -91,3 +91,75 @@ __device__ __forceinline__ df32 df_sqr_f(float a) {
 }
 
 __device__ __forceinline__ float df_to_f(df32 x) { return __fadd_rn(x.hi, x.lo); }
+
+// ---------------------------------------------------------------------------------
+// Packed forms for two independent lanes (x, y), using the FP32x2 instructions of
+// sm_100+ (one issue slot for two correctly rounded operations). Each lane computes
+// exactly the same bits as the scalar form.
+
+// The operations are issued as inline PTX (add/mul/fma.rn.f32x2). The error-free
+// transformations below rely on every operation being exactly one correctly rounded IEEE
+// step. Measured on sm_103a: a packed multiply whose result feeds a packed add may be
+// fused into one FMA by the backend, which drops the product's rounding; so a packed
+// add/sub never takes a raw packed product as an operand in this library (such sums are
+// done with scalar __fadd_rn, which is never contracted). Products as FMA addends, and
+// sums of FMA/add results, are safe.
+__device__ __forceinline__ unsigned long long pack_f2(float2 v) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 unpack_f2(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack_f2(a)), "l"(pack_f2(b)));
+    return unpack_f2(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack_f2(a)), "l"(pack_f2(b)));
+    return unpack_f2(d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pack_f2(a)), "l"(pack_f2(b)), "l"(pack_f2(c)));
+    return unpack_f2(d);
+}
+// a - b as fma(b, -1, a): one rounding, identical to a scalar subtraction
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return fma2(b, make_float2(-1.f, -1.f), a); }
+
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+    s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    const float2 aa = sub2(s, bb);
+    e = add2(sub2(a, aa), sub2(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2& s, float2& e) {
+    s = add2(a, b);
+    e = sub2(b, sub2(s, a));
+}
+
+// Running-sum update (hi, lo) += y1 + y2 for two float terms: two TwoSums into the
+// leading part, their errors folded into lo, one renormalization (17 ops for 2 lanes).
+__device__ __forceinline__ void acc2_ff(float2& hi, float2& lo, float2 y1, float2 y2) {
+    float2 s1, e1, s2, e2;
+    two_sum2(hi, y1, s1, e1);
+    two_sum2(s1, y2, s2, e2);
+    const float2 l = add2(add2(lo, e1), e2);
+    fast_two_sum2(s2, l, hi, lo);
+}
+
+// Running-sum update (hi, lo) += (y1h + y1l) + (y2h + y2l) for two double-word terms.
+__device__ __forceinline__ void acc2_dd(float2& hi, float2& lo, float2 y1h, float2 y1l, float2 y2h, float2 y2l) {
+    float2 s1, e1, s2, e2;
+    two_sum2(hi, y1h, s1, e1);
+    two_sum2(s1, y2h, s2, e2);
+    const float2 l = add2(add2(add2(lo, e1), add2(e2, y1l)), y2l);
+    fast_two_sum2(s2, l, hi, lo);
+}

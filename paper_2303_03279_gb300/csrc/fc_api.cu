@@ -166,6 +166,7 @@ PairArgs pair_args(fc_session* s, bool stream_kernel, int count) {
     a.update = 1;
     a.write_acc = 0;
     a.count = count;
+    a.grid_ctas = 2 * s->num_sms;
     a.ctrl = s->ctrl;
     return a;
 }
@@ -333,6 +334,8 @@ fc_status read_ctrl(fc_session* s, FcCtrl* h) {
 fc_status check_latched(fc_session* s, FcCtrl* h) {
     fc_status st = read_ctrl(s, h);
     if (st != FC_OK) return st;
+    if (h->timeout)
+        return fail(FC_ERR_TIMEOUT, "a bounded device-side wait ran out; the session state is unreliable");
     if (h->bad_latched) {
         CK(cudaMemsetAsync(&s->ctrl->bad_latched, 0, sizeof(int), s->stream));
         CK(cudaStreamSynchronize(s->stream));
@@ -416,6 +419,9 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
     s->P = (long long)n_nodes * (n_nodes - 1) / 2;
     s->slots = cfg.mode == FC_MODE_FULL ? window : (window > 0 ? window + 1 : 1);
     cudaGetDevice(&s->device);
+    if (cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
+        s->num_sms < 1)
+        s->num_sms = 152;
 
     auto cleanup = [&](fc_status st) {
         if (s->stream) cudaStreamSynchronize(s->stream);

@@ -47,6 +47,8 @@ struct FcCtrl {
     int bad_latched;       // a rejection happened since the host last looked
     unsigned int max_bits; // calibration: max |re|,|im| of the first spectra (float bits)
     float scale;           // power-of-two prescale of all spectra (0 = not calibrated)
+    int timeout;           // a bounded device-side wait ran out
+    int pad_;
 };
 
 struct FcPendingTiming {
@@ -66,6 +68,7 @@ struct fc_session {
     bool own_stream;
     cudaStream_t stream;
     int device;
+    int num_sms;
 
     // derived sizes
     int nt;             // node tiles
@@ -160,6 +163,7 @@ struct PairArgs {
     int update;        // stream kernel: 1 = add/subtract the trials, 0 = finalize only
     int write_acc;     // window kernel: store accumulators (re-sum)
     int count;         // trials pushed by this call (window end = pushed + count)
+    int grid_ctas;     // persistent grid size of the streaming kernel
     const FcCtrl* ctrl;
 };
 cudaError_t launch_stream_update(const PairArgs& a, cudaStream_t st);

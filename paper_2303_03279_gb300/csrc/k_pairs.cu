@@ -4,10 +4,7 @@
 // kept ("running average"); the metric is computed from the sums for one half of the
 // edge weights (undirected). Supplementary Information 1 defines the metrics.
 //
-// k_stream  (streaming update): for each (pair, bin), add the terms of the newest trial
-//           and subtract those of the trial leaving the window, on resident double-float
-//           accumulators (52 bytes of state per pair-bin), then finalize the metrics and
-//           their band average in the same pass. HBM-bound: 104 B moved per pair-bin.
+// (the streaming add/subtract update lives in k_stream.cu)
 // k_window  (full-window sums): the same sums over all K trials of the window from the
 //           stored spectra, in registers, with the finalize in the epilogue; optionally
 //           stores the accumulators (re-sum that resets the drift of the streaming state).
@@ -15,95 +12,11 @@
 #include "df32.cuh"
 #include "fc_internal.h"
 #include "terms.cuh"
+#include "pair_common.cuh"
 
 namespace {
 
-__device__ __forceinline__ long long packed_index(int i, int j, int n) {
-    return (long long)i * n - (long long)i * (i + 1) / 2 + (j - i - 1);
-}
-
-__device__ __forceinline__ float get4(const float4& v, int q) {
-    return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
-}
-__device__ __forceinline__ void set4(float4& v, int q, float x) {
-    if (q == 0) v.x = x; else if (q == 1) v.y = x; else if (q == 2) v.z = x; else v.w = x;
-}
-__device__ __forceinline__ int geti4(const int4& v, int q) {
-    return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
-}
-__device__ __forceinline__ void seti4(int4& v, int q, int x) {
-    if (q == 0) v.x = x; else if (q == 1) v.y = x; else if (q == 2) v.z = x; else v.w = x;
-}
-
-// Window facts read from the device control block.
-struct WinFacts {
-    long long end;     // trials accepted after this call (exclusive end of the window)
-    long long start;   // first trial of the window
-    int K;             // trials in the window
-};
-__device__ __forceinline__ WinFacts window_facts(const FcCtrl* c, int W, int count) {
-    WinFacts w;
-    w.end = c->pushed + count;
-    w.start = (W > 0 && w.end > W) ? w.end - W : 0;
-    w.K = (int)(w.end - w.start);
-    return w;
-}
-
-// Per-bin metrics from the sums of one pair-bin (Supplementary Information 1).
-//   f[0..5]: CSD re, CSD im (= sum Im), phasor re, phasor im, sum |Im|, sum Im^2.
-//   out[0..6]: COH, IMAGCOHY, PLV, PLI, USPLI, WPLI, DSWPLI.
-// inv_i, inv_j = 1/sqrt(sum PSD); COHY = S_csd inv_i inv_j (the 1/K factors cancel).
-__device__ __forceinline__ void finalize_bin(const df32* f, int sign, float inv_i, float inv_j,
-                                             int K, float inv_K, float* out) {
-    const float cre = __fmul_rn(__fmul_rn(df_to_f(f[0]), inv_i), inv_j);
-    const float cim = __fmul_rn(__fmul_rn(df_to_f(f[1]), inv_i), inv_j);
-    out[0] = sqrtf(__fmaf_rn(cre, cre, __fmul_rn(cim, cim)));
-    out[1] = cim;
-    const float ure = df_to_f(f[2]), uim = df_to_f(f[3]);
-    out[2] = __fmul_rn(sqrtf(__fmaf_rn(ure, ure, __fmul_rn(uim, uim))), inv_K);
-    const float as = (float)abs(sign);
-    out[3] = __fdiv_rn(as, (float)K);
-    out[4] = (K >= 2) ? __fdiv_rn((float)((long long)sign * sign - K), (float)K * (float)(K - 1))
-                      : __int_as_float(0x7fc00000);
-    const float sabs = df_to_f(f[4]);
-    out[5] = (sabs > 0.f) ? __fdiv_rn(fabsf(df_to_f(f[1])), sabs) : 0.f;
-    const df32 num = df_add_df(df_sqr(f[1]), df_neg(f[5]));
-    const df32 den = df_add_df(df_sqr(f[4]), df_neg(f[5]));
-    const float dn = df_to_f(den);
-    out[6] = (dn != 0.f) ? __fdiv_rn(df_to_f(num), dn) : 0.f;
-}
-
-__device__ __forceinline__ void write_band(const PairArgs& a, int g, const float (*band)[4],
-                                           int gi, int gj0, unsigned vmask, int nbins_group) {
-    const float invB = 1.0f / (float)a.B;
-    for (int m = 0; m < 7; ++m) {
-        if (!(a.mask & (1u << (m + 2)))) continue;
-        if (a.groups == 1) {
-            float* dst = a.net + (size_t)(m + 2) * a.P;
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (vmask & (1u << q)) dst[packed_index(gi, gj0 + q, a.n)] = __fmul_rn(band[m][q], invB);
-        } else {
-            float* dst = a.partial + ((size_t)g * 7 + m) * a.P;
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (vmask & (1u << q)) dst[packed_index(gi, gj0 + q, a.n)] = band[m][q];
-        }
-    }
-    (void)nbins_group;
-}
-
-__device__ __forceinline__ unsigned pair_mask(int ta, int tb, int li, int lj0, int n) {
-    unsigned v = 0;
-    const int gi = ta * FC_T + li;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int gj = tb * FC_T + lj0 + q;
-        const bool ok = gi < n && gj < n && (ta != tb || lj0 + q > li);
-        v |= ok ? (1u << q) : 0u;
-    }
-    return v;
-}
+using namespace fcpair;
 
 // ------------------------------------------------------------------------------- node
 __global__ void k_node(NodeArgs a) {
@@ -134,124 +47,6 @@ __global__ void k_node(NodeArgs a) {
     a.inv_psd[e] = (s > 0.0) ? (float)(1.0 / sqrt(s)) : 0.f;
 }
 
-// ----------------------------------------------------------------------- stream update
-// CTA: one tile pair x one group of bins. Thread: row li, columns lj0..lj0+3 of the tile.
-__global__ void __launch_bounds__(256, 2) k_stream(PairArgs a) {
-    const FcCtrl* c = a.ctrl;
-    if (c->bad) return;
-    // t: the newest trial of the window after this call (count = 1: the trial being
-    // added; count = 0: finalize-only pass over the current sums)
-    const long long t = c->pushed + a.count - 1;
-    const bool upd = a.update != 0;
-    const int slot_new = upd ? (int)(t % a.slots) : 0;
-    const bool sub = upd && (a.W > 0) && (t >= a.W);
-    const int slot_old = sub ? (int)((t - a.W) % a.slots) : 0;
-    const int K = (a.W > 0 && t + 1 > a.W) ? a.W : (int)(t + 1);
-    if (K <= 0) return;
-    const float inv_K = 1.0f / (float)K;
-
-    const int tp = blockIdx.x;
-    const int g = blockIdx.y;
-    const int f0 = g * a.group_bins;
-    const int f1 = min(a.B, f0 + a.group_bins);
-    const int ta = a.tile_a[tp], tb = a.tile_b[tp];
-    const int tid = threadIdx.x;
-    const int li = tid >> 3, lj0 = (tid & 7) * 4;
-    const unsigned vmask = pair_mask(ta, tb, li, lj0, a.n);
-    const int gi = ta * FC_T + li, gj0 = tb * FC_T + lj0;
-
-    __shared__ float2 sx[4][FC_T];  // new row nodes, new col nodes, old row, old col
-    __shared__ float2 su[4][FC_T];
-    __shared__ float sinv[2][FC_T];
-
-    float band[7][4];
-#pragma unroll
-    for (int m = 0; m < 7; ++m)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) band[m][q] = 0.f;
-
-    const int w0 = li * FC_T + lj0;
-    for (int f = f0; f < f1; ++f) {
-        if (tid < 128) {
-            const int w = tid >> 5, l = tid & 31;
-            const int node = ((w & 1) ? tb : ta) * FC_T + l;
-            const bool old = w >= 2;
-            float2 X = make_float2(0.f, 0.f);
-            if (upd && node < a.n && (!old || sub))
-                X = a.ring[((size_t)(old ? slot_old : slot_new) * a.B + f) * a.n + node];
-            sx[w][l] = X;
-            su[w][l] = phasor_of(X);
-        } else if (tid < 192) {
-            const int w = (tid - 128) >> 5, l = tid & 31;
-            const int node = (w ? tb : ta) * FC_T + l;
-            sinv[w][l] = node < a.n ? a.inv_psd[(size_t)f * a.n + node] : 0.f;
-        }
-        __syncthreads();
-        if (vmask) {
-            float* blk = a.acc + ((size_t)tp * a.B + f) * FC_BLOCK_WORDS;
-            float4 hi[FC_NFIELD], lo[FC_NFIELD];
-#pragma unroll
-            for (int k = 0; k < FC_NFIELD; ++k) {
-                hi[k] = __ldcs(reinterpret_cast<const float4*>(blk + (2 * k) * FC_TT + w0));
-                lo[k] = __ldcs(reinterpret_cast<const float4*>(blk + (2 * k + 1) * FC_TT + w0));
-            }
-            int4 sg = __ldcs(reinterpret_cast<const int4*>(blk + 12 * FC_TT + w0));
-            const float2 xi_n = sx[0][li], ui_n = su[0][li];
-            const float2 xi_o = sx[2][li], ui_o = su[2][li];
-            const float inv_i = sinv[0][li];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                df32 v[FC_NFIELD];
-#pragma unroll
-                for (int k = 0; k < FC_NFIELD; ++k) v[k] = df_make(get4(hi[k], q), get4(lo[k], q));
-                int s = geti4(sg, q);
-                if (upd) {
-                    const PairTerms tn = pair_terms(xi_n, sx[1][lj0 + q], ui_n, su[1][lj0 + q]);
-                    v[0] = df_add_f(v[0], tn.re);
-                    v[1] = df_add_f(v[1], tn.im);
-                    v[2] = df_add_f(v[2], tn.ure);
-                    v[3] = df_add_f(v[3], tn.uim);
-                    v[4] = df_add_f(v[4], fabsf(tn.im));
-                    v[5] = df_add_df(v[5], df_sqr_f(tn.im));
-                    s += tn.sgn;
-                }
-                if (sub) {
-                    const PairTerms to = pair_terms(xi_o, sx[3][lj0 + q], ui_o, su[3][lj0 + q]);
-                    v[0] = df_add_f(v[0], -to.re);
-                    v[1] = df_add_f(v[1], -to.im);
-                    v[2] = df_add_f(v[2], -to.ure);
-                    v[3] = df_add_f(v[3], -to.uim);
-                    v[4] = df_add_f(v[4], -fabsf(to.im));
-                    v[5] = df_add_df(v[5], df_neg(df_sqr_f(to.im)));
-                    s -= to.sgn;
-                }
-#pragma unroll
-                for (int k = 0; k < FC_NFIELD; ++k) {
-                    set4(hi[k], q, v[k].hi);
-                    set4(lo[k], q, v[k].lo);
-                }
-                seti4(sg, q, s);
-                if (a.finalize && (vmask & (1u << q))) {
-                    float m[7];
-                    finalize_bin(v, s, inv_i, sinv[1][lj0 + q], K, inv_K, m);
-#pragma unroll
-                    for (int mm = 0; mm < 7; ++mm) band[mm][q] = __fadd_rn(band[mm][q], m[mm]);
-                }
-            }
-            if (upd) {
-#pragma unroll
-                for (int k = 0; k < FC_NFIELD; ++k) {
-                    __stcs(reinterpret_cast<float4*>(blk + (2 * k) * FC_TT + w0), hi[k]);
-                    __stcs(reinterpret_cast<float4*>(blk + (2 * k + 1) * FC_TT + w0), lo[k]);
-                }
-                __stcs(reinterpret_cast<int4*>(blk + 12 * FC_TT + w0), sg);
-            }
-        }
-        __syncthreads();
-    }
-    if (a.finalize && vmask) write_band(a, g, band, gi, gj0, vmask, f1 - f0);
-}
-
 // ---------------------------------------------------------------- full-window sums
 constexpr int WK = 16;  // trials staged per chunk
 
@@ -260,7 +55,7 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
     if (c->bad) return;
     const WinFacts wf = window_facts(c, a.W, a.count);
     const int K = wf.K;
-    const float inv_K = 1.0f / (float)K;
+    const KConst kc = make_kconst(K);
 
     const int tp = blockIdx.x;
     const int g = blockIdx.y;
@@ -314,7 +109,9 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
                     const float2 xi = sx[kk][li], ui = su[kk][li];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const PairTerms tt = pair_terms(xi, sx[kk][FC_T + lj0 + q], ui, su[kk][FC_T + lj0 + q]);
+                        const float2 xj = sx[kk][FC_T + lj0 + q];
+                        const PairTerms tt = pair_terms(xi, xj, ui, su[kk][FC_T + lj0 + q],
+                                                        node_tiny(xi) || node_tiny(xj));
                         v[q][0] = df_add_f(v[q][0], tt.re);
                         v[q][1] = df_add_f(v[q][1], tt.im);
                         v[q][2] = df_add_f(v[q][2], tt.ure);
@@ -346,7 +143,7 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
                 for (int q = 0; q < 4; ++q) {
                     if (!(vmask & (1u << q))) continue;
                     float m[7];
-                    finalize_bin(v[q], s[q], inv_i, sinv[1][lj0 + q], K, inv_K, m);
+                    finalize_bin(v[q], s[q], inv_i, sinv[1][lj0 + q], kc, m);
                     if (bins_out) {
                         bins_out[(size_t)f * a.P + packed_index(gi, gj0 + q, a.n)] = m[bins_metric - 2];
                     } else {
@@ -366,7 +163,7 @@ __global__ void __launch_bounds__(256) k_bins_from_acc(PairArgs a, int metric, f
     const FcCtrl* c = a.ctrl;
     const long long t = c->pushed;
     const int K = (a.W > 0 && t > a.W) ? a.W : (int)t;
-    const float inv_K = 1.0f / (float)K;
+    const KConst kc = make_kconst(K);
     const int tp = blockIdx.x, f = blockIdx.y;
     const int ta = a.tile_a[tp], tb = a.tile_b[tp];
     const int tid = threadIdx.x, li = tid >> 3, lj0 = (tid & 7) * 4;
@@ -384,7 +181,7 @@ __global__ void __launch_bounds__(256) k_bins_from_acc(PairArgs a, int metric, f
             v[k] = df_make(blk[(2 * k) * FC_TT + w0 + q], blk[(2 * k + 1) * FC_TT + w0 + q]);
         const int s = reinterpret_cast<const int*>(blk + 12 * FC_TT)[w0 + q];
         float m[7];
-        finalize_bin(v, s, inv_i, a.inv_psd[(size_t)f * a.n + gj0 + q], K, inv_K, m);
+        finalize_bin(v, s, inv_i, a.inv_psd[(size_t)f * a.n + gj0 + q], kc, m);
         out[(size_t)f * a.P + packed_index(gi, gj0 + q, a.n)] = m[metric - 2];
     }
 }
@@ -442,12 +239,6 @@ __global__ void k_df_planes(const float* acc2, long long P, double* out) {
 cudaError_t launch_node(const NodeArgs& a, cudaStream_t st) {
     const int total = a.B * a.n;
     k_node<<<(total + 255) / 256, 256, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_stream_update(const PairArgs& a, cudaStream_t st) {
-    dim3 grid(a.ntp, a.groups);
-    k_stream<<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

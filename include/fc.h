@@ -234,6 +234,42 @@ typedef enum {
 fc_status fc_debug_get_accumulators(fc_session* s, fc_acc_field field, double* out,
                                     size_t out_len);
 
+/* ---- allocation-free entry point ------------------------------------------------ */
+
+/* Size of the device scratch array behind fc_window_networks_noalloc (16 MiB). */
+#define FC_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Band-averaged spectral networks of one window, computed without allocating anything.
+ * The paper has no counterpart to this call; it exists for callers that must not call
+ * cudaMalloc: a real-time acquisition loop where an allocation (which can synchronize
+ * the whole device and take an unbounded time) would miss the per-trial deadline, or a
+ * host application whose device memory is owned by another allocator (a framework's
+ * caching allocator, a pre-reserved pool).
+ *
+ *   spectra:  device pointer, [n_trials][n_bins][n_nodes] complex values stored as
+ *             (re, im) float pairs - the layout of the library's own spectra (see
+ *             fc_debug_get_spectra). The window is all n_trials trials.
+ *   metric_mask: nonzero subset of FC_SPECTRAL_METRICS.
+ *   out:      device pointer, out[7][P] (P = n_nodes (n_nodes - 1) / 2, packed upper
+ *             per plane) in the order COH, IMAGCOHY, PLV, PLI, USPLI, WPLI, DSWPLI; only
+ *             the planes of metrics in the mask are written. out_len: element capacity.
+ *   stream:   cudaStream_t to enqueue on (NULL: the legacy default stream). The call is
+ *             asynchronous; results are ready when the stream reaches this point.
+ *
+ * Every intermediate (window control block, per-node PSD sums, tile tables, band
+ * partial sums) lives in one file-scope device array of FC_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits. Limits: the PSD sums and
+ * tile tables must fit in it (n_bins * n_nodes below about 1.3 million); the band-partial
+ * work split shrinks to what fits. Sizes beyond the limit return FC_ERR_INVALID_ARG with a
+ * message in fc_last_error(). The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. All calls share the array and it keeps the last call's contents
+ * (the control block is cleared on every call): calls whose work overlaps on the GPU
+ * (different streams, no ordering between them) race and corrupt each other.
+ * No cudaMalloc, cudaFree or allocating library routine is called. */
+fc_status fc_window_networks_noalloc(const float* spectra, int n_trials, int n_bins, int n_nodes,
+                                     uint32_t metric_mask, float* out, size_t out_len, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -347,6 +347,8 @@ fc_status check_latched(fc_session* s, FcCtrl* h) {
 
 }  // namespace
 
+void fc_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
+
 // ====================================================================== public API
 extern "C" {
 

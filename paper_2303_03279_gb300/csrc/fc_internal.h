@@ -213,6 +213,9 @@ cudaError_t launch_xcor_spectra(const XcorArgs& a, cudaStream_t st);
 cudaError_t launch_xcor_pairs(const XcorArgs& a, cudaStream_t st);
 cudaError_t launch_xcor_update(const XcorArgs& a, cudaStream_t st);
 
+// Set the thread-local message returned by fc_last_error() (for entry points outside fc_api.cu).
+void fc_internal_set_error(const char* msg);
+
 cudaError_t launch_expand_dense(const float* packed, float* dense, int n, int antisym,
                                 cudaStream_t st);
 cudaError_t launch_acc_field(const float* acc, const unsigned short* ta, const unsigned short* tb,

@@ -1,0 +1,149 @@
+// fc_noalloc.cu - spectral networks of one window without any device allocation.
+//
+// Some callers cannot call cudaMalloc: a real-time acquisition loop where an allocation
+// (which may synchronize the whole device and take an unbounded time) would break the
+// per-trial deadline, or a host application whose device memory is owned entirely by
+// another allocator (a framework's caching allocator, a pre-reserved pool). For them,
+// fc_window_networks_noalloc computes the band-averaged spectral networks of a window
+// from spectra the caller already holds on the device, into an output the caller owns,
+// and keeps every intermediate (window control block, per-node PSD sums, tile tables,
+// band partial sums) in one file-scope device array of FC_NOALLOC_SCRATCH_BYTES that
+// the library holds on every GPU that loads it, until the process exits.
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "fc_internal.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)FC_NOALLOC_SCRATCH_BYTES;
+
+// The shared scratch: every call uses it, and it keeps the last call's contents.
+static __device__ __align__(256) unsigned char fc_noalloc_scratch[kScratchBytes];
+
+// Device address of the scratch array per device (the host symbol is only a stand-in).
+constexpr int kMaxDevices = 64;
+void* g_scratch_addr[kMaxDevices];
+std::once_flag g_scratch_once[kMaxDevices];
+cudaError_t g_scratch_status[kMaxDevices];
+
+cudaError_t scratch_address(int dev, void** out) {
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::call_once(g_scratch_once[dev], [dev]() {
+        void* p = nullptr;
+        g_scratch_status[dev] = cudaGetSymbolAddress(&p, fc_noalloc_scratch);
+        g_scratch_addr[dev] = p;
+    });
+    *out = g_scratch_addr[dev];
+    return g_scratch_status[dev];
+}
+
+__global__ void k_noalloc_tiles(unsigned short* ta, unsigned short* tb, int nt) {
+    const int tp = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tp >= nt * (nt + 1) / 2) return;
+    int r = tp, a = 0;
+    while (r >= nt - a) {
+        r -= nt - a;
+        ++a;
+    }
+    ta[tp] = (unsigned short)a;
+    tb[tp] = (unsigned short)(a + r);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+fc_status noalloc_fail(fc_status st, const char* msg) {
+    fc_internal_set_error(msg);
+    return st;
+}
+
+}  // namespace
+
+extern "C" fc_status fc_window_networks_noalloc(const float* spectra, int n_trials, int n_bins, int n_nodes,
+                                                uint32_t metric_mask, float* out, size_t out_len,
+                                                void* stream) {
+    if (!spectra || !out) return noalloc_fail(FC_ERR_INVALID_ARG, "spectra and out must be device pointers");
+    if (n_trials < 1 || n_bins < 1 || n_nodes < 2 || n_nodes > 65535 * FC_T)
+        return noalloc_fail(FC_ERR_INVALID_ARG, "need n_trials >= 1, n_bins >= 1, n_nodes >= 2");
+    if ((metric_mask & ~(uint32_t)FC_SPECTRAL_METRICS) || !(metric_mask & FC_SPECTRAL_METRICS))
+        return noalloc_fail(FC_ERR_INVALID_ARG, "metric_mask must be a nonzero subset of the spectral metrics");
+    const long long P = (long long)n_nodes * (n_nodes - 1) / 2;
+    if (out_len < (size_t)(7 * P)) return noalloc_fail(FC_ERR_INVALID_ARG, "out_len must be >= 7 * n(n-1)/2");
+
+    // scratch plan: control block | PSD sums (double) | 1/sqrt(PSD) | tile tables | band partials
+    const int nt = (n_nodes + FC_T - 1) / FC_T;
+    const int ntp = nt * (nt + 1) / 2;
+    const size_t off_psd = align256(sizeof(FcCtrl));
+    const size_t off_inv = align256(off_psd + sizeof(double) * (size_t)n_bins * n_nodes);
+    const size_t off_ta = align256(off_inv + sizeof(float) * (size_t)n_bins * n_nodes);
+    const size_t off_tb = align256(off_ta + sizeof(unsigned short) * (size_t)ntp);
+    const size_t off_part = align256(off_tb + sizeof(unsigned short) * (size_t)ntp);
+    if (off_part > kScratchBytes)
+        return noalloc_fail(FC_ERR_INVALID_ARG,
+                            "window too large for the fixed scratch (n_bins * n_nodes must stay below ~1.3 M)");
+    // bin groups: as many as fill the GPU and fit in the remaining scratch
+    int groups = std::min(n_bins, std::max(1, (152 * 4 + ntp - 1) / ntp));
+    const size_t per_group = sizeof(float) * 7 * (size_t)P;
+    while (groups > 1 && off_part + per_group * groups > kScratchBytes) --groups;
+    const int group_bins = (n_bins + groups - 1) / groups;
+    groups = (n_bins + group_bins - 1) / group_bins;
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    void* base = nullptr;
+    if (e == cudaSuccess) e = scratch_address(dev, &base);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return noalloc_fail(FC_ERR_CUDA, cudaGetErrorString(e));
+    }
+    unsigned char* s = static_cast<unsigned char*>(base);
+    FcCtrl* ctrl = reinterpret_cast<FcCtrl*>(s);
+    double* psd = reinterpret_cast<double*>(s + off_psd);
+    float* inv = reinterpret_cast<float*>(s + off_inv);
+    unsigned short* ta = reinterpret_cast<unsigned short*>(s + off_ta);
+    unsigned short* tb = reinterpret_cast<unsigned short*>(s + off_tb);
+    float* partial = groups > 1 ? reinterpret_cast<float*>(s + off_part) : nullptr;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // the window control block must start at zero: trials [0, n_trials) of the given spectra
+    e = cudaMemsetAsync(ctrl, 0, sizeof(FcCtrl), st);
+    if (e == cudaSuccess) {
+        k_noalloc_tiles<<<(ntp + 255) / 256, 256, 0, st>>>(ta, tb, nt);
+        e = cudaGetLastError();
+    }
+    const float2* ring = reinterpret_cast<const float2*>(spectra);
+    if (e == cudaSuccess) {
+        NodeArgs na{ring, psd, inv, n_trials, n_nodes, n_bins, n_trials, 1, ctrl, n_trials};
+        e = launch_node(na, st);
+    }
+    PairArgs pa{};
+    pa.ring = ring;
+    pa.inv_psd = inv;
+    pa.acc = nullptr;
+    pa.tile_a = ta;
+    pa.tile_b = tb;
+    // the kernels address network planes 2..8 (the spectral metrics) of a [9][P] block:
+    // base the block two planes before `out` so that they land in out[0..6][P]
+    pa.net = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(out) - 2 * sizeof(float) * (size_t)P);
+    pa.partial = partial;
+    pa.slots = n_trials;
+    pa.n = n_nodes;
+    pa.B = n_bins;
+    pa.W = n_trials;
+    pa.ntp = ntp;
+    pa.P = P;
+    pa.groups = groups;
+    pa.group_bins = group_bins;
+    pa.mask = metric_mask;
+    pa.finalize = 1;
+    pa.update = 1;
+    pa.write_acc = 0;
+    pa.count = n_trials;
+    pa.grid_ctas = 2 * 152;
+    pa.ctrl = ctrl;
+    if (e == cudaSuccess) e = launch_window_sums(pa, st);
+    if (e == cudaSuccess && groups > 1) e = launch_band_reduce(pa, st);
+    if (e != cudaSuccess) return noalloc_fail(FC_ERR_CUDA, cudaGetErrorString(e));
+    return FC_OK;
+}

@@ -101,6 +101,8 @@ _SIGNATURES = [
     ("fc_debug_get_spectra", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
     ("fc_debug_get_scale", C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
     ("fc_debug_get_accumulators", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
+    ("fc_window_networks_noalloc", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_void_p,
+                                             C.c_size_t, C.c_void_p]),
 ]
 
 
@@ -257,6 +259,21 @@ def fc_debug_get_accumulators(s, field, out):
     if dev:
         raise ValueError("host output expected")
     _check(_LIB.fc_debug_get_accumulators(s, int(field), p, nel))
+
+
+def fc_window_networks_noalloc(spectra, n_trials: int, n_bins: int, n_nodes: int, metric_mask: int, out,
+                               stream=None):
+    """Allocation-free band-averaged spectral networks of one window (device tensors).
+
+    spectra: CUDA float32 tensor [n_trials][n_bins][n_nodes][2]; out: CUDA float32 tensor
+    with at least 7 * n_nodes * (n_nodes - 1) / 2 elements; stream: cudaStream_t or None.
+    """
+    p_in, dev_in, _ = _ptr(spectra, np.float32)
+    p_out, dev_out, nel = _ptr(out, np.float32)
+    if not (dev_in and dev_out):
+        raise ValueError("spectra and out must be CUDA tensors")
+    _check(load().fc_window_networks_noalloc(p_in, int(n_trials), int(n_bins), int(n_nodes), int(metric_mask),
+                                             p_out, nel, C.c_void_p(int(stream) if stream else 0)))
 
 
 # ----------------------------------------------------------------- convenience

@@ -132,7 +132,7 @@ def measured_peaks():
 
 def stream_kernel_hash():
     h = hashlib.sha256()
-    for f in ("k_pairs.cu", "df32.cuh", "terms.cuh", "fc_internal.h"):
+    for f in ("k_stream.cu", "pair_common.cuh", "df32.cuh", "terms.cuh"):
         with open(os.path.join(ROOT, "paper_2303_03279_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -141,15 +141,15 @@ def stream_kernel_hash():
 def ncu_traffic(kernel_hash, workload):
     """DRAM bytes per launch of the streaming kernel from the committed ncu summary, or None
     when the kernel source changed since the counters were taken."""
-    p = os.path.join(ROOT, "profiles", "k_stream_traffic.json")
+    p = os.path.join(ROOT, "profiles", "k_stream_traffic.txt")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        d = json.load(f)
-    e = d.get(workload)
-    if not e or e.get("kernel_hash") != kernel_hash:
-        return None
-    return float(e["dram_bytes_per_launch"])
+        for line in f:
+            parts = line.split()
+            if len(parts) == 3 and not line.startswith("#") and parts[0] == workload and parts[1] == kernel_hash:
+                return float(parts[2])
+    return None
 
 
 # ----------------------------------------------------------------- trial pool

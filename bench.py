@@ -341,6 +341,7 @@ def run_ours(args, w, wname):
 
     # plain FP32 comparator: CUDA-core full-window recompute per push, no accumulators
     plain = None
+    mixed = None
     if not args.no_plain:
         ps = fc.Session(n, N, w["fs"], B_band, "hann", mask, W, mode=fc.FC_MODE_FULL, stream=stream.cuda_stream)
         fc.fc_push_trials(ps.handle, dev[:W].contiguous(), W)
@@ -358,6 +359,38 @@ def run_ours(args, w, wname):
                  "latency_ms": {"p50": pl[len(pl) // 2], "p99": pl[-1]}, "steps": pst,
                  "path": "CUDA-core full-window recompute per push (FC_MODE_FULL), FP32"}
         ps.close()
+        del ps
+        # mixed precision full window: tensor-core linear sums (BF16) + CUDA-core non-linear sums
+        ms = fc.Session(n, N, w["fs"], B_band, "hann", mask, W, mode=fc.FC_MODE_FULL, precision=fc.FC_PREC_BF16,
+                        stream=stream.cuda_stream)
+        fc.fc_push_trials(ms.handle, dev[:W].contiguous(), W)
+        fc.fc_sync(ms.handle)
+        fc.fc_set_profiling(ms.handle, True)
+        fc.fc_kernel_times(ms.handle, reset=True)
+        mst = max(3, min(args.plain_steps * 3, steps))
+        mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(mst)]
+        for k in range(mst):
+            mev[k][0].record(stream)
+            fc.fc_push_trial(ms.handle, trial(W + k))
+            mev[k][1].record(stream)
+        torch.cuda.synchronize()
+        mkt = fc.fc_kernel_times(ms.handle, reset=True)
+        ml = sorted(a.elapsed_time(b) for a, b in mev)
+        mms = sum(ml) / len(ml)
+        tc_launches, tc_ms = mkt["herk_tc"]
+        mixed = {"value": world * units / (mms / 1000.0), "unit": UNIT, "ms_per_step": mms,
+                 "latency_ms": {"p50": ml[len(ml) // 2], "p99": ml[-1]}, "steps": mst,
+                 "path": "full-window recompute per push: tcgen05 BF16 Hermitian products (COH, IMAGCOHY, PLV) "
+                         "+ CUDA-core non-linear sums (PLI, USPLI, WPLI, DSWPLI)",
+                 "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in mkt.items() if v[0]}}
+        if tc_launches:
+            # tensor-core work: 4 real GEMMs of 128 x 128 x Kp per (128-node tile pair, bin), Kp = 2W padded to 64
+            nt128 = (n + 127) // 128
+            kp = ((2 * W + 63) // 64) * 64
+            flops = 4 * 2 * 128 * 128 * kp * (nt128 * (nt128 + 1) // 2) * B
+            mixed["tensor"] = {"flops_per_push": flops, "herk_ms_per_push": tc_ms / tc_launches * 2,
+                               "note": "herk_tc timing covers the operand pack and the MMA kernel"}
+        ms.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -382,7 +415,7 @@ def run_ours(args, w, wname):
                    "l2": "inputs larger than L2 (27.8 GB resident state), no flush",
                    "parallelism": f"{world} independent session(s), one per GPU"},
         "latency_ms": {"p50": p50, "p99": p99, "what": "device time from push enqueue to network ready"},
-        "plain_fp32": plain, "roofline": roofline, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
+        "plain_fp32": plain, "mixed_bf16_full_window": mixed, "roofline": roofline, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
         "clocks": clocks.summary(), "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)

@@ -258,6 +258,52 @@ fc_status stage_time_metrics(fc_session* s, const float* x, int count, int write
 fc_status stage_window(fc_session* s, int count, bool write_acc) {
     NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, 1, s->ctrl, count};
     LAUNCH(FC_K_NODE, launch_node(na, s->stream));
+    if (s->ops && !write_acc) {
+        // mixed precision: linear sums (COH, IMAGCOHY, PLV) on the tensor cores, the
+        // non-linear sums (PLI, USPLI, WPLI, DSWPLI) on the CUDA cores
+        PackArgs pk{};
+        pk.ring = s->ring;
+        pk.ops = s->ops;
+        pk.n = s->n;
+        pk.B = s->B;
+        pk.W = s->W;
+        pk.slots = s->slots;
+        pk.ntiles = s->nt128;
+        pk.nchunks = s->nchunks;
+        pk.count = count;
+        pk.ab_format = s->ab_format;
+        pk.ctrl = s->ctrl;
+        HerkArgs ha{};
+        ha.ops = s->ops;
+        ha.tile_a = s->tile_a128;
+        ha.tile_b = s->tile_b128;
+        ha.inv_psd = s->inv_psd;
+        ha.bins_out = s->herk_bins;
+        ha.net = s->net;
+        ha.n = s->n;
+        ha.B = s->B;
+        ha.ntp = s->ntp128;
+        ha.nchunks = s->nchunks;
+        ha.W = s->W;
+        ha.count = count;
+        ha.ab_format = s->ab_format;
+        ha.grid_ctas = s->num_sms;
+        ha.P = s->P;
+        ha.mask = s->mask;
+        ha.ctrl = s->ctrl;
+        if (s->mask & (FC_COH | FC_IMAGCOHY | FC_PLV)) {
+            LAUNCH(FC_K_HERK_TC, launch_pack_operands(pk, s->stream));
+            LAUNCH(FC_K_HERK_TC, launch_herk_tc(ha, s->stream));
+            LAUNCH(FC_K_BAND_REDUCE, launch_herk_band(ha, s->stream));
+        }
+        PairArgs pn = pair_args(s, false, count);
+        pn.mask = s->mask & (FC_PLI | FC_USPLI | FC_WPLI | FC_DSWPLI);
+        if (pn.mask) {
+            LAUNCH(FC_K_WINDOW, launch_nonlinear_sums(pn, s->stream));
+            if (pn.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pn, s->stream));
+        }
+        return FC_OK;
+    }
     PairArgs pa = pair_args(s, false, count);
     pa.write_acc = write_acc ? 1 : 0;
     pa.finalize = (s->mask & FC_SPECTRAL_METRICS) ? 1 : 0;
@@ -382,8 +428,9 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
     if (cfg.mode != FC_MODE_STREAM && cfg.mode != FC_MODE_FULL) return fail(FC_ERR_INVALID_ARG, "bad mode");
     if (cfg.mode == FC_MODE_FULL && window < 1) return fail(FC_ERR_INVALID_ARG, "full mode needs window >= 1");
     if (cfg.precision < FC_PREC_FP32 || cfg.precision > FC_PREC_FP16) return fail(FC_ERR_INVALID_ARG, "bad precision");
-    if (cfg.precision != FC_PREC_FP32)
-        return fail(FC_ERR_UNSUPPORTED, "tensor-core precisions are not available in this build");
+    if (cfg.precision != FC_PREC_FP32 && cfg.mode != FC_MODE_FULL)
+        return fail(FC_ERR_UNSUPPORTED,
+                    "tensor-core precisions apply to FC_MODE_FULL; the streaming sums stay exact FP32 terms");
     if ((cfg.dev_alloc == nullptr) != (cfg.dev_free == nullptr))
         return fail(FC_ERR_INVALID_ARG, "dev_alloc and dev_free must be given together");
     // band bins: f_lo <= k fs / nfft < f_hi
@@ -487,6 +534,25 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
         cudaMemcpy(s->tile_b, tb.data(), tb.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
     }
     if (cfg.mode == FC_MODE_STREAM) TRY(alloc_zero(s, (size_t)s->ntp * B * FC_BLOCK_WORDS, &s->acc));
+    if (cfg.precision != FC_PREC_FP32) {
+        s->ab_format = cfg.precision == FC_PREC_BF16 ? 1 : (cfg.precision == FC_PREC_FP16 ? 0 : 2);
+        const int per_chunk = s->ab_format == 2 ? 32 : 64;  // inner elements per 128-byte K-chunk
+        s->nchunks = (2 * window + per_chunk - 1) / per_chunk;
+        s->nt128 = (n_nodes + 127) / 128;
+        s->ntp128 = s->nt128 * (s->nt128 + 1) / 2;
+        std::vector<unsigned short> ta, tb;
+        for (int a = 0; a < s->nt128; ++a)
+            for (int b = a; b < s->nt128; ++b) {
+                ta.push_back((unsigned short)a);
+                tb.push_back((unsigned short)b);
+            }
+        TRY(alloc_zero(s, ta.size(), &s->tile_a128));
+        TRY(alloc_zero(s, tb.size(), &s->tile_b128));
+        cudaMemcpy(s->tile_a128, ta.data(), ta.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
+        cudaMemcpy(s->tile_b128, tb.data(), tb.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
+        TRY(alloc_zero(s, (size_t)s->nt128 * B * 4 * s->nchunks * herk_chunk_bytes(), &s->ops));
+        TRY(alloc_zero(s, (size_t)B * 3 * s->P, &s->herk_bins));
+    }
     TRY(alloc_zero(s, (size_t)FC_NMETRIC * s->P, &s->net));
     if (max_groups > 1) TRY(alloc_zero(s, (size_t)max_groups * 7 * s->P, &s->partial));
     if (s->time_mask & FC_COR) {
@@ -610,6 +676,7 @@ fc_status fc_get_network_bins(fc_session* s, uint32_t metric, float* out, size_t
     if (!s || !out) return fail(FC_ERR_INVALID_ARG, "NULL session or output");
     const int mi = metric_index(metric);
     if (mi < MI_COH) return fail(FC_ERR_INVALID_ARG, "per-bin values exist for spectral metrics only");
+    if (s->ops) return fail(FC_ERR_UNSUPPORTED, "per-bin values are available with FC_PREC_FP32 sessions");
     const size_t need = (size_t)s->B * s->P;
     if (out_len < need) return fail(FC_ERR_INVALID_ARG, "out_len %zu < %zu", out_len, need);
     CK(cudaSetDevice(s->device));
@@ -672,9 +739,8 @@ fc_status fc_set_metric_mask(fc_session* s, uint32_t metric_mask) {
             LAUNCH(FC_K_STREAM, launch_stream_update(pa, s->stream));
             if (pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
         } else {
-            PairArgs pa = pair_args(s, false, 0);
-            LAUNCH(FC_K_WINDOW, launch_window_sums(pa, s->stream));
-            if (pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
+            fc_status st = stage_window(s, 0, false);
+            if (st != FC_OK) return st;
         }
     }
     return FC_OK;

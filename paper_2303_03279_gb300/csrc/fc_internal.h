@@ -110,6 +110,12 @@ struct fc_session {
     float2* xcor_spec;      // XCOR spectra of the trials in flight [count][n][L/2+1]
     float* xcor_energy;     // XCOR [count][n]
     int xcor_spec_trials;
+    // tensor-core full-window path (precision BF16 / FP16 / TF32)
+    int nt128, ntp128, nchunks, ab_format;
+    unsigned short* tile_a128;
+    unsigned short* tile_b128;
+    unsigned char* ops;     // packed operands [nt128][B][4][nchunks][16 KB]
+    float* herk_bins;       // [B][3][P] per-bin COH, IMAGCOHY, PLV
     size_t device_bytes;
 
     // measurement
@@ -171,6 +177,33 @@ cudaError_t launch_window_sums(const PairArgs& a, cudaStream_t st);
 cudaError_t launch_band_reduce(const PairArgs& a, cudaStream_t st);
 cudaError_t launch_bins_from_acc(const PairArgs& a, int metric_index, float* out, cudaStream_t st);
 cudaError_t launch_bins_window(const PairArgs& a, int metric_index, float* out, cudaStream_t st);
+
+// Tensor-core full-window linear sums (k_herk_tc.cu).
+struct PackArgs {
+    const float2* ring;
+    unsigned char* ops;   // [tiles128][B][4 kinds][nchunks][16 KB]
+    int n, B, W, slots, ntiles, nchunks, count;
+    int ab_format;        // 0 = FP16, 1 = BF16, 2 = TF32
+    const FcCtrl* ctrl;
+};
+struct HerkArgs {
+    const unsigned char* ops;
+    const unsigned short* tile_a;  // 128-node tile pairs
+    const unsigned short* tile_b;
+    const float* inv_psd;
+    float* bins_out;      // [B][3][P] per-bin COH, IMAGCOHY, PLV
+    float* net;           // [FC_NMETRIC][P]
+    int n, B, ntp, nchunks, W, count, ab_format, grid_ctas;
+    long long P;
+    uint32_t mask;
+    const FcCtrl* ctrl;
+};
+cudaError_t launch_pack_operands(const PackArgs& a, cudaStream_t st);
+cudaError_t launch_herk_tc(const HerkArgs& a, cudaStream_t st);
+cudaError_t launch_herk_band(const HerkArgs& a, cudaStream_t st);
+size_t herk_chunk_bytes();
+// Non-linear sums only (signs, |Im|, Im, Im^2) with the PLI/USPLI/WPLI/DSWPLI finalize.
+cudaError_t launch_nonlinear_sums(const PairArgs& a, cudaStream_t st);
 
 struct CommitArgs {
     FcCtrl* ctrl;

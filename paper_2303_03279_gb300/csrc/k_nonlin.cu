@@ -1,0 +1,132 @@
+// k_nonlin.cu - the non-linear pair sums of the mixed-precision full-window path.
+//
+// The phase-lag metrics need sums that are not contractions (Supplementary Information 1):
+//   PLI = |sum sign(Im CSD)| / K, USPLI from the same integer,
+//   WPLI = |sum Im| / sum |Im|,  DSWPLI = ((sum Im)^2 - sum Im^2) / ((sum |Im|)^2 - sum Im^2),
+// with Im = Im(X_i X_j*). Here they run on the CUDA cores beside the tensor-core linear
+// sums (k_herk_tc.cu), which produce COH, IMAGCOHY and PLV. Im and its exact sign use the
+// same term code as the exact path (terms.cuh). The sums run in FP32 over chunks of 16
+// trials and each chunk's partial sums (Im, |Im|, Im^2) are promoted to double-word
+// accumulators, so the debiased cancellation (sum Im)^2 - sum Im^2 is evaluated from
+// FP64-class sums; the sign count is an exact int32.
+//
+// CTA: one 32 x 32 tile pair x a group of bins; thread: 4 adjacent pairs of the tile.
+#include "df32.cuh"
+#include "fc_internal.h"
+#include "pair_common.cuh"
+#include "terms.cuh"
+
+namespace {
+
+using namespace fcpair;
+
+constexpr int NK = 16;  // trials per staged chunk (and per FP32 partial sum)
+
+__global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
+    const FcCtrl* c = a.ctrl;
+    if (c->bad) return;
+    const long long end = c->pushed + a.count;
+    const long long start = (a.W > 0 && end > a.W) ? end - a.W : 0;
+    const int K = (int)(end - start);
+    if (K <= 0) return;
+    const KConst kc = make_kconst(K);
+
+    const int tp = blockIdx.x, g = blockIdx.y;
+    const int f0 = g * a.group_bins, f1 = min(a.B, f0 + a.group_bins);
+    const int ta = a.tile_a[tp], tb = a.tile_b[tp];
+    const int tid = threadIdx.x, li = tid >> 3, lj0 = (tid & 7) * 4;
+    const unsigned vmask = pair_mask(ta, tb, li, lj0, a.n);
+    const int gi = ta * FC_T + li, gj0 = tb * FC_T + lj0;
+
+    __shared__ float2 sx[NK][2 * FC_T];
+    __shared__ unsigned char stiny[NK][2 * FC_T];
+
+    float band[7][4];
+#pragma unroll
+    for (int m = 0; m < 7; ++m)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) band[m][q] = 0.f;
+
+    for (int f = f0; f < f1; ++f) {
+        df32 s_im[4], s_sq[4], s_abs[4];
+        int s_sg[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            s_im[q] = s_sq[q] = s_abs[q] = df_make(0.f, 0.f);
+            s_sg[q] = 0;
+        }
+        for (int k0 = 0; k0 < K; k0 += NK) {
+            const int kn = min(NK, K - k0);
+            __syncthreads();
+            for (int e = tid; e < kn * 2 * FC_T; e += 256) {
+                const int kk = e / (2 * FC_T), l = e % (2 * FC_T);
+                const int node = l < FC_T ? ta * FC_T + l : tb * FC_T + l - FC_T;
+                const long long trial = start + k0 + kk;
+                float2 X = make_float2(0.f, 0.f);
+                if (node < a.n) X = a.ring[((size_t)(trial % a.slots) * a.B + f) * a.n + node];
+                sx[kk][l] = X;
+                stiny[kk][l] = node_tiny(X) ? 1 : 0;
+            }
+            __syncthreads();
+            if (!vmask) continue;
+            float p_im[4] = {0.f, 0.f, 0.f, 0.f}, p_sq[4] = {0.f, 0.f, 0.f, 0.f}, p_abs[4] = {0.f, 0.f, 0.f, 0.f};
+            float p_sqe[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int kk = 0; kk < kn; ++kk) {
+                const float2 xi = sx[kk][li];
+                const bool ti = stiny[kk][li] != 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 xj = sx[kk][FC_T + lj0 + q];
+                    // Im(X_i X_j*) and its exact sign, as in pair_terms (terms.cuh)
+                    const float p = __fmul_rn(xi.y, xj.x), np = __fmul_rn(-xi.y, xj.x);
+                    const float qq = __fmul_rn(xi.x, xj.y), nq = __fmul_rn(-xi.x, xj.y);
+                    const float e = __fmaf_rn(xi.y, xj.x, np);
+                    const float nf = __fmaf_rn(-xi.x, xj.y, qq);
+                    const float d1 = __fadd_rn(p, nq), d2 = __fadd_rn(e, nf);
+                    float im = __fadd_rn(d1, d2);
+                    int sg = sign_of(d1 != 0.f ? d1 : d2);
+                    if (ti || stiny[kk][FC_T + lj0 + q]) im_sign_fp64(xi.x, xi.y, xj.x, xj.y, im, sg);
+                    s_sg[q] += sg;
+                    p_abs[q] = __fadd_rn(p_abs[q], fabsf(im));
+                    p_im[q] = __fadd_rn(p_im[q], im);
+                    // im^2 as an exact two-product (t + r): a lone nonzero term then gives
+                    // (sum |Im|)^2 - sum Im^2 = 0 exactly, as in the exact path
+                    float t, r;
+                    two_prod(im, im, t, r);
+                    p_sq[q] = __fadd_rn(p_sq[q], t);
+                    p_sqe[q] = __fadd_rn(p_sqe[q], r);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                s_im[q] = df_add_f(s_im[q], p_im[q]);
+                s_sq[q] = df_add_f(df_add_f(s_sq[q], p_sq[q]), p_sqe[q]);
+                s_abs[q] = df_add_f(s_abs[q], p_abs[q]);
+            }
+        }
+        if (vmask) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!(vmask & (1u << q))) continue;
+                // PLI, USPLI, WPLI, DSWPLI (metric slots 3..6)
+                band[3][q] = __fadd_rn(band[3][q], __fmul_rn((float)abs(s_sg[q]), kc.inv_K));
+                band[4][q] = __fadd_rn(band[4][q], __fmul_rn((float)((long long)s_sg[q] * s_sg[q] - K), kc.inv_KK1));
+                const float sim = df_to_f(s_im[q]);
+                const float sab = df_to_f(s_abs[q]);
+                band[5][q] = __fadd_rn(band[5][q], sab > 0.f ? __fdividef(fabsf(sim), sab) : 0.f);
+                const float num = df_sq_minus(s_im[q], s_sq[q]);
+                const float den = df_sq_minus(s_abs[q], s_sq[q]);
+                band[6][q] = __fadd_rn(band[6][q], den != 0.f ? __fdividef(num, den) : 0.f);
+            }
+        }
+    }
+    if (vmask) write_band(a, g, band, gi, gj0, vmask, f1 - f0);
+}
+
+}  // namespace
+
+cudaError_t launch_nonlinear_sums(const PairArgs& a, cudaStream_t st) {
+    dim3 grid(a.ntp, a.groups);
+    k_nonlin<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}

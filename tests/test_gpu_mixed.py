@@ -1,0 +1,100 @@
+"""Mixed-precision full-window path against the FP64 oracle.
+
+COH, IMAGCOHY and PLV come from the tensor-core Hermitian products (tcgen05, BF16 / FP16
+/ TF32 operands, FP32 accumulation): |gpu - oracle| <= 5e-3 absolute. PLI, USPLI, WPLI and
+DSWPLI come from the CUDA-core non-linear sums on the exact FP32 terms: 1e-5 relative,
+with the sign sums recovered exactly. The oracle runs on the GPU's own FP32 spectra, so
+the differences isolate the operand rounding of the contraction.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import eeg_sinusoid_trials, meg_pink_trials, white_trials
+from _fc_helpers import assert_close, window_spectra, packed_index
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2303_03279_gb300 import fc  # noqa: E402
+
+LINEAR = ("COH", "IMAGCOHY", "PLV")
+NONLINEAR = ("PLI", "USPLI", "WPLI", "DSWPLI")
+PRECISIONS = {"bf16": fc.FC_PREC_BF16, "fp16": fc.FC_PREC_FP16, "tf32": fc.FC_PREC_TF32}
+TOL_TC = {"bf16": 5e-3, "fp16": 5e-3, "tf32": 5e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fc.load()
+
+
+def _check(s, K, I=None, J=None, prec="bf16"):
+    X = window_spectra(s, K)
+    n = s.n
+    if I is None:
+        I, J = np.triu_indices(n, 1)
+    ref = O.spectral_networks_pairs(X, I, J)
+    p = packed_index(I, J, n)
+    errs = {}
+    for m in LINEAR:
+        got = s.network(m, packed=True)[0].astype(np.float64)[p]
+        err = np.abs(got - ref[m])
+        errs[m] = float(err.max())
+        assert err.max() <= TOL_TC[prec], (m, prec, err.max())
+    for m in NONLINEAR:
+        got = s.network(m, packed=True)[0].astype(np.float64)[p]
+        assert_close(got, ref[m], what=f"{m} ({prec})")
+        errs[m] = float(np.abs(got - ref[m]).max())
+    pli = s.network("PLI", packed=True)[0].astype(np.float64)[p]
+    assert np.array_equal(np.rint(pli * K * s.B), np.rint(ref["PLI"] * K * s.B))
+    print(f"[{prec}] max |gpu - oracle|:", {k: f"{v:.2e}" for k, v in errs.items()})
+    return errs
+
+
+@pytest.mark.parametrize("prec", sorted(PRECISIONS))
+def test_mixed_full_window_eeg(prec):
+    x, _ = eeg_sinusoid_trials(7)  # 60 ch, 20 trials, 500 samples
+    K, n, N = x.shape
+    with fc.Session(n, N, 1000.0, (1.0, 50.0, 512), "hann", fc.FC_SPECTRAL_METRICS, K,
+                    mode=fc.FC_MODE_FULL, precision=PRECISIONS[prec]) as s:
+        s.push(x)
+        _check(s, K, prec=prec)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_mixed_full_window_meg_sampled(prec):
+    x, _ = meg_pink_trials(8)  # 306 ch, 100 trials, 1000 samples, 101 bins
+    K, n, N = x.shape
+    rng = np.random.default_rng(3)
+    with fc.Session(n, N, 1000.0, (1.0, 100.0, 1024), "hann", fc.FC_SPECTRAL_METRICS, K,
+                    mode=fc.FC_MODE_FULL, precision=PRECISIONS[prec]) as s:
+        s.push(x)
+        iu = np.triu_indices(n, 1)
+        pick = rng.choice(len(iu[0]), 2000, replace=False)
+        # include pairs across the 128-node tile boundaries and in the ragged last tile
+        I = np.concatenate([iu[0][pick], [0, 127, 127, 255, 300]])
+        J = np.concatenate([iu[1][pick], [1, 128, 255, 256, 305]])
+        _check(s, K, I, J, prec=prec)
+
+
+def test_mixed_window_fill_and_slide():
+    # the window fills (K < W), then slides; the contraction length follows K
+    n, N, W = 150, 128, 6
+    x = white_trials(17, 9, n, N)
+    with fc.Session(n, N, 256.0, (4.0, 60.0, 128), "hann", fc.FC_SPECTRAL_METRICS, W,
+                    mode=fc.FC_MODE_FULL, precision=fc.FC_PREC_BF16) as s:
+        for t in range(9):
+            s.push(x[t])
+            if t + 1 in (1, 4, 9):
+                _check(s, min(t + 1, W))
+
+
+def test_streaming_rejects_tensor_core_precision():
+    with pytest.raises(fc.FcError) as e:
+        fc.Session(40, 64, 128.0, (4.0, 40.0, 64), "hann", fc.FC_SPECTRAL_METRICS, 4,
+                   mode=fc.FC_MODE_STREAM, precision=fc.FC_PREC_BF16)
+    assert e.value.status == fc.FC_ERR_UNSUPPORTED

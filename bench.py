@@ -152,6 +152,22 @@ def ncu_traffic(kernel_hash, workload):
     return None
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's value (the whole job ends when its last rank ends)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Units all ranks processed per second: every rank runs its own session (weak scaling)."""
+    return world * units_per_rank / (ms_per_step / 1000.0)
+
+
 # ----------------------------------------------------------------- trial pool
 
 
@@ -182,12 +198,29 @@ def _oracle_sample_job(args):
     return dt, P * len(bins)
 
 
-def cpu_oracle_time(w, n_sub, reps=1):
-    """Time the oracle, single-threaded (BLAS threads pinned to 1), in a spawned process."""
+def host_cpu():
+    """CPU model and logical core count of this host."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    return {"model": model or "unknown", "nproc": os.cpu_count() or 1}
+
+
+def cpu_oracle_time(w, n_sub, reps=1, threads=1):
+    """Time the oracle in a spawned process; BLAS threads pinned to ``threads`` (the numpy
+    oracle's only multithreaded steps are its library matmuls)."""
     env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     old = {k: os.environ.get(k) for k in env_keys}
     for k in env_keys:
-        os.environ[k] = "1"
+        os.environ[k] = str(threads)
     try:
         ctx = mp.get_context("spawn")
         with ctx.Pool(1) as pool:
@@ -229,6 +262,76 @@ def run_reference(args, w, wname):
 
 
 # ----------------------------------------------------------------- GPU leg
+
+
+SERVING = dict(N=500, fs=1000.0, pool=4,
+               desc="16 concurrent sessions (4x60, 4x128, 4x306, 3x1000, 1x5124 nodes), windows "
+                    "W ~ U{20..100} trials x 500 samples @1 kHz, 7 spectral metrics; sensor-size sessions "
+                    "(<= 306 nodes) nfft 512, 1-50 Hz (25 bins), source-size sessions nfft 1000, 4-44 Hz "
+                    "(40 bins); Poisson arrivals at U[5, 50] trials/s per session; N(0,1) trials")
+
+
+def serving_band(n_nodes):
+    """Sensor-size sessions: 1-50 Hz at nfft 512; source-size sessions: 4-44 Hz at nfft 1000."""
+    return (1.0, 50.0, 512) if n_nodes <= 306 else (4.0, 44.0, 1000)
+
+
+def band_bin_count(band, fs):
+    return sum(1 for k in range(band[2] // 2 + 1) if band[0] * band[2] <= k * fs < band[1] * band[2])
+
+
+def serving_leg(fc, plain, duration_s, seed, saturate=False):
+    """Replay the serving trace through one fc_server (batched streaming, or plain FP32).
+
+    Every session gets one untimed trial first (calibration, module load). In replay mode
+    each trial is submitted at its Poisson arrival time; with ``saturate`` every trial of
+    the trace is submitted at once (peak aggregate throughput). Latency = completion time
+    of the trial's network - its arrival time (host clock).
+    """
+    from synth import serving_trace, white_trials
+
+    trace = serving_trace(seed, duration_s)
+    N, fs = SERVING["N"], SERVING["fs"]
+    pools = {n: white_trials(1000 + n, SERVING["pool"], n, N) for n in sorted({s.n_nodes for s in trace})}
+    sv = fc.fc_server_create(plain=plain)
+    try:
+        ids = [fc.fc_server_open(sv, s.n_nodes, N, fs, serving_band(s.n_nodes), "hann", fc.FC_SPECTRAL_METRICS,
+                                 s.window) for s in trace]
+        for k, s in enumerate(trace):
+            fc.fc_server_submit(sv, ids[k], pools[s.n_nodes][SERVING["pool"] - 1], fc.fc_server_now_ms())
+        fc.fc_server_drain(sv, 600000)
+        fc.fc_server_poll(sv, len(trace) + 8)
+        st0 = fc.fc_server_stats_get(sv)
+        events = sorted((float(t), k) for k, s in enumerate(trace) for t in s.arrivals_s)
+        units = {ids[k]: (s.n_nodes * (s.n_nodes - 1) // 2) * band_bin_count(serving_band(s.n_nodes), fs)
+                 for k, s in enumerate(trace)}
+        t0 = fc.fc_server_now_ms()
+        for i, (t, k) in enumerate(events):
+            if not saturate:
+                target = t0 + 1000.0 * t
+                while True:
+                    d = target - fc.fc_server_now_ms()
+                    if d <= 0:
+                        break
+                    time.sleep(min(d, 2.0) / 1000.0)
+            fc.fc_server_submit(sv, ids[k], pools[trace[k].n_nodes][i % (SERVING["pool"] - 1)], fc.fc_server_now_ms())
+        fc.fc_server_drain(sv, 600000)
+        res = fc.fc_server_poll(sv, len(events) + 8)
+        st1 = fc.fc_server_stats_get(sv)
+    finally:
+        fc.fc_server_destroy(sv)
+    assert len(res) == len(events) and all(r[2] == fc.FC_OK for r in res), "serving trace did not complete"
+    lat = sorted(r[4] - r[3] for r in res)
+    span_ms = max(r[4] for r in res) - t0
+    upd = sum(units[r[0]] for r in res)
+    launches = st1["launches"] - st0["launches"]
+    return {"trials": len(res), "value": upd / (span_ms / 1000.0), "unit": UNIT, "span_ms": span_ms,
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))],
+                           "max": lat[-1], "what": "trial arrival to network ready (host clock)"},
+            "ticks": launches, "trials_per_tick": (st1["batched_trials"] - st0["batched_trials"]) / max(1, launches),
+            "sessions_per_stream_launch": float(np.mean([r[5] for r in res])),
+            "hbm_used_bytes": st1["hbm_used"],
+            "windows": [s.window for s in trace], "rates_per_s": [round(s.rate_hz, 2) for s in trace]}
 
 
 def run_ours(args, w, wname):
@@ -290,16 +393,12 @@ def run_ours(args, w, wname):
     launches = fc.fc_launch_count(sess.handle) - launches0
     ktimes = fc.fc_kernel_times(sess.handle, reset=True)
     fc.fc_set_profiling(sess.handle, False)
-    total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), world, "cuda")
     ms_per_step = total_ms / steps
     lat = sorted(a.elapsed_time(b) for a, b in ev)
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
-    value = world * units / (ms_per_step / 1000.0)
+    value = whole_job_rate(units, world, ms_per_step)
 
     # roofline of the dominant kernel (streaming update)
     launches_k, tot_k = ktimes["stream"]
@@ -356,6 +455,7 @@ def run_ours(args, w, wname):
         pl = sorted(a.elapsed_time(b) for a, b in pev)
         pms = sum(pl) / len(pl)
         plain = {"value": world * units / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
+                 "contributions_per_s": world * units * W / (pms / 1000.0),
                  "latency_ms": {"p50": pl[len(pl) // 2], "p99": pl[-1]}, "steps": pst,
                  "path": "CUDA-core full-window recompute per push (FC_MODE_FULL), FP32"}
         ps.close()
@@ -379,6 +479,7 @@ def run_ours(args, w, wname):
         mms = sum(ml) / len(ml)
         tc_launches, tc_ms = mkt["herk_tc"]
         mixed = {"value": world * units / (mms / 1000.0), "unit": UNIT, "ms_per_step": mms,
+                 "contributions_per_s": world * units * W / (mms / 1000.0),
                  "latency_ms": {"p50": ml[len(ml) // 2], "p99": ml[-1]}, "steps": mst,
                  "path": "full-window recompute per push: tcgen05 BF16 Hermitian products (COH, IMAGCOHY, PLV) "
                          "+ CUDA-core non-linear sums (PLI, USPLI, WPLI, DSWPLI)",
@@ -392,6 +493,18 @@ def run_ours(args, w, wname):
                                "note": "herk_tc timing covers the operand pack and the MMA kernel"}
         ms.close()
 
+    # serving: many concurrent sessions, continuous batching vs plain FP32 one trial at a time
+    serving = None
+    if world == 1 and not args.no_serving:
+        del dev
+        torch.cuda.empty_cache()
+        serving = {"trace": SERVING["desc"], "seconds": args.serving_seconds,
+                   "batched_replay": serving_leg(fc, False, args.serving_seconds, 11),
+                   "batched_saturated": serving_leg(fc, False, args.serving_seconds, 11, saturate=True),
+                   "plain_fp32_replay": serving_leg(fc, True, args.serving_seconds, 11),
+                   "batched_path": "streaming add/subtract update, up to 32 sessions per launch of the persistent kernel",
+                   "plain_path": "one trial at a time, full-window FP32 recompute (FC_MODE_FULL), no batching"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         res = cpu_oracle_time(w, args.cpu_nodes)
@@ -399,7 +512,13 @@ def run_ours(args, w, wname):
         cpu = {"value": pb / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_nodes}-node subset of the workload, one full-window FP64 oracle "
                          f"evaluation (W={W} trials, {B} bins, 7 spectral metrics); the oracle has no "
-                         f"streaming form, so one push costs a full window", "seconds": dt}
+                         f"streaming form, so one push costs a full window", "seconds": dt,
+               "host": host_cpu()}
+        if not args.no_cpu_all_core:
+            nproc = cpu["host"]["nproc"]
+            (dta, pba), = cpu_oracle_time(w, args.cpu_nodes, threads=nproc)
+            cpu["all_core"] = {"value": pba / dta, "threads": nproc, "seconds": dta,
+                               "note": "same sample; BLAS threads = nproc (the oracle's matmuls)"}
 
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -415,7 +534,7 @@ def run_ours(args, w, wname):
                    "l2": "inputs larger than L2 (27.8 GB resident state), no flush",
                    "parallelism": f"{world} independent session(s), one per GPU"},
         "latency_ms": {"p50": p50, "p99": p99, "what": "device time from push enqueue to network ready"},
-        "plain_fp32": plain, "mixed_bf16_full_window": mixed, "roofline": roofline, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
+        "plain_fp32": plain, "mixed_bf16_full_window": mixed, "serving": serving, "roofline": roofline, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
         "clocks": clocks.summary(), "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)
@@ -438,6 +557,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-cpu-all-core", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -102,8 +102,10 @@ typedef struct {
     fc_precision precision;
     fc_mode mode;
     void* stream;     /* cudaStream_t to enqueue on; NULL: the library creates one */
-    int resum_period; /* stream mode: pushes between re-sums of the accumulators from the
-                         stored spectra (drift reset); 0 = the window length; -1 = never */
+    int resum_period; /* stream mode: every accumulator is re-summed from the stored spectra
+                         once per resum_period pushes (drift reset), spread as one slice of
+                         1/resum_period of the tile pairs per push; 0 = the window length;
+                         -1 = never */
     /* Optional device allocator (e.g. a framework's caching allocator). Both NULL: cudaMalloc. */
     void* (*dev_alloc)(size_t bytes, void* ctx);
     void (*dev_free)(void* ptr, void* ctx);
@@ -233,6 +235,79 @@ typedef enum {
 } fc_acc_field;
 fc_status fc_debug_get_accumulators(fc_session* s, fc_acc_field field, double* out,
                                     size_t out_len);
+
+/* ---- serving: many concurrent sessions, continuous batching ----------------------- */
+/*
+ * A server holds many sessions resident on one GPU and turns every arriving trial of any
+ * session into a request (the paper's online setting, Methods 2.5 / Results 3.2.3: each
+ * new trial is added to the network as it arrives, under a per-block deadline). A worker
+ * thread batches the pending trials of all sessions into one launch of the persistent
+ * streaming kernel per tick (at most one trial per session per launch, FIFO within a
+ * session, oldest arrivals first across sessions); trials arriving while a launch runs
+ * join the next one, and up to two launches are in flight, so host staging overlaps the
+ * device work. Sessions are admitted against a device-memory budget.
+ */
+typedef struct fc_server fc_server;
+
+typedef struct {
+    size_t hbm_budget; /* device bytes the server may hold for sessions (0: no limit) */
+    int max_batch;     /* sessions per launch, 1..32 (0: 32) */
+    int plain;         /* 1: comparison mode - FC_MODE_FULL FP32 sessions, one trial at a time,
+                          each a full-window recompute (no batching, no streaming sums) */
+} fc_server_config;
+
+typedef struct {
+    int session;       /* server session id */
+    long long seq;     /* index of the trial within its session's submissions (0-based) */
+    fc_status status;  /* FC_OK, or FC_ERR_NONFINITE when the trial was rejected */
+    double arrival_ms; /* the submitter's arrival stamp */
+    double done_ms;    /* when the server observed the network ready (same clock) */
+    int batch;         /* sessions in the launch that carried this trial */
+} fc_result;
+
+typedef struct {
+    long long submitted, completed, launches, batched_trials;
+    long long pair_bin_updates; /* sum of P * B over completed trials */
+    size_t hbm_used;
+    int sessions;
+} fc_server_stats;
+
+/* Milliseconds on the server's clock (steady, process-wide); use it for arrival stamps. */
+double fc_server_now_ms(void);
+
+fc_status fc_server_create(const fc_server_config* cfg, fc_server** out);
+
+/* Open a session (same settings as fc_session_create, streaming mode, FP32). Returns
+ * FC_ERR_ADMISSION without allocating when its device memory would exceed the budget;
+ * the caller may retry after closing sessions. *session_id receives the id. */
+fc_status fc_server_open(fc_server* sv, int n_nodes, int n_samples, double fs, fc_band band,
+                         fc_taper taper, uint32_t metric_mask, int window, int* session_id);
+
+/* Device bytes a session with these settings would hold (the admission figure). */
+fc_status fc_server_session_bytes(int n_nodes, int n_samples, double fs, fc_band band,
+                                  uint32_t metric_mask, int window, int plain, size_t* bytes);
+
+/* Queue one trial x[n_nodes][n_samples] (host memory, copied before return). */
+fc_status fc_server_submit(fc_server* sv, int session_id, const float* x, double arrival_ms);
+
+/* Completed trials, oldest first: up to max results into out; waits up to wait_ms for at
+ * least one (0: no wait). */
+fc_status fc_server_poll(fc_server* sv, fc_result* out, int max, int* n_out, int wait_ms);
+
+/* Wait until every submitted trial has completed (up to timeout_ms; FC_ERR_TIMEOUT after). */
+fc_status fc_server_drain(fc_server* sv, int timeout_ms);
+
+/* Current band-averaged network of a session (packed upper, host memory). */
+fc_status fc_server_get_network(fc_server* sv, int session_id, uint32_t metric, float* out,
+                                size_t out_len);
+
+/* Finish the session's queued trials and free its memory (returns it to the budget). */
+fc_status fc_server_close(fc_server* sv, int session_id);
+
+fc_status fc_server_stats_get(fc_server* sv, fc_server_stats* st);
+
+/* Stop the worker, close every session, free everything. NULL is accepted. */
+fc_status fc_server_destroy(fc_server* sv);
 
 /* ---- allocation-free entry point ------------------------------------------------ */
 

@@ -145,6 +145,20 @@ __device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2& s, flo
     e = sub2(b, sub2(s, a));
 }
 
+// Running-sum update (hi, lo) += y for one float term: DWPlusFP per lane (10 ops for 2 lanes).
+__device__ __forceinline__ void acc2_f(float2& hi, float2& lo, float2 y) {
+    float2 s, e;
+    two_sum2(hi, y, s, e);
+    fast_two_sum2(s, add2(lo, e), hi, lo);
+}
+
+// Running-sum update (hi, lo) += yh + yl for one double-word term (yh, yl) per lane.
+__device__ __forceinline__ void acc2_d(float2& hi, float2& lo, float2 yh, float2 yl) {
+    float2 s, e;
+    two_sum2(hi, yh, s, e);
+    fast_two_sum2(s, add2(add2(lo, e), yl), hi, lo);
+}
+
 // Running-sum update (hi, lo) += y1 + y2 for two float terms: two TwoSums into the
 // leading part, their errors folded into lo, one renormalization (17 ops for 2 lanes).
 __device__ __forceinline__ void acc2_ff(float2& hi, float2& lo, float2 y1, float2 y2) {

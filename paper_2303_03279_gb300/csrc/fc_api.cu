@@ -3,9 +3,10 @@
 // A push enqueues, on the session's stream and without waiting for the device:
 //   validate  -> taper + band spectrum into the ring slot of the new trial
 //   -> (first pushes) power-of-two calibration of the spectra
-//   -> per-node PSD sums -> pair update (streaming add/subtract, or a full re-sum of the
-//      window every `resum_period` pushes, or the full-window recompute in FC_MODE_FULL)
-//   -> band reduction (small sessions) -> COR / XCOR -> commit.
+//   -> per-node PSD sums -> pair update (streaming add/subtract, or the full-window
+//      recompute in FC_MODE_FULL) -> band reduction (small sessions)
+//   -> (stream mode) re-sum of one slice of the accumulators from the stored spectra
+//   -> COR / XCOR -> commit.
 // The window position lives in a device control block, so a rejected (non-finite) trial
 // is skipped by every kernel and the host never synchronizes inside a push.
 #include <algorithm>
@@ -312,27 +313,47 @@ fc_status stage_window(fc_session* s, int count, bool write_acc) {
     return FC_OK;
 }
 
+// Drift reset of the streaming sums, spread over the pushes: push r of every period of R
+// pushes (R = resum_period, default W) re-sums the tile pairs [ntp r / R, ntp (r+1) / R)
+// from the stored spectra of the window, after the streaming update of that push, so every
+// accumulator block is recomputed exactly once per R pushes and no push carries a whole
+// window's recompute. The per-node PSD sums are re-summed at r = 0.
+bool resum_on(const fc_session* s) { return s->W > 0 && s->cfg.resum_period >= 0; }
+
+int push_node_mode(const fc_session* s) { return (resum_on(s) && s->resum_phase == 0) ? 1 : 0; }
+
+fc_status stage_resum_slice(fc_session* s) {
+    if (!resum_on(s)) return FC_OK;
+    const long long R = s->cfg.resum_period > 0 ? s->cfg.resum_period : s->W;
+    const long long r = s->resum_phase % R;
+    s->resum_phase = (r + 1) % R;
+    const int tp0 = (int)(s->ntp * r / R), tp1 = (int)(s->ntp * (r + 1) / R);
+    if (tp1 <= tp0) return FC_OK;
+    PairArgs pa = pair_args(s, false, 1);
+    pa.write_acc = 1;
+    pa.finalize = 0;
+    pa.tp0 = tp0;
+    pa.tp_count = tp1 - tp0;
+    pa.groups = s->B;  // one CTA per (tile pair, bin): a slice still fills the GPU
+    pa.group_bins = 1;
+    LAUNCH(FC_K_WINDOW, launch_window_sums(pa, s->stream));
+    return FC_OK;
+}
+
 // One trial through the streaming path: x points at one [n][N] trial on the device.
 fc_status push_one_stream(fc_session* s, const float* x, bool finalize) {
     const long long nx = (long long)s->n * s->N;
     LAUNCH(FC_K_OTHER, launch_validate(x, nx, s->ctrl, s->stream));
     fc_status st = stage_spectra(s, x, 1, 0);
     if (st != FC_OK) return st;
-    const bool resum = s->W > 0 && s->cfg.resum_period >= 0 &&
-                       s->since_resum + 1 >= (s->cfg.resum_period > 0 ? s->cfg.resum_period : s->W);
-    if (resum) {
-        st = stage_window(s, 1, true);
-        if (st != FC_OK) return st;
-        s->since_resum = 0;
-    } else {
-        NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, 0, s->ctrl, 1};
-        LAUNCH(FC_K_NODE, launch_node(na, s->stream));
-        PairArgs pa = pair_args(s, true, 1);
-        pa.finalize = (finalize && (s->mask & FC_SPECTRAL_METRICS)) ? 1 : 0;
-        LAUNCH(FC_K_STREAM, launch_stream_update(pa, s->stream));
-        if (pa.finalize && pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
-        s->since_resum++;
-    }
+    NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, push_node_mode(s), s->ctrl, 1};
+    LAUNCH(FC_K_NODE, launch_node(na, s->stream));
+    PairArgs pa = pair_args(s, true, 1);
+    pa.finalize = (finalize && (s->mask & FC_SPECTRAL_METRICS)) ? 1 : 0;
+    LAUNCH(FC_K_STREAM, launch_stream_update(pa, s->stream));
+    if (pa.finalize && pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
+    st = stage_resum_slice(s);
+    if (st != FC_OK) return st;
     st = stage_time_metrics(s, x, 1, 0, 0);
     if (st != FC_OK) return st;
     CommitArgs ca{s->ctrl, 1};
@@ -356,7 +377,6 @@ fc_status push_bulk(fc_session* s, const float* x, int count, bool write_acc) {
     CommitArgs ca{s->ctrl, count};
     LAUNCH(FC_K_OTHER, launch_commit(ca, s->stream));
     s->enqueued += count;
-    if (write_acc) s->since_resum = 0;
     return FC_OK;
 }
 
@@ -394,6 +414,78 @@ fc_status check_latched(fc_session* s, FcCtrl* h) {
 }  // namespace
 
 void fc_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
+
+// ------------------------------------------------- streaming push in pieces (serving)
+bool fc_push_needs_single(fc_session* s) {
+    return !s->calibrated || s->time_mask != 0 || s->cfg.mode != FC_MODE_STREAM;
+}
+
+fc_status fc_push_single(fc_session* s, const float* xdev) {
+    if (s->cfg.mode == FC_MODE_FULL) return push_bulk(s, xdev, 1, false);
+    return push_one_stream(s, xdev, true);
+}
+
+fc_status fc_push_stage_pre(fc_session* s, const float* xdev) {
+    const long long nx = (long long)s->n * s->N;
+    LAUNCH(FC_K_OTHER, launch_validate(xdev, nx, s->ctrl, s->stream));
+    fc_status st = stage_spectra(s, xdev, 1, 0);
+    if (st != FC_OK) return st;
+    NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, push_node_mode(s), s->ctrl, 1};
+    LAUNCH(FC_K_NODE, launch_node(na, s->stream));
+    return FC_OK;
+}
+
+PairArgs fc_push_stream_args(fc_session* s) {
+    PairArgs pa = pair_args(s, true, 1);
+    pa.finalize = (s->mask & FC_SPECTRAL_METRICS) ? 1 : 0;
+    return pa;
+}
+
+fc_status fc_push_stage_post(fc_session* s) {
+    PairArgs pa = fc_push_stream_args(s);
+    if (pa.finalize && pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
+    fc_status st = stage_resum_slice(s);
+    if (st != FC_OK) return st;
+    CommitArgs ca{s->ctrl, 1};
+    LAUNCH(FC_K_OTHER, launch_commit(ca, s->stream));
+    s->enqueued += 1;
+    return FC_OK;
+}
+
+void fc_count_launch(fc_session* s) { s->launches++; }
+
+// Device bytes fc_session_create would allocate for these settings (mirrors its allocations).
+size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode mode) {
+    const size_t nt = (n + FC_T - 1) / FC_T, ntp = nt * (nt + 1) / 2;
+    const size_t P = (size_t)n * (n - 1) / 2;
+    const size_t slots = mode == FC_MODE_FULL ? W : (W > 0 ? W + 1 : 1);
+    size_t b = 256 + (size_t)N * B * 8 + slots * B * n * 8 + (size_t)B * n * 12 + ntp * 4 + 9 * P * 4 +
+               (size_t)n * N * 4;
+    if (mode == FC_MODE_STREAM) b += ntp * B * FC_BLOCK_WORDS * 4;
+    const int groups = std::min(B, std::max(1, (int)((152 * 4 + ntp - 1) / ntp)));
+    if (groups > 1) b += (size_t)groups * 7 * P * 4;
+    if (mask & FC_COR) b += slots * n * N * 4 + 2 * P * 4;
+    if (mask & FC_XCOR) {
+        size_t L = 1;
+        while (L < (size_t)(2 * N - 1)) L *= 2;
+        if (L < 64) L = 64;
+        b += L / 2 * 8 + slots * n * (L / 2 + 1) * 8 + slots * n * 4 + slots * P * 4 + P * 4 + 2 * P * 4;
+    }
+    return b;
+}
+
+int fc_band_bins(double fs, fc_band band, int* first) {
+    int f0 = -1, B = 0;
+    for (int k = 0; k <= band.nfft / 2; ++k) {
+        const double kf = (double)k * fs;
+        if (kf >= band.f_lo * band.nfft && kf < band.f_hi * band.nfft) {
+            if (f0 < 0) f0 = k;
+            ++B;
+        }
+    }
+    if (first) *first = f0;
+    return B;
+}
 
 // ====================================================================== public API
 extern "C" {

@@ -82,7 +82,7 @@ struct fc_session {
 
     // host mirror of the enqueued push count (scheduling only; the device count rules)
     long long enqueued;
-    long long since_resum;
+    long long resum_phase;  // next slice of the sliced re-sum (0 .. period - 1)
     bool calibrated;        // the device prescale is known to be set
 
     float* dense_scratch;   // n x n staging for dense host outputs
@@ -168,11 +168,22 @@ struct PairArgs {
     int finalize;      // write networks / partials
     int update;        // stream kernel: 1 = add/subtract the trials, 0 = finalize only
     int write_acc;     // window kernel: store accumulators (re-sum)
+    int tp0, tp_count; // window kernel: tile pairs tp0 .. tp0 + tp_count - 1 (tp_count 0: all)
     int count;         // trials pushed by this call (window end = pushed + count)
     int grid_ctas;     // persistent grid size of the streaming kernel
     const FcCtrl* ctrl;
 };
 cudaError_t launch_stream_update(const PairArgs& a, cudaStream_t st);
+
+// A batch of sessions updated by one launch of the streaming kernel (passed by value as
+// the kernel's parameter block; units of session s are [unit_prefix[s], unit_prefix[s+1])).
+#define FC_MAX_BATCH 32
+struct StreamBatch {
+    int nsess;
+    int unit_prefix[FC_MAX_BATCH + 1];
+    PairArgs a[FC_MAX_BATCH];
+};
+cudaError_t launch_stream_batch(const StreamBatch& b, int grid_ctas, cudaStream_t st);
 cudaError_t launch_window_sums(const PairArgs& a, cudaStream_t st);
 cudaError_t launch_band_reduce(const PairArgs& a, cudaStream_t st);
 cudaError_t launch_bins_from_acc(const PairArgs& a, int metric_index, float* out, cudaStream_t st);
@@ -248,6 +259,20 @@ cudaError_t launch_xcor_update(const XcorArgs& a, cudaStream_t st);
 
 // Set the thread-local message returned by fc_last_error() (for entry points outside fc_api.cu).
 void fc_internal_set_error(const char* msg);
+
+// A streaming push split into pieces, for the serving engine (fc_server.cu): the trial is
+// already in s->x_stage (device). pre: validate, spectrum, per-node sums; the pair update
+// is batched across sessions (launch_stream_batch with fc_push_stream_args); post: band
+// reduction (if any), commit, bookkeeping. Sessions that are uncalibrated, due for a
+// re-sum, hold COR/XCOR or are in full mode take fc_push_single instead.
+bool fc_push_needs_single(fc_session* s);
+fc_status fc_push_single(fc_session* s, const float* xdev);
+fc_status fc_push_stage_pre(fc_session* s, const float* xdev);
+PairArgs fc_push_stream_args(fc_session* s);
+fc_status fc_push_stage_post(fc_session* s);
+void fc_count_launch(fc_session* s);
+size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode mode);
+int fc_band_bins(double fs, fc_band band, int* first);
 
 cudaError_t launch_expand_dense(const float* packed, float* dense, int n, int antisym,
                                 cudaStream_t st);

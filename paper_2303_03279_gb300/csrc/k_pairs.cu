@@ -48,8 +48,11 @@ __global__ void k_node(NodeArgs a) {
 }
 
 // ---------------------------------------------------------------- full-window sums
-constexpr int WK = 16;  // trials staged per chunk
+constexpr int WK = 16;     // trials staged per chunk
+constexpr int NODE_W = 5;  // staged words per node: a, b, Re u, Im u, tiny flag
 
+// Thread: row node li of tile ta against columns lj0 .. lj0 + 3 of tile tb, as two packed
+// column pairs (FP32x2 lanes), double-float running sums per lane (acc2_f / acc2_d).
 __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, float* bins_out) {
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
@@ -57,7 +60,7 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
     const int K = wf.K;
     const KConst kc = make_kconst(K);
 
-    const int tp = blockIdx.x;
+    const int tp = a.tp0 + blockIdx.x;
     const int g = blockIdx.y;
     const int f0 = g * a.group_bins;
     const int f1 = min(a.B, f0 + a.group_bins);
@@ -67,8 +70,9 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
     const unsigned vmask = pair_mask(ta, tb, li, lj0, a.n);
     const int gi = ta * FC_T + li, gj0 = tb * FC_T + lj0;
 
-    __shared__ float2 sx[WK][2 * FC_T];
-    __shared__ float2 su[WK][2 * FC_T];
+    // [trial][side: 0 row tile, 1 column tile][word][node], planar so that two adjacent
+    // column nodes load as one packed operand
+    __shared__ __align__(16) float sn[WK][2][NODE_W][FC_T];
     __shared__ float sinv[2][FC_T];
 
     float band[7][4];
@@ -78,62 +82,82 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
         for (int q = 0; q < 4; ++q) band[m][q] = 0.f;
 
     for (int f = f0; f < f1; ++f) {
-        df32 v[4][FC_NFIELD];
-        int s[4];
+        float2 vh[2][FC_NFIELD], vl[2][FC_NFIELD];
+        int s[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            s[q] = 0;
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int k = 0; k < FC_NFIELD; ++k) v[q][k] = df_make(0.f, 0.f);
-        }
+            for (int k = 0; k < FC_NFIELD; ++k) vh[h][k] = vl[h][k] = make_float2(0.f, 0.f);
         if (tid < 64) {
             const int w = tid >> 5, l = tid & 31;
             const int node = (w ? tb : ta) * FC_T + l;
             sinv[w][l] = node < a.n ? a.inv_psd[(size_t)f * a.n + node] : 0.f;
         }
         for (int k0 = 0; k0 < K; k0 += WK) {
-            const int kc = min(WK, K - k0);
+            const int kn = min(WK, K - k0);
             __syncthreads();
-            for (int e = tid; e < kc * 2 * FC_T; e += 256) {
-                const int kk = e / (2 * FC_T), l = e % (2 * FC_T);
-                const int node = (l < FC_T ? ta * FC_T + l : tb * FC_T + l - FC_T);
-                const long long trial = wf.start + k0 + kk;
+            for (int e = tid; e < WK * 2 * FC_T; e += 256) {
+                const int kk = e / (2 * FC_T), side = (e / FC_T) & 1, l = e % FC_T;
+                const int node = (side ? tb : ta) * FC_T + l;
                 float2 X = make_float2(0.f, 0.f);
-                if (node < a.n) X = a.ring[((size_t)(trial % a.slots) * a.B + f) * a.n + node];
-                sx[kk][l] = X;
-                su[kk][l] = phasor_of(X);
+                if (kk < kn && node < a.n)
+                    X = a.ring[((size_t)((wf.start + k0 + kk) % a.slots) * a.B + f) * a.n + node];
+                const float2 u = phasor_of(X);
+                sn[kk][side][0][l] = X.x;
+                sn[kk][side][1][l] = X.y;
+                sn[kk][side][2][l] = u.x;
+                sn[kk][side][3][l] = u.y;
+                sn[kk][side][4][l] = node_tiny(X) ? 1.f : 0.f;
             }
             __syncthreads();
             if (vmask) {
-                for (int kk = 0; kk < kc; ++kk) {
-                    const float2 xi = sx[kk][li], ui = su[kk][li];
+                for (int kk = 0; kk < kn; ++kk) {
+                    const float (*r)[FC_T] = sn[kk][0];
+                    const float (*cl)[FC_T] = sn[kk][1];
+                    const RowConst rc = row_const(r[0][li], r[1][li], r[2][li], r[3][li], r[4][li] != 0.f);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float2 xj = sx[kk][FC_T + lj0 + q];
-                        const PairTerms tt = pair_terms(xi, xj, ui, su[kk][FC_T + lj0 + q],
-                                                        node_tiny(xi) || node_tiny(xj));
-                        v[q][0] = df_add_f(v[q][0], tt.re);
-                        v[q][1] = df_add_f(v[q][1], tt.im);
-                        v[q][2] = df_add_f(v[q][2], tt.ure);
-                        v[q][3] = df_add_f(v[q][3], tt.uim);
-                        v[q][4] = df_add_f(v[q][4], fabsf(tt.im));
-                        v[q][5] = df_add_df(v[q][5], df_sqr_f(tt.im));
-                        s[q] += tt.sgn;
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = lj0 + 2 * h;
+                        const float2 tj = *reinterpret_cast<const float2*>(&cl[4][j]);
+                        const PairTerms2 t = pair_terms2(rc, *reinterpret_cast<const float2*>(&cl[0][j]),
+                                                         *reinterpret_cast<const float2*>(&cl[1][j]),
+                                                         *reinterpret_cast<const float2*>(&cl[2][j]),
+                                                         *reinterpret_cast<const float2*>(&cl[3][j]), tj.x != 0.f,
+                                                         tj.y != 0.f);
+                        acc2_f(vh[h][0], vl[h][0], t.re);
+                        acc2_f(vh[h][1], vl[h][1], t.im);
+                        acc2_f(vh[h][2], vl[h][2], t.ure);
+                        acc2_f(vh[h][3], vl[h][3], t.uim);
+                        acc2_f(vh[h][4], vl[h][4], make_float2(fabsf(t.im.x), fabsf(t.im.y)));
+                        // im^2 as an exact two-product, scalar: the product feeds additions
+                        float2 p2, e2;
+                        two_prod(t.im.x, t.im.x, p2.x, e2.x);
+                        two_prod(t.im.y, t.im.y, p2.y, e2.y);
+                        acc2_d(vh[h][5], vl[h][5], p2, e2);
+                        s[2 * h] += t.s0;
+                        s[2 * h + 1] += t.s1;
                     }
                 }
             }
         }
         __syncthreads();  // sinv visible
         if (vmask) {
+            df32 v[4][FC_NFIELD];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < FC_NFIELD; ++k)
+                    v[q][k] = (q & 1) ? df_make(vh[q >> 1][k].y, vl[q >> 1][k].y)
+                                      : df_make(vh[q >> 1][k].x, vl[q >> 1][k].x);
             if (a.write_acc) {
                 float* blk = a.acc + ((size_t)tp * a.B + f) * FC_BLOCK_WORDS;
                 const int w0 = li * FC_T + lj0;
 #pragma unroll
                 for (int k = 0; k < FC_NFIELD; ++k) {
-                    float4 h = make_float4(v[0][k].hi, v[1][k].hi, v[2][k].hi, v[3][k].hi);
-                    float4 l = make_float4(v[0][k].lo, v[1][k].lo, v[2][k].lo, v[3][k].lo);
-                    __stcs(reinterpret_cast<float4*>(blk + (2 * k) * FC_TT + w0), h);
-                    __stcs(reinterpret_cast<float4*>(blk + (2 * k + 1) * FC_TT + w0), l);
+                    float4 hq = make_float4(v[0][k].hi, v[1][k].hi, v[2][k].hi, v[3][k].hi);
+                    float4 lq = make_float4(v[0][k].lo, v[1][k].lo, v[2][k].lo, v[3][k].lo);
+                    __stcs(reinterpret_cast<float4*>(blk + (2 * k) * FC_TT + w0), hq);
+                    __stcs(reinterpret_cast<float4*>(blk + (2 * k + 1) * FC_TT + w0), lq);
                 }
                 __stcs(reinterpret_cast<int4*>(blk + 12 * FC_TT + w0), make_int4(s[0], s[1], s[2], s[3]));
             }
@@ -243,7 +267,8 @@ cudaError_t launch_node(const NodeArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_window_sums(const PairArgs& a, cudaStream_t st) {
-    dim3 grid(a.ntp, a.groups);
+    if (a.tp0 < 0 || a.tp_count < 0 || a.tp0 + (a.tp_count ? a.tp_count : a.ntp) > a.ntp) return cudaErrorInvalidValue;
+    dim3 grid(a.tp_count ? a.tp_count : a.ntp, a.groups);
     k_window<<<grid, 256, 0, st>>>(a, 0, nullptr);
     return cudaGetLastError();
 }
@@ -253,6 +278,8 @@ cudaError_t launch_bins_window(const PairArgs& a, int metric_index, float* out, 
     PairArgs b = a;
     b.finalize = 0;
     b.write_acc = 0;
+    b.tp0 = 0;
+    b.tp_count = 0;
     k_window<<<grid, 256, 0, st>>>(b, metric_index, out);
     return cudaGetLastError();
 }

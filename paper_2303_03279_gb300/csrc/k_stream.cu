@@ -76,27 +76,44 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 struct Step {
-    int u;  // unit index: tile pair * groups + bin group
-    int f;  // bin
+    int u;   // unit index over the whole batch
+    int f;   // bin
+    int s;   // session of the unit
+    int lu;  // unit index within its session: tile pair * groups + bin group
 };
 
-__global__ void __launch_bounds__(256, 2) k_stream(PairArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    FcCtrl* c = const_cast<FcCtrl*>(a.ctrl);
-    if (c->bad) return;
-    const int units = a.ntp * a.groups;
-    if ((int)blockIdx.x >= units) return;
-
-    // window facts: t = newest trial after this call (count 1: being added; 0: finalize only)
+// Facts of one session's push, read from its control block: window position, ring slots
+// of the trial added and of the trial leaving, window length.
+struct SessFacts {
+    bool skip;  // the push was rejected (non-finite trial) or the window is empty
+    bool upd, sub;
+    int slot_new, slot_old;
+    KConst kc;
+};
+__device__ __forceinline__ SessFacts facts_of(const PairArgs& a) {
+    SessFacts F;
+    const FcCtrl* c = a.ctrl;
+    // t = newest trial after this call (count 1: being added; 0: finalize only)
     const long long t = c->pushed + a.count - 1;
-    const bool upd = a.update != 0;
-    const int slot_new = upd ? (int)(t % a.slots) : 0;
-    const bool sub = upd && (a.W > 0) && (t >= a.W);
-    const int slot_old = sub ? (int)((t - a.W) % a.slots) : 0;
+    F.upd = a.update != 0;
+    F.slot_new = F.upd ? (int)(t % a.slots) : 0;
+    F.sub = F.upd && (a.W > 0) && (t >= a.W);
+    F.slot_old = F.sub ? (int)((t - a.W) % a.slots) : 0;
     const int K = (a.W > 0 && t + 1 > a.W) ? a.W : (int)(t + 1);
-    if (K <= 0) return;
-    const KConst kc = make_kconst(K);
-    const bool one_group = a.groups == 1;
+    F.skip = c->bad != 0 || K <= 0;
+    F.kc = make_kconst(K > 0 ? K : 1);
+    return F;
+}
+
+// One launch updates every session of the batch: the units of all sessions form one list
+// (batch.unit_prefix), walked round-robin by the persistent CTAs. MULTI = false is the
+// single-session instantiation: every parameter read has a constant offset.
+template <bool MULTI>
+__global__ void __launch_bounds__(256, 2) k_stream(const StreamBatch batch) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    auto sess = [&](int s) -> const PairArgs& { return batch.a[MULTI ? s : 0]; };
+    const int units = MULTI ? batch.unit_prefix[batch.nsess] : batch.unit_prefix[1];
+    if ((int)blockIdx.x >= units) return;
 
     float* buf[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem + BLK_BYTES)};
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + OFF_MBAR);
@@ -106,34 +123,54 @@ __global__ void __launch_bounds__(256, 2) k_stream(PairArgs a) {
     const int li = tid >> 3, lj0 = (tid & 7) * 4;
     const int w0 = li * FC_T + lj0;
 
-    auto unit_tp = [&](int u) { return one_group ? u : u / a.groups; };
-    auto unit_first_bin = [&](int u) { return one_group ? 0 : (u % a.groups) * a.group_bins; };
-    auto unit_end_bin = [&](int u) { return one_group ? a.B : min(a.B, (u % a.groups) * a.group_bins + a.group_bins); };
-    auto next_step = [&](Step s) -> Step {
-        if (s.f + 1 < unit_end_bin(s.u)) return Step{s.u, s.f + 1};
-        const int nu = s.u + (int)gridDim.x;
-        return Step{nu, nu < units ? unit_first_bin(nu) : 0};
+    auto make_step = [&](int u) -> Step {  // first bin of unit u
+        Step r{u, 0, 0, 0};
+        if (u >= units) return r;
+        if (MULTI) {
+            while (r.s + 1 < batch.nsess && u >= batch.unit_prefix[r.s + 1]) ++r.s;
+            r.lu = u - batch.unit_prefix[r.s];
+        } else {
+            r.lu = u;
+        }
+        const PairArgs& A = sess(r.s);
+        r.f = A.groups == 1 ? 0 : (r.lu % A.groups) * A.group_bins;
+        return r;
     };
-    auto block_ptr = [&](Step s) -> float* {
-        return a.acc + ((size_t)unit_tp(s.u) * a.B + s.f) * FC_BLOCK_WORDS;
+    auto unit_tp = [&](const Step& s) {
+        const PairArgs& A = sess(s.s);
+        return A.groups == 1 ? s.lu : s.lu / A.groups;
+    };
+    auto next_step = [&](Step s) -> Step {
+        const PairArgs& A = sess(s.s);
+        const int end = A.groups == 1 ? A.B : min(A.B, (s.lu % A.groups) * A.group_bins + A.group_bins);
+        if (s.f + 1 < end) {
+            s.f += 1;
+            return s;
+        }
+        return make_step(s.u + (int)gridDim.x);
+    };
+    auto block_ptr = [&](const Step& s) -> float* {
+        const PairArgs& A = sess(s.s);
+        return A.acc + ((size_t)unit_tp(s) * A.B + s.f) * FC_BLOCK_WORDS;
     };
     // spectra (threads 0..127: set w = tid/32, node l = tid%32) or 1/sqrt(PSD)
     // (threads 128..191) of step s
-    auto fetch = [&](Step s, float2& X, float& inv) {
-        const int tp = unit_tp(s.u);
-        const int ta = a.tile_a[tp], tb = a.tile_b[tp];
+    auto fetch = [&](const Step& s, const SessFacts& F, float2& X, float& inv) {
+        const PairArgs& A = sess(s.s);
+        const int tp = unit_tp(s);
+        const int ta = A.tile_a[tp], tb = A.tile_b[tp];
         if (tid < 128) {
             const int w = tid >> 5, l = tid & 31;
             const int node = ((w & 1) ? tb : ta) * FC_T + l;
             const bool old = w >= 2;
             X = make_float2(0.f, 0.f);
-            if (upd && node < a.n && (!old || sub))
-                X = a.ring[((size_t)(old ? slot_old : slot_new) * a.B + s.f) * a.n + node];
+            if (F.upd && !F.skip && node < A.n && (!old || F.sub))
+                X = A.ring[((size_t)(old ? F.slot_old : F.slot_new) * A.B + s.f) * A.n + node];
             if (w == 3) X = make_float2(-X.x, -X.y);  // leaving trial, column side: negated
         } else if (tid < 192) {
             const int w = (tid - 128) >> 5, l = tid & 31;
             const int node = (w ? tb : ta) * FC_T + l;
-            inv = node < a.n ? a.inv_psd[(size_t)s.f * a.n + node] : 0.f;
+            inv = node < A.n ? A.inv_psd[(size_t)s.f * A.n + node] : 0.f;
         }
     };
     auto stage = [&](int st, float2 X, float inv) {
@@ -152,7 +189,8 @@ __global__ void __launch_bounds__(256, 2) k_stream(PairArgs a) {
         }
     };
 
-    Step cur{(int)blockIdx.x, unit_first_bin((int)blockIdx.x)};
+    Step cur = make_step((int)blockIdx.x);
+    SessFacts Fc = facts_of(sess(cur.s));
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
@@ -171,7 +209,7 @@ __global__ void __launch_bounds__(256, 2) k_stream(PairArgs a) {
     {
         float2 X = make_float2(0.f, 0.f);
         float inv = 0.f;
-        fetch(cur, X, inv);
+        fetch(cur, Fc, X, inv);
         stage(0, X, inv);
     }
     __syncthreads();
@@ -184,15 +222,19 @@ __global__ void __launch_bounds__(256, 2) k_stream(PairArgs a) {
     while (cur.u < units) {
         const int st = it & 1;
         const uint32_t parity = (it >> 1) & 1;
+        const PairArgs& a = sess(cur.s);
+        const bool upd = Fc.upd, sub = Fc.sub;
+        const KConst& kc = Fc.kc;
         const Step nxt = next_step(cur);
+        const SessFacts Fn = (nxt.u < units && nxt.s != cur.s) ? facts_of(sess(nxt.s)) : Fc;
         float2 pX = make_float2(0.f, 0.f);
         float pinv = 0.f;
-        if (nxt.u < units) fetch(nxt, pX, pinv);  // latency hidden behind this bin's work
+        if (nxt.u < units) fetch(nxt, Fn, pX, pinv);  // latency hidden behind this bin's work
 
         const bool arrived = mbar_wait_bounded(&mbar[st], parity);
-        const int tp = unit_tp(cur.u);
+        const int tp = unit_tp(cur);
         const int ta = a.tile_a[tp], tb = a.tile_b[tp];
-        const unsigned vmask = arrived ? pair_mask(ta, tb, li, lj0, a.n) : 0u;
+        const unsigned vmask = (arrived && !Fc.skip) ? pair_mask(ta, tb, li, lj0, a.n) : 0u;
         if (vmask) {
             const float* blk = buf[st];
             const float* g = stg + st * STAGE_WORDS;
@@ -306,7 +348,7 @@ __global__ void __launch_bounds__(256, 2) k_stream(PairArgs a) {
                     bq[m][0] = band[m][0].x; bq[m][1] = band[m][0].y;
                     bq[m][2] = band[m][1].x; bq[m][3] = band[m][1].y;
                 }
-                write_band(a, one_group ? 0 : cur.u % a.groups, bq, ta * FC_T + li, tb * FC_T + lj0, vmask, 0);
+                write_band(a, a.groups == 1 ? 0 : cur.lu % a.groups, bq, ta * FC_T + li, tb * FC_T + lj0, vmask, 0);
             }
 #pragma unroll
             for (int m = 0; m < 7; ++m) band[m][0] = band[m][1] = make_float2(0.f, 0.f);
@@ -314,7 +356,7 @@ __global__ void __launch_bounds__(256, 2) k_stream(PairArgs a) {
         if (nxt.u < units) stage(st ^ 1, pX, pinv);
         const int timed_out = __syncthreads_or(arrived ? 0 : 1);
         if (timed_out) {
-            if (tid == 0) atomicOr(&c->timeout, 1);
+            if (tid == 0) atomicOr(&const_cast<FcCtrl*>(a.ctrl)->timeout, 1);
             // let the other stage's copy land before leaving (bounded)
             mbar_wait_bounded(&mbar[st ^ 1], ((it + 1) >> 1) & 1);
             return;
@@ -328,17 +370,34 @@ __global__ void __launch_bounds__(256, 2) k_stream(PairArgs a) {
             }
         }
         cur = nxt;
+        Fc = Fn;
         ++it;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_stream_update(const PairArgs& a, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+cudaError_t launch_stream_batch(const StreamBatch& b, int grid_ctas, cudaStream_t st) {
+    if (b.nsess < 1 || b.nsess > FC_MAX_BATCH) return cudaErrorInvalidValue;
+    const bool multi = b.nsess > 1;
+    cudaError_t e = multi ? cudaFuncSetAttribute(k_stream<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
+                          : cudaFuncSetAttribute(k_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    const int units = a.ntp * a.groups;
-    const int ctas = units < a.grid_ctas ? units : a.grid_ctas;
-    k_stream<<<ctas, 256, SMEM_BYTES, st>>>(a);
+    const int units = b.unit_prefix[b.nsess];
+    if (units <= 0) return cudaSuccess;
+    const int ctas = units < grid_ctas ? units : grid_ctas;
+    if (multi)
+        k_stream<true><<<ctas, 256, SMEM_BYTES, st>>>(b);
+    else
+        k_stream<false><<<ctas, 256, SMEM_BYTES, st>>>(b);
     return cudaGetLastError();
+}
+
+cudaError_t launch_stream_update(const PairArgs& a, cudaStream_t st) {
+    StreamBatch b;
+    b.nsess = 1;
+    b.unit_prefix[0] = 0;
+    b.unit_prefix[1] = a.ntp * a.groups;
+    b.a[0] = a;
+    return launch_stream_batch(b, a.grid_ctas, st);
 }

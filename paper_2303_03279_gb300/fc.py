@@ -70,6 +70,21 @@ class fc_kernel_time(C.Structure):
     _fields_ = [("launches", C.c_int), ("total_ms", C.c_double)]
 
 
+class fc_server_config(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_batch", C.c_int), ("plain", C.c_int)]
+
+
+class fc_result(C.Structure):
+    _fields_ = [("session", C.c_int), ("seq", C.c_longlong), ("status", C.c_int), ("arrival_ms", C.c_double),
+                ("done_ms", C.c_double), ("batch", C.c_int)]
+
+
+class fc_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("launches", C.c_longlong),
+                ("batched_trials", C.c_longlong), ("pair_bin_updates", C.c_longlong), ("hbm_used", C.c_size_t),
+                ("sessions", C.c_int)]
+
+
 class FcError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"fc status {status}: {message}")
@@ -103,6 +118,19 @@ _SIGNATURES = [
     ("fc_debug_get_accumulators", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
     ("fc_window_networks_noalloc", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_void_p,
                                              C.c_size_t, C.c_void_p]),
+    ("fc_server_now_ms", C.c_double, []),
+    ("fc_server_create", C.c_int, [C.POINTER(fc_server_config), C.POINTER(C.c_void_p)]),
+    ("fc_server_open", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, fc_band, C.c_int, C.c_uint32, C.c_int,
+                                 C.POINTER(C.c_int)]),
+    ("fc_server_session_bytes", C.c_int, [C.c_int, C.c_int, C.c_double, fc_band, C.c_uint32, C.c_int, C.c_int,
+                                          C.POINTER(C.c_size_t)]),
+    ("fc_server_submit", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_double]),
+    ("fc_server_poll", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
+    ("fc_server_drain", C.c_int, [C.c_void_p, C.c_int]),
+    ("fc_server_get_network", C.c_int, [C.c_void_p, C.c_int, C.c_uint32, C.c_void_p, C.c_size_t]),
+    ("fc_server_close", C.c_int, [C.c_void_p, C.c_int]),
+    ("fc_server_stats_get", C.c_int, [C.c_void_p, C.POINTER(fc_server_stats)]),
+    ("fc_server_destroy", C.c_int, [C.c_void_p]),
 ]
 
 
@@ -274,6 +302,71 @@ def fc_window_networks_noalloc(spectra, n_trials: int, n_bins: int, n_nodes: int
         raise ValueError("spectra and out must be CUDA tensors")
     _check(load().fc_window_networks_noalloc(p_in, int(n_trials), int(n_bins), int(n_nodes), int(metric_mask),
                                              p_out, nel, C.c_void_p(int(stream) if stream else 0)))
+
+
+def fc_server_now_ms() -> float:
+    return float(load().fc_server_now_ms())
+
+
+def fc_server_create(hbm_budget: int = 0, max_batch: int = 0, plain: bool = False):
+    cfg = fc_server_config(int(hbm_budget), int(max_batch), 1 if plain else 0)
+    out = C.c_void_p()
+    _check(load().fc_server_create(C.byref(cfg), C.byref(out)))
+    return out
+
+
+def fc_server_open(sv, n_nodes, n_samples, fs, band, taper, metric_mask, window) -> int:
+    if isinstance(taper, str):
+        taper = TAPERS[taper]
+    sid = C.c_int(0)
+    _check(_LIB.fc_server_open(sv, int(n_nodes), int(n_samples), float(fs), fc_band(float(band[0]), float(band[1]),
+                               int(band[2])), int(taper), int(metric_mask), int(window), C.byref(sid)))
+    return sid.value
+
+
+def fc_server_session_bytes(n_nodes, n_samples, fs, band, metric_mask, window, plain=False) -> int:
+    out = C.c_size_t(0)
+    _check(load().fc_server_session_bytes(int(n_nodes), int(n_samples), float(fs),
+                                          fc_band(float(band[0]), float(band[1]), int(band[2])), int(metric_mask),
+                                          int(window), 1 if plain else 0, C.byref(out)))
+    return int(out.value)
+
+
+def fc_server_submit(sv, session_id: int, x, arrival_ms: float):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    _check(_LIB.fc_server_submit(sv, int(session_id), C.c_void_p(x.ctypes.data), float(arrival_ms)))
+
+
+def fc_server_poll(sv, max_results: int = 256, wait_ms: int = 0):
+    arr = (fc_result * max_results)()
+    n = C.c_int(0)
+    _check(_LIB.fc_server_poll(sv, arr, int(max_results), C.byref(n), int(wait_ms)))
+    return [(r.session, r.seq, r.status, r.arrival_ms, r.done_ms, r.batch) for r in arr[: n.value]]
+
+
+def fc_server_drain(sv, timeout_ms: int = 60000):
+    _check(_LIB.fc_server_drain(sv, int(timeout_ms)))
+
+
+def fc_server_get_network(sv, session_id: int, metric: int, out):
+    p, dev, nel = _ptr(out, np.float32)
+    if dev:
+        raise ValueError("host output expected")
+    _check(_LIB.fc_server_get_network(sv, int(session_id), int(metric), p, nel))
+
+
+def fc_server_close(sv, session_id: int):
+    _check(_LIB.fc_server_close(sv, int(session_id)))
+
+
+def fc_server_stats_get(sv) -> dict:
+    st = fc_server_stats()
+    _check(_LIB.fc_server_stats_get(sv, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in fc_server_stats._fields_}
+
+
+def fc_server_destroy(sv):
+    _check(load().fc_server_destroy(sv))
 
 
 # ----------------------------------------------------------------- convenience

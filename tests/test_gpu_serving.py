@@ -1,0 +1,126 @@
+"""Serving: many sessions on one GPU, continuous batching, admission by device-memory budget.
+
+* Each session's networks are bit-identical when it is served alone and when its trials
+  share launches with other sessions (the batched kernel computes every pair with the same
+  arithmetic), and agree with a standalone session fed the same trials (1e-5).
+* Plain mode (full-window FP32 recompute per trial, no batching) gives the same networks.
+* A session whose device memory would exceed the budget is refused with FC_ERR_ADMISSION
+  and admitted once another session has closed.
+"""
+
+import numpy as np
+import pytest
+
+from synth import white_trials
+from _fc_helpers import assert_close
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2303_03279_gb300 import fc  # noqa: E402
+
+SPECTRAL = ("COH", "IMAGCOHY", "PLV", "PLI", "USPLI", "WPLI", "DSWPLI")
+CONFIGS = [  # n, N, fs, band, W, trials
+    (60, 200, 500.0, (1.0, 50.0, 256), 8, 14),
+    (128, 200, 500.0, (4.0, 44.0, 250), 12, 17),
+    (70, 128, 256.0, (8.0, 40.0, 128), 5, 11),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fc.load()
+
+
+def _trials():
+    return [white_trials(40 + k, t, n, N) for k, (n, N, fs, band, W, t) in enumerate(CONFIGS)]
+
+
+def _serve(which, interleave=True, plain=False, max_batch=0):
+    """Run the listed configs through one server; returns {config index: {metric: network}}."""
+    xs = _trials()
+    sv = fc.fc_server_create(max_batch=max_batch, plain=plain)
+    try:
+        ids = {}
+        for k in which:
+            n, N, fs, band, W, _ = CONFIGS[k]
+            ids[k] = fc.fc_server_open(sv, n, N, fs, band, "hann", fc.FC_SPECTRAL_METRICS, W)
+        # arrival order: round-robin across sessions (mixed) or session after session
+        order = []
+        if interleave:
+            for t in range(max(CONFIGS[k][5] for k in which)):
+                order += [(k, t) for k in which if t < CONFIGS[k][5]]
+        else:
+            order = [(k, t) for k in which for t in range(CONFIGS[k][5])]
+        for k, t in order:
+            fc.fc_server_submit(sv, ids[k], xs[k][t], fc.fc_server_now_ms())
+        fc.fc_server_drain(sv, 120000)
+        res = fc.fc_server_poll(sv, 4096)
+        assert len(res) == sum(CONFIGS[k][5] for k in which)
+        for sid, seq, status, arr, done, batch in res:
+            assert status == fc.FC_OK and done >= arr and batch >= 1
+        out = {}
+        for k in which:
+            n = CONFIGS[k][0]
+            P = n * (n - 1) // 2
+            nets = {}
+            for m in SPECTRAL:
+                buf = np.empty(P, np.float32)
+                fc.fc_server_get_network(sv, ids[k], fc.METRIC_BITS[m], buf)
+                nets[m] = buf
+            out[k] = nets
+        stats = fc.fc_server_stats_get(sv)
+        return out, stats, res
+    finally:
+        fc.fc_server_destroy(sv)
+
+
+def test_same_alone_and_in_the_mix():
+    mixed, stats, res = _serve([0, 1, 2], interleave=True)
+    assert max(r[5] for r in res) > 1  # some launches carried several sessions
+    assert stats["batched_trials"] > stats["launches"]
+    for k in range(3):
+        alone, _, _ = _serve([k], interleave=False)
+        for m in SPECTRAL:
+            assert np.array_equal(alone[k][m], mixed[k][m], equal_nan=True), (k, m)
+
+
+def test_served_equals_standalone_session_and_plain_mode():
+    served, _, _ = _serve([0, 1, 2], interleave=True)
+    plain, _, _ = _serve([0, 1, 2], interleave=True, plain=True)
+    xs = _trials()
+    for k, (n, N, fs, band, W, T) in enumerate(CONFIGS):
+        with fc.Session(n, N, fs, band, "hann", fc.FC_SPECTRAL_METRICS, W) as s:
+            for t in range(T):
+                s.push(xs[k][t])
+            for m in SPECTRAL:
+                ref = s.network(m, packed=True)[0]
+                assert_close(served[k][m], ref, what=f"served {m} cfg {k}")
+                assert_close(plain[k][m], ref, what=f"plain {m} cfg {k}")
+
+
+def test_admission_by_device_memory_budget():
+    need = [fc.fc_server_session_bytes(n, N, fs, band, fc.FC_SPECTRAL_METRICS, W)
+            for (n, N, fs, band, W, _) in CONFIGS]
+    sv = fc.fc_server_create(hbm_budget=need[0] + need[1] + 1024)
+    try:
+        a = fc.fc_server_open(sv, *CONFIGS[0][:3], CONFIGS[0][3], "hann", fc.FC_SPECTRAL_METRICS, CONFIGS[0][4])
+        b = fc.fc_server_open(sv, *CONFIGS[1][:3], CONFIGS[1][3], "hann", fc.FC_SPECTRAL_METRICS, CONFIGS[1][4])
+        with pytest.raises(fc.FcError) as e:
+            fc.fc_server_open(sv, *CONFIGS[1][:3], CONFIGS[1][3], "hann", fc.FC_SPECTRAL_METRICS, CONFIGS[1][4])
+        assert e.value.status == fc.FC_ERR_ADMISSION
+        assert fc.fc_server_stats_get(sv)["hbm_used"] == need[0] + need[1]
+        fc.fc_server_close(sv, b)  # frees need[1]: the refused session now fits
+        assert fc.fc_server_stats_get(sv)["hbm_used"] == need[0]
+        c = fc.fc_server_open(sv, *CONFIGS[1][:3], CONFIGS[1][3], "hann", fc.FC_SPECTRAL_METRICS, CONFIGS[1][4])
+        assert c not in (a, b)
+        with pytest.raises(fc.FcError):  # a closed session takes no more trials
+            fc.fc_server_submit(sv, b, white_trials(8, 1, CONFIGS[1][0], CONFIGS[1][1])[0], 0.0)
+        x = white_trials(9, 1, CONFIGS[1][0], CONFIGS[1][1])[0]
+        fc.fc_server_submit(sv, c, x, fc.fc_server_now_ms())
+        fc.fc_server_drain(sv, 60000)
+        assert len(fc.fc_server_poll(sv, 16)) == 1
+    finally:
+        fc.fc_server_destroy(sv)

@@ -20,7 +20,7 @@ connectivity analysis of large all-to-all networks"):
    describes XCOR via FFT convolution and returning the highest value and its
    index).
 
-Readings where the paper is silent or garbled (all listed in the design doc):
+Readings where the paper is silent or garbled:
 * COHY's printed second form repeats PSD_y; the first form (PSD_x, PSD_y) is used.
 * DSWPLI is printed as WPLI^2; the debiased estimator of the cited Vinck et al.
   (2011) is used: ((sum Im)^2 - sum Im^2) / ((sum |Im|)^2 - sum Im^2).
@@ -51,7 +51,7 @@ __all__ = [
     "pair_sums_dense", "pair_sums_pairs", "metrics_from_sums", "band_average",
     "spectral_networks_dense", "spectral_networks_pairs",
     "cor_trial", "cor_network", "xcor_trial_pair", "xcor_trial_dense", "xcor_network",
-    "window_trials", "networks_dense",
+    "window_trials", "networks_dense", "network_top",
 ]
 
 
@@ -410,3 +410,47 @@ def networks_dense(x: np.ndarray, fs: float, nfft: int, f_lo: float, f_hi: float
     if "XCOR" in metrics:
         out["XCOR"], out["XCOR_LAG"] = xcor_network(x)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Network post-processing (the paper's display pipeline)
+
+
+def network_top(w_packed, n: int, percent: float):
+    """Normalize a network by its maximum edge weight, keep its strongest ``percent`` % of
+    edges and give the kept network's node degree and node strength.
+
+    §3.1.2 and §3.2.2: every network is normalized by its maximum edge weight; §3.2.2,
+    §3.2.3 and the figure captions: only the strongest 5 %, 10 % or 25 % of the edges are
+    shown; §1: node degree and node strength are the graph measures drawn.
+
+    Readings: maximum and strength are taken by magnitude |w| (IMAGCOHY is signed); the
+    number of edges kept is ceil(percent * P / 100); among equal magnitudes the lower packed
+    index is kept first; a NaN edge (USPLI with fewer than two trials) counts as 0; node
+    strength is the sum of the kept normalized magnitudes. The edge ranking uses the
+    magnitudes of the given (FP32) weights exactly.
+
+    Returns (weights [P]: normalized kept weights, 0 elsewhere; degree [n] int64;
+    strength [n]; max_abs; kept).
+    """
+    w = np.asarray(w_packed, np.float64).copy()
+    P = n * (n - 1) // 2
+    assert w.shape == (P,)
+    w[np.isnan(w)] = 0.0
+    mag = np.abs(w)
+    max_abs = float(mag.max()) if P else 0.0
+    kept = min(P, max(0, int(math.ceil(percent * P / 100.0))))
+    order = np.lexsort((np.arange(P), -mag))  # by magnitude descending, then index
+    keep = np.zeros(P, bool)
+    keep[order[:kept]] = True
+    out = np.zeros(P)
+    if max_abs > 0:
+        out[keep] = w[keep] / max_abs
+    I, J = np.triu_indices(n, 1)
+    degree = np.zeros(n, np.int64)
+    strength = np.zeros(n)
+    for e in np.nonzero(keep)[0]:
+        for node in (I[e], J[e]):
+            degree[node] += 1
+            strength[node] += abs(out[e])
+    return out, degree, strength, max_abs, kept

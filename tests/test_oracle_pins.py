@@ -273,3 +273,52 @@ def test_eeg_workload_planted_couplings_visible():
         assert coh[a, b] > np.percentile(off, 99)
         if abs(lag - math.pi / 2) < 1e-9:
             assert abs(nets["IMAGCOHY"][a, b]) > np.percentile(np.abs(nets["IMAGCOHY"]), 99)
+
+
+# ------------------------------------------------------------ network post-processing
+
+
+def test_network_top_golden_example_with_a_tie():
+    g = json.load(open(os.path.join(GOLDEN, "network_top_4nodes.json")))
+    w = np.array([np.nan if v == "nan" else v for v in g["weights"]], np.float64)
+    out, deg, stren, mx, kept = O.network_top(w, g["n_nodes"], g["percent"])
+    assert kept == g["expected_kept"] and mx == pytest.approx(g["expected_max_abs"])
+    np.testing.assert_allclose(out, g["expected_weights"], rtol=0, atol=1e-15)
+    assert deg.tolist() == g["expected_degree"]
+    np.testing.assert_allclose(stren, g["expected_strength"], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("n,percent", [(30, 5.0), (41, 10.0), (17, 25.0), (9, 0.0)])
+def test_network_top_invariants(n, percent):
+    rng = np.random.default_rng(n)
+    w = rng.standard_normal(n * (n - 1) // 2).astype(np.float32)
+    out, deg, stren, mx, kept = O.network_top(w, n, percent)
+    P = w.size
+    assert kept == math.ceil(percent * P / 100)
+    keep = out != 0
+    assert keep.sum() == kept and deg.sum() == 2 * kept
+    if kept:
+        assert np.abs(w[keep]).min() >= np.abs(w[~keep]).max()  # strongest edges kept
+        assert np.abs(out).max() == 1.0
+        np.testing.assert_allclose(out[keep], w[keep] / np.abs(w).max())
+    np.testing.assert_allclose(stren.sum(), 2 * np.abs(out).sum())
+
+
+def test_network_top_everything_kept_gives_dense_row_sums():
+    n = 23
+    rng = np.random.default_rng(5)
+    w = rng.uniform(-1, 1, n * (n - 1) // 2)
+    out, deg, stren, mx, kept = O.network_top(w, n, 100.0)
+    dense = np.zeros((n, n))
+    dense[np.triu_indices(n, 1)] = np.abs(w)
+    dense = dense + dense.T
+    assert (deg == n - 1).all()
+    np.testing.assert_allclose(stren, dense.sum(axis=1) / np.abs(w).max(), rtol=1e-13)
+
+
+def test_network_top_equal_weights_keep_lowest_indices():
+    n = 10
+    w = np.full(n * (n - 1) // 2, 0.25)
+    out, deg, stren, mx, kept = O.network_top(w, n, 20.0)
+    assert kept == 9 and (out[:9] == 1.0).all() and (out[9:] == 0).all()
+    assert deg[0] == 9 and (deg[1:] == 1).all()  # pairs (0, 1) .. (0, 9)

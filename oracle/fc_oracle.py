@@ -51,7 +51,7 @@ __all__ = [
     "pair_sums_dense", "pair_sums_pairs", "metrics_from_sums", "band_average",
     "spectral_networks_dense", "spectral_networks_pairs",
     "cor_trial", "cor_network", "xcor_trial_pair", "xcor_trial_dense", "xcor_network",
-    "window_trials", "networks_dense", "network_top",
+    "window_trials", "networks_dense", "network_top", "project",
 ]
 
 
@@ -454,3 +454,22 @@ def network_top(w_packed, n: int, percent: float):
             degree[node] += 1
             strength[node] += abs(out[e])
     return out, degree, strength, max_abs, kept
+
+
+# ---------------------------------------------------------------------------
+# Source projection ahead of the spectrum
+
+
+def project(op, x):
+    """Source trials from sensor trials: y_k = M x_k for every trial k.
+
+    §2.5 / Figure 1: in the source-level pipeline each trial is mapped to the source
+    space (RTC-MNE) before the connectivity step; the inverse operator M is a
+    [n_sources][n_channels] matrix applied to the [n_channels][n_samples] trial. A matmul
+    is the library step here.
+    """
+    M = np.asarray(op, np.float64)
+    X = np.asarray(x, np.float64)
+    if X.ndim == 2:
+        return M @ X
+    return np.stack([M @ xk for xk in X])

@@ -322,3 +322,26 @@ def test_network_top_equal_weights_keep_lowest_indices():
     out, deg, stren, mx, kept = O.network_top(w, n, 20.0)
     assert kept == 9 and (out[:9] == 1.0).all() and (out[9:] == 0).all()
     assert deg[0] == 9 and (deg[1:] == 1).all()  # pairs (0, 1) .. (0, 9)
+
+
+# ------------------------------------------------------------------------- projection
+
+
+def test_project_hand_example_and_identity():
+    M = np.array([[1.0, 0.0, 2.0], [0.0, -1.0, 0.5]])  # 2 sources x 3 sensors
+    x = np.array([[1.0, 2.0], [3.0, 4.0], [5.0, 6.0]])  # 3 sensors x 2 samples
+    # y_0 = x_0 + 2 x_2 = (11, 14); y_1 = -x_1 + 0.5 x_2 = (-0.5, -1)
+    np.testing.assert_array_equal(O.project(M, x), [[11.0, 14.0], [-0.5, -1.0]])
+    t = np.random.default_rng(0).standard_normal((4, 7, 9))
+    np.testing.assert_array_equal(O.project(np.eye(7), t), t)
+
+
+def test_projected_networks_of_a_permutation_are_permuted():
+    """A permutation operator relabels the nodes: the networks are the permuted ones."""
+    x, _ = eeg_sinusoid_trials(7, 8, 12, 256, n_pairs=5)
+    perm = np.random.default_rng(1).permutation(12)
+    M = np.eye(12)[perm]
+    a = O.networks_dense(x, 1000.0, 256, 1.0, 50.0, metrics=("COH", "PLI", "COR"))
+    b = O.networks_dense(O.project(M, x), 1000.0, 256, 1.0, 50.0, metrics=("COH", "PLI", "COR"))
+    for m in ("COH", "PLI", "COR"):
+        np.testing.assert_allclose(b[m], a[m][np.ix_(perm, perm)], atol=1e-12)

@@ -334,6 +334,49 @@ def serving_leg(fc, plain, duration_s, seed, saturate=False):
             "windows": [s.window for s in trace], "rates_per_s": [round(s.rate_hz, 2) for s in trace]}
 
 
+def run_sweep(args):
+    """Secondary sweep shaped like the paper's performance evaluation (Results 3.1: fs = nfft
+    = 600 Hz, 8-12 Hz = 4 bins, storage mode off so that every evaluation recomputes the
+    window; node counts x window sizes for one trial, node counts x trial counts at 1,000
+    samples). Each row: device time of one full evaluation (bulk push of the K trials through
+    the full-window path, FP32) and its network read into device memory."""
+    import torch
+    from paper_2303_03279_gb300 import fc
+    from synth import white_trials
+
+    fc.load()
+    stream = torch.cuda.Stream()
+    nodes = [60, 128, 306, 1000, 2000]
+    shapes = [(1, ns) for ns in (500, 1000, 2000, 4000, 8000)] + [(k, 1000) for k in (10, 50, 100)]
+    metrics = {"COR": fc.FC_COR, "XCOR": fc.FC_XCOR, "spectral (COH ... DSWPLI)": fc.FC_SPECTRAL_METRICS}
+    rows = []
+    for n in nodes:
+        for K, N in shapes:
+            x = torch.from_numpy(white_trials(n + K + N, K, n, N)).cuda()
+            for mname, mask in metrics.items():
+                if mname == "XCOR" and n * (n - 1) // 2 * K * N > 2e10:
+                    continue  # bounded run time
+                with fc.Session(n, N, 600.0, (8.0, 12.0, 600), "hann", mask, K, mode=fc.FC_MODE_FULL,
+                                stream=stream.cuda_stream) as sess:
+                    out = torch.empty(n * (n - 1) // 2, device="cuda")
+                    bit = fc.FC_COR if mask == fc.FC_COR else (fc.FC_XCOR if mask == fc.FC_XCOR else fc.FC_COH)
+                    reps, t = 3, []
+                    for r in range(reps + 1):
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        fc.fc_push_trials(sess.handle, x, K)
+                        fc.fc_get_network(sess.handle, bit, 1, out)
+                        b.record(stream)
+                        b.synchronize()
+                        if r:
+                            t.append(a.elapsed_time(b))
+                rows.append({"metric": mname, "nodes": n, "samples": N, "trials": K,
+                             "ms": round(sum(t) / len(t), 4)})
+    print(json.dumps({"sweep": "paper-style performance sweep (fs = nfft = 600, 8-12 Hz, full recompute)",
+                      "unit": "ms per evaluation", "rows": rows}), flush=True)
+    return 0
+
+
 def run_ours(args, w, wname):
     import torch
     from paper_2303_03279_gb300 import fc
@@ -559,11 +602,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cpu-all-core", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="print the paper-style performance sweep instead")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     w = WORKLOADS[args.workload]
+    if args.sweep:
+        return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args, w, args.workload)
     return run_ours(args, w, args.workload)

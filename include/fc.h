@@ -162,6 +162,58 @@ fc_status fc_get_network(fc_session* s, uint32_t metric, int packed_upper, float
                          size_t out_len, int out_on_device, int* k_used);
 
 /* Per-bin values of one spectral metric, out[n_bins][P] (packed upper per bin). */
+/* Post-processing of the current band-averaged network of one metric, as the paper
+ * presents its networks (Results 3.1.2, 3.2.2: normalized by the maximum edge weight;
+ * Results 3.2.2, 3.2.3: only the strongest 5 / 10 / 25 % of the edges; Introduction: node
+ * degree and node strength). Edges are ranked by magnitude |w| (IMAGCOHY is signed);
+ * kept = ceil(percent * P / 100) edges, among equal magnitudes the lower packed index
+ * first; NaN edges count as 0.
+ *   weights  [P] packed upper: w / max|w| for kept edges, 0 elsewhere (NULL: not returned)
+ *   degree   [n] kept edges at each node; strength [n] sum of their normalized |w|
+ *            (both NULL, or both given)
+ * Outputs are host or device memory (out_on_device) and belong to the caller; the call
+ * synchronizes the session's stream. Uses session-owned device scratch (allocated on
+ * first use, about 5 B per pair). Errors: FC_ERR_INVALID_ARG (metric, percent, outputs),
+ * FC_ERR_NOT_READY (nothing accepted yet), FC_ERR_NONFINITE (a rejection to report first). */
+typedef struct {
+    float max_abs;    /* the normalizer, max |w| over the edges (0: an all-zero network) */
+    float threshold;  /* |w| of the weakest kept edge, before normalization (0 if none kept) */
+    long long kept;   /* edges kept */
+} fc_top_info;
+fc_status fc_get_network_top(fc_session* s, uint32_t metric, double percent, float* weights,
+                             int* degree, float* strength, int out_on_device, fc_top_info* info);
+
+/* Change the band the networks average over to [f_lo, f_hi) Hz, a sub-band of the bins the
+ * session computes (its creation band at the same nfft). The networks are refinalized from
+ * the per-bin sums at once and every later push averages over the new band; no trial is
+ * reprocessed in streaming mode (the per-bin accumulators hold everything; the Discussion,
+ * section 4, contrasts this CSD/PSD design with methods that filter the signal to one band
+ * before a Hilbert transform); full mode recomputes the window from its stored spectra. FC_ERR_INVALID_ARG if the band selects no bin or reaches
+ * outside the computed ones (create the session with the wider band). */
+fc_status fc_set_band(fc_session* s, double f_lo, double f_hi);
+
+/* Session snapshot: the whole device state of a session (spectra ring, per-bin sums,
+ * networks, control block, COR/XCOR state) and its window position, as one byte image in
+ * caller-owned host memory, e.g. to checkpoint a long online session. fc_session_snapshot
+ * synchronizes the session; fc_session_restore overwrites the state of a session created
+ * with identical settings (FC_ERR_INVALID_ARG otherwise, or for a short or foreign buffer),
+ * which then continues exactly as the snapshotted one would. The image is a header, the
+ * buffer sizes and the buffers, in this library version's layout. */
+fc_status fc_session_snapshot_size(fc_session* s, size_t* bytes);
+fc_status fc_session_snapshot(fc_session* s, void* host_buf, size_t len);
+fc_status fc_session_restore(fc_session* s, const void* host_buf, size_t len);
+
+/* Source projection ahead of the spectrum (Methods 2.5, Figure 1: in the source-level
+ * pipeline each trial is mapped to the source space by the inverse operator before the
+ * connectivity step). op is M [n_nodes][n_channels], row-major, FP32, host or device
+ * memory (copied). After this call every push takes sensor trials x[n_channels][n_samples]
+ * (same host/device rules as before) and the session's nodes are the n_nodes sources:
+ * y = M x per trial, FP32 on the CUDA cores, then validation, spectrum, COR/XCOR as usual.
+ * op == NULL removes the projection (pushes take [n_nodes][n_samples] again). The operator
+ * is configuration, not state: snapshots do not carry it. FC_ERR_INVALID_ARG for
+ * n_channels < 1 with a non-NULL op. */
+fc_status fc_set_projection(fc_session* s, const float* op, int n_channels, int op_on_device);
+
 fc_status fc_get_network_bins(fc_session* s, uint32_t metric, float* out, size_t out_len,
                               int out_on_device);
 
@@ -196,6 +248,7 @@ typedef enum {
     FC_K_BAND_REDUCE,  /* band average of per-bin-group partial sums */
     FC_K_COR,          /* correlation products */
     FC_K_XCOR,         /* cross-correlation via FFT */
+    FC_K_PROJECT,      /* source projection of sensor trials */
     FC_K_OTHER,
     FC_K_COUNT
 } fc_kernel_id;
@@ -233,6 +286,14 @@ typedef enum {
     FC_ACC_CSD_RE = 0, FC_ACC_CSD_IM, FC_ACC_U_RE, FC_ACC_U_IM, FC_ACC_ABS, FC_ACC_SQ,
     FC_ACC_SIGN, FC_ACC_PSD, FC_ACC_COR, FC_ACC_XCOR
 } fc_acc_field;
+/* Self-test of failure detection: a kernel waits, through the library's bounded-wait
+ * routine, on a device barrier that nothing completes, with a budget of limit_ms (0 < limit
+ * <= 1000). The wait gives up, the kernel records a timeout in the session's control block
+ * and returns (no fault, the context stays usable); the call then returns FC_ERR_TIMEOUT,
+ * as any call would after a real wait ran out. The session reports FC_ERR_TIMEOUT from then
+ * on: use a throwaway session. */
+fc_status fc_debug_wait_probe(fc_session* s, double limit_ms);
+
 fc_status fc_debug_get_accumulators(fc_session* s, fc_acc_field field, double* out,
                                     size_t out_len);
 
@@ -241,11 +302,14 @@ fc_status fc_debug_get_accumulators(fc_session* s, fc_acc_field field, double* o
  * A server holds many sessions resident on one GPU and turns every arriving trial of any
  * session into a request (the paper's online setting, Methods 2.5 / Results 3.2.3: each
  * new trial is added to the network as it arrives, under a per-block deadline). A worker
- * thread batches the pending trials of all sessions into one launch of the persistent
- * streaming kernel per tick (at most one trial per session per launch, FIFO within a
- * session, oldest arrivals first across sessions); trials arriving while a launch runs
- * join the next one, and up to two launches are in flight, so host staging overlaps the
- * device work. Sessions are admitted against a device-memory budget.
+ * thread runs ticks; each tick is one launch of the persistent streaming kernel over a
+ * share of the pushes of up to max_batch sessions (FIFO within a session, one trial in
+ * progress per session). A launch carries at most launch_blocks state blocks; a larger push
+ * is split over consecutive launches and its trial completes with the last one, so the
+ * trials of small sessions are not held back by a large session's push. Trials arriving
+ * while a launch runs join the next one, and up to two launches are in flight, so host
+ * staging overlaps the device work. Sessions are admitted against a device-memory budget.
+ * Results are identical whichever sessions share a launch.
  */
 typedef struct fc_server fc_server;
 
@@ -254,20 +318,27 @@ typedef struct {
     int max_batch;     /* sessions per launch, 1..32 (0: 32) */
     int plain;         /* 1: comparison mode - FC_MODE_FULL FP32 sessions, one trial at a time,
                           each a full-window recompute (no batching, no streaming sums) */
+    int launch_blocks; /* state blocks (one 32 x 32 tile pair x one bin, 106 KB of traffic)
+                          per launch: 0 = 65536 (about 1.2 ms on GB300); < 0 = no limit */
 } fc_server_config;
 
 typedef struct {
     int session;       /* server session id */
     long long seq;     /* index of the trial within its session's submissions (0-based) */
-    fc_status status;  /* FC_OK, or FC_ERR_NONFINITE when the trial was rejected */
+    fc_status status;  /* FC_OK; FC_ERR_NONFINITE: the trial held NaN/Inf and was rejected
+                          (the session state is unchanged); FC_ERR_TIMEOUT: a bounded device
+                          wait ran out */
     double arrival_ms; /* the submitter's arrival stamp */
     double done_ms;    /* when the server observed the network ready (same clock) */
-    int batch;         /* sessions in the launch that carried this trial */
+    int batch;         /* sessions in the streaming-kernel launch that completed this trial
+                          (1: it ran alone, e.g. a session's first, calibrating push) */
 } fc_result;
 
 typedef struct {
-    long long submitted, completed, launches, batched_trials;
-    long long pair_bin_updates; /* sum of P * B over completed trials */
+    long long submitted, completed;
+    long long launches;         /* ticks with device work */
+    long long batched_trials;   /* session shares over all ticks */
+    long long pair_bin_updates; /* sum of P * B over trials completed with FC_OK */
     size_t hbm_used;
     int sessions;
 } fc_server_stats;
@@ -297,7 +368,8 @@ fc_status fc_server_poll(fc_server* sv, fc_result* out, int max, int* n_out, int
 /* Wait until every submitted trial has completed (up to timeout_ms; FC_ERR_TIMEOUT after). */
 fc_status fc_server_drain(fc_server* sv, int timeout_ms);
 
-/* Current band-averaged network of a session (packed upper, host memory). */
+/* Current band-averaged network of a session (packed upper, host memory), after its last
+ * trial whose push is fully enqueued; waits while a push is split between launches. */
 fc_status fc_server_get_network(fc_server* sv, int session_id, uint32_t metric, float* out,
                                 size_t out_len);
 

@@ -73,6 +73,7 @@ fc_status alloc_zero(fc_session* s, size_t count, T** out) {
     fc_status st = dev_alloc(s, count * sizeof(T), &p);
     if (st != FC_OK) return st;
     CK(cudaMemsetAsync(p, 0, count * sizeof(T), s->stream));
+    s->state_bufs.emplace_back(p, count * sizeof(T) ? count * sizeof(T) : 16);
     *out = static_cast<T*>(p);
     return FC_OK;
 }
@@ -168,6 +169,8 @@ PairArgs pair_args(fc_session* s, bool stream_kernel, int count) {
     a.write_acc = 0;
     a.count = count;
     a.grid_ctas = 2 * s->num_sms;
+    a.fsel0 = s->sel0;
+    a.fsel1 = s->sel1;
     a.ctrl = s->ctrl;
     return a;
 }
@@ -291,6 +294,8 @@ fc_status stage_window(fc_session* s, int count, bool write_acc) {
         ha.grid_ctas = s->num_sms;
         ha.P = s->P;
         ha.mask = s->mask;
+        ha.fsel0 = s->sel0;
+        ha.fsel1 = s->sel1;
         ha.ctrl = s->ctrl;
         if (s->mask & (FC_COH | FC_IMAGCOHY | FC_PLV)) {
             LAUNCH(FC_K_HERK_TC, launch_pack_operands(pk, s->stream));
@@ -546,6 +551,8 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
     s->n = n_nodes;
     s->N = n_samples;
     s->B = B;
+    s->sel0 = 0;
+    s->sel1 = B;
     s->first_bin = first;
     s->nfft = band.nfft;
     s->W = window;
@@ -687,6 +694,9 @@ fc_status fc_session_destroy(fc_session* s) {
     free_all(s);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     if (s->dense_scratch) cudaFree(s->dense_scratch);
+    if (s->post_scratch) cudaFree(s->post_scratch);
+    if (s->proj) cudaFree(s->proj);
+    if (s->proj_in) cudaFree(s->proj_in);
     delete s;
     return FC_OK;
 }
@@ -697,7 +707,27 @@ fc_status fc_push_trials(fc_session* s, const float* x, int count, int x_on_devi
     CK(cudaSetDevice(s->device));
     const float* xd = x;
     const size_t per = (size_t)s->n * s->N;
-    if (!x_on_device) {
+    if (s->proj) {
+        // sensor trials [count][C][N] -> source trials [count][n][N] in the staging buffer
+        const size_t per_in = (size_t)s->proj_C * s->N;
+        if (count > 65535) return fail(FC_ERR_INVALID_ARG, "at most 65535 trials per call with a projection");
+        const float* xin = x;
+        if (!x_on_device) {
+            if (s->proj_in_trials < count) {
+                if (s->proj_in) cudaFree(s->proj_in);
+                s->proj_in = nullptr;
+                s->proj_in_trials = 0;
+                CK(cudaMalloc(&s->proj_in, per_in * count * sizeof(float)));
+                s->proj_in_trials = count;
+            }
+            CK(cudaMemcpyAsync(s->proj_in, x, per_in * count * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+            xin = s->proj_in;
+        }
+        fc_status st = ensure_stage(s, count);
+        if (st != FC_OK) return st;
+        LAUNCH(FC_K_PROJECT, launch_project(s->proj, xin, s->x_stage, s->n, s->proj_C, s->N, count, s->stream));
+        xd = s->x_stage;
+    } else if (!x_on_device) {
         fc_status st = ensure_stage(s, count);
         if (st != FC_OK) return st;
         CK(cudaMemcpyAsync(s->x_stage, x, per * count * sizeof(float), cudaMemcpyHostToDevice, s->stream));
@@ -761,6 +791,61 @@ fc_status fc_get_network(fc_session* s, uint32_t metric, int packed_upper, float
         if (!out_on_device) CK(cudaMemcpyAsync(out, dst, need * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
     }
     if (!out_on_device) CK(cudaStreamSynchronize(s->stream));
+    return FC_OK;
+}
+
+fc_status fc_get_network_top(fc_session* s, uint32_t metric, double percent, float* weights, int* degree,
+                             float* strength, int out_on_device, fc_top_info* info) {
+    if (!s) return fail(FC_ERR_INVALID_ARG, "NULL session");
+    const int mi = metric_index(metric);
+    if (mi < 0) return fail(FC_ERR_INVALID_ARG, "metric must be a single FC_* bit");
+    if (!(s->mask & metric)) return fail(FC_ERR_INVALID_ARG, "metric 0x%x is not in the session mask", metric);
+    if (!(percent >= 0.0 && percent <= 100.0)) return fail(FC_ERR_INVALID_ARG, "percent must be in [0, 100]");
+    if ((degree == nullptr) != (strength == nullptr))
+        return fail(FC_ERR_INVALID_ARG, "degree and strength are given together or not at all");
+    CK(cudaSetDevice(s->device));
+    if (s->enqueued == 0) return fail(FC_ERR_NOT_READY, "no trial has been pushed");
+    FcCtrl h;
+    fc_status st = check_latched(s, &h);
+    if (st != FC_OK) return st;
+    if (h.pushed == 0) return fail(FC_ERR_NOT_READY, "no trial has been accepted");
+    const long long P = s->P;
+    const long long k = std::min(P, std::max(0LL, (long long)std::ceil(percent * (double)P / 100.0)));
+    // scratch: select state + ties + flags, then device outputs when the caller's are on the host
+    const size_t base = (post_scratch_bytes(P) + 255) / 256 * 256;
+    const size_t need = base + (size_t)P * sizeof(float) + (size_t)s->n * (sizeof(int) + sizeof(float)) + 256;
+    if (s->post_scratch_len < need) {
+        if (s->post_scratch) cudaFree(s->post_scratch);
+        s->post_scratch = nullptr;
+        s->post_scratch_len = 0;
+        CK(cudaMalloc(&s->post_scratch, need));
+        s->post_scratch_len = need;
+    }
+    char* sc = static_cast<char*>(s->post_scratch);
+    float* d_w = (weights && out_on_device) ? weights : reinterpret_cast<float*>(sc + base);
+    int* d_deg = nullptr;
+    float* d_str = nullptr;
+    if (degree) {
+        d_deg = out_on_device ? degree : reinterpret_cast<int*>(sc + base + (size_t)P * sizeof(float));
+        d_str = out_on_device ? strength : reinterpret_cast<float*>(sc + base + (size_t)P * sizeof(float) +
+                                                                     (size_t)s->n * sizeof(int));
+    }
+    CK(launch_network_top(s->net + (size_t)mi * P, P, s->n, k, sc, d_w, d_deg, d_str, s->num_sms, s->stream));
+    if (!out_on_device) {
+        if (weights) CK(cudaMemcpy(weights, d_w, (size_t)P * sizeof(float), cudaMemcpyDeviceToHost));
+        if (degree) {
+            CK(cudaMemcpy(degree, d_deg, (size_t)s->n * sizeof(int), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(strength, d_str, (size_t)s->n * sizeof(float), cudaMemcpyDeviceToHost));
+        }
+    }
+    if (info) {
+        PostState ps;
+        CK(cudaMemcpy(&ps, s->post_scratch, sizeof(PostState), cudaMemcpyDeviceToHost));
+        std::memcpy(&info->max_abs, &ps.max_key, sizeof(float));
+        info->threshold = 0.f;
+        if (k > 0) std::memcpy(&info->threshold, &ps.prefix, sizeof(float));
+        info->kept = k;
+    }
     return FC_OK;
 }
 
@@ -835,6 +920,161 @@ fc_status fc_set_metric_mask(fc_session* s, uint32_t metric_mask) {
             if (st != FC_OK) return st;
         }
     }
+    return FC_OK;
+}
+
+fc_status fc_debug_wait_probe(fc_session* s, double limit_ms) {
+    if (!s) return fail(FC_ERR_INVALID_ARG, "NULL session");
+    if (!(limit_ms > 0.0 && limit_ms <= 1000.0)) return fail(FC_ERR_INVALID_ARG, "limit_ms must be in (0, 1000]");
+    CK(cudaSetDevice(s->device));
+    LAUNCH(FC_K_OTHER, launch_wait_probe(s->ctrl, (unsigned long long)(limit_ms * 1e6), s->stream));
+    FcCtrl h;
+    return check_latched(s, &h);
+}
+
+fc_status fc_set_projection(fc_session* s, const float* op, int n_channels, int op_on_device) {
+    if (!s) return fail(FC_ERR_INVALID_ARG, "NULL session");
+    CK(cudaSetDevice(s->device));
+    CK(cudaStreamSynchronize(s->stream));  // pushes in flight used the previous operator
+    if (!op) {
+        if (s->proj) cudaFree(s->proj);
+        s->proj = nullptr;
+        s->proj_C = 0;
+        return FC_OK;
+    }
+    if (n_channels < 1) return fail(FC_ERR_INVALID_ARG, "n_channels must be >= 1");
+    const size_t bytes = (size_t)s->n * n_channels * sizeof(float);
+    if (s->proj && s->proj_C != n_channels) {
+        cudaFree(s->proj);
+        s->proj = nullptr;
+    }
+    if (!s->proj) CK(cudaMalloc(&s->proj, bytes));
+    s->proj_C = n_channels;
+    CK(cudaMemcpy(s->proj, op, bytes, op_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    return FC_OK;
+}
+
+fc_status fc_set_band(fc_session* s, double f_lo, double f_hi) {
+    if (!s) return fail(FC_ERR_INVALID_ARG, "NULL session");
+    fc_band b = s->band;
+    b.f_lo = f_lo;
+    b.f_hi = f_hi;
+    int first = -1;
+    const int cnt = fc_band_bins(s->fs, b, &first);
+    if (cnt <= 0) return fail(FC_ERR_INVALID_ARG, "the band [%g, %g) Hz selects no bin", f_lo, f_hi);
+    if (first < s->first_bin || first + cnt > s->first_bin + s->B)
+        return fail(FC_ERR_INVALID_ARG,
+                    "the band [%g, %g) Hz reaches outside the computed bins %d..%d: create the session with "
+                    "the wider band", f_lo, f_hi, s->first_bin, s->first_bin + s->B - 1);
+    CK(cudaSetDevice(s->device));
+    s->sel0 = first - s->first_bin;
+    s->sel1 = s->sel0 + cnt;
+    if (s->enqueued > 0 && (s->mask & FC_SPECTRAL_METRICS)) {
+        // new band averages from the per-bin sums: no trial is reprocessed
+        if (s->cfg.mode == FC_MODE_STREAM) {
+            PairArgs pa = pair_args(s, true, 0);
+            pa.finalize = 1;
+            pa.update = 0;
+            LAUNCH(FC_K_STREAM, launch_stream_update(pa, s->stream));
+            if (pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
+        } else {
+            fc_status st = stage_window(s, 0, false);
+            if (st != FC_OK) return st;
+        }
+    }
+    return FC_OK;
+}
+
+// ------------------------------------------------------------ snapshot / restore
+namespace {
+struct SnapHeader {
+    char magic[8];
+    int n, N, B, first_bin, nfft, W, slots, mode, precision, taper;
+    double fs, f_lo, f_hi;
+    uint32_t mask, time_mask;
+    int sel0, sel1, nbufs, calibrated;
+    long long enqueued, resum_phase;
+};
+const char kSnapMagic[8] = {'F', 'C', 'S', 'N', 'A', 'P', '1', 0};
+
+size_t snapshot_bytes(const fc_session* s) {
+    size_t b = sizeof(SnapHeader) + s->state_bufs.size() * sizeof(unsigned long long);
+    for (const auto& sb : s->state_bufs) b += sb.second;
+    return b;
+}
+}  // namespace
+
+fc_status fc_session_snapshot_size(fc_session* s, size_t* bytes) {
+    if (!s || !bytes) return fail(FC_ERR_INVALID_ARG, "NULL argument");
+    *bytes = snapshot_bytes(s);
+    return FC_OK;
+}
+
+fc_status fc_session_snapshot(fc_session* s, void* host_buf, size_t len) {
+    if (!s || !host_buf) return fail(FC_ERR_INVALID_ARG, "NULL argument");
+    if (len < snapshot_bytes(s)) return fail(FC_ERR_INVALID_ARG, "buffer of %zu bytes < %zu", len, snapshot_bytes(s));
+    CK(cudaSetDevice(s->device));
+    FcCtrl h;
+    fc_status st = read_ctrl(s, &h);  // synchronizes: every enqueued push is in the state
+    if (st != FC_OK) return st;
+    SnapHeader hd;
+    std::memset(&hd, 0, sizeof hd);
+    std::memcpy(hd.magic, kSnapMagic, sizeof hd.magic);
+    hd.n = s->n; hd.N = s->N; hd.B = s->B; hd.first_bin = s->first_bin; hd.nfft = s->nfft; hd.W = s->W;
+    hd.slots = s->slots; hd.mode = (int)s->cfg.mode; hd.precision = (int)s->cfg.precision; hd.taper = (int)s->taper;
+    hd.fs = s->fs; hd.f_lo = s->band.f_lo; hd.f_hi = s->band.f_hi;
+    hd.mask = s->mask; hd.time_mask = s->time_mask; hd.sel0 = s->sel0; hd.sel1 = s->sel1;
+    hd.nbufs = (int)s->state_bufs.size(); hd.calibrated = s->calibrated ? 1 : 0;
+    hd.enqueued = s->enqueued; hd.resum_phase = s->resum_phase;
+    char* out = static_cast<char*>(host_buf);
+    std::memcpy(out, &hd, sizeof hd);
+    size_t off = sizeof hd;
+    for (const auto& sb : s->state_bufs) {
+        const unsigned long long b = sb.second;
+        std::memcpy(out + off, &b, sizeof b);
+        off += sizeof b;
+    }
+    for (const auto& sb : s->state_bufs) {
+        CK(cudaMemcpy(out + off, sb.first, sb.second, cudaMemcpyDeviceToHost));
+        off += sb.second;
+    }
+    return FC_OK;
+}
+
+fc_status fc_session_restore(fc_session* s, const void* host_buf, size_t len) {
+    if (!s || !host_buf) return fail(FC_ERR_INVALID_ARG, "NULL argument");
+    if (len < sizeof(SnapHeader)) return fail(FC_ERR_INVALID_ARG, "not a session snapshot (too short)");
+    SnapHeader hd;
+    std::memcpy(&hd, host_buf, sizeof hd);
+    if (std::memcmp(hd.magic, kSnapMagic, sizeof hd.magic) != 0)
+        return fail(FC_ERR_INVALID_ARG, "not a session snapshot (bad magic)");
+    const bool same = hd.n == s->n && hd.N == s->N && hd.B == s->B && hd.first_bin == s->first_bin &&
+                      hd.nfft == s->nfft && hd.W == s->W && hd.slots == s->slots && hd.mode == (int)s->cfg.mode &&
+                      hd.precision == (int)s->cfg.precision && hd.taper == (int)s->taper && hd.fs == s->fs &&
+                      hd.f_lo == s->band.f_lo && hd.f_hi == s->band.f_hi && hd.time_mask == s->time_mask &&
+                      hd.nbufs == (int)s->state_bufs.size();
+    if (!same) return fail(FC_ERR_INVALID_ARG, "the snapshot was taken from a session with other settings");
+    if (len < snapshot_bytes(s)) return fail(FC_ERR_INVALID_ARG, "snapshot truncated");
+    const char* in = static_cast<const char*>(host_buf);
+    size_t off = sizeof hd;
+    for (const auto& sb : s->state_bufs) {
+        unsigned long long b;
+        std::memcpy(&b, in + off, sizeof b);
+        off += sizeof b;
+        if (b != sb.second) return fail(FC_ERR_INVALID_ARG, "the snapshot's buffer sizes differ from this session's");
+    }
+    CK(cudaSetDevice(s->device));
+    CK(cudaStreamSynchronize(s->stream));
+    for (const auto& sb : s->state_bufs) {
+        CK(cudaMemcpy(sb.first, in + off, sb.second, cudaMemcpyHostToDevice));
+        off += sb.second;
+    }
+    s->mask = hd.mask;
+    s->sel0 = hd.sel0;
+    s->sel1 = hd.sel1;
+    s->calibrated = hd.calibrated != 0;
+    s->enqueued = hd.enqueued;
+    s->resum_phase = hd.resum_phase;
     return FC_OK;
 }
 

@@ -84,9 +84,16 @@ struct fc_session {
     long long enqueued;
     long long resum_phase;  // next slice of the sliced re-sum (0 .. period - 1)
     bool calibrated;        // the device prescale is known to be set
+    int sel0, sel1;         // selected sub-band: bins sel0 .. sel1 - 1 of the B computed
 
     float* dense_scratch;   // n x n staging for dense host outputs
     size_t dense_scratch_len;
+    void* post_scratch;     // network post-processing: select state, ties, flags, outputs
+    size_t post_scratch_len;
+    float* proj;            // source projection M [n][proj_C] (NULL: none)
+    int proj_C;
+    float* proj_in;         // staged sensor trials [proj_in_trials][proj_C][N]
+    int proj_in_trials;
 
     // device buffers
     FcCtrl* ctrl;
@@ -124,6 +131,7 @@ struct fc_session {
     std::vector<FcPendingTiming> pending;
     fc_kernel_time ktime[FC_K_COUNT];
     std::vector<void*> allocations;
+    std::vector<std::pair<void*, size_t>> state_bufs;  // persistent state, in allocation order
 };
 
 // ---------------------------------------------------------------------------------
@@ -169,6 +177,8 @@ struct PairArgs {
     int update;        // stream kernel: 1 = add/subtract the trials, 0 = finalize only
     int write_acc;     // window kernel: store accumulators (re-sum)
     int tp0, tp_count; // window kernel: tile pairs tp0 .. tp0 + tp_count - 1 (tp_count 0: all)
+    int u0;            // stream kernel: first unit of this launch (a push may span launches)
+    int fsel0, fsel1;  // bins fsel0 .. fsel1 - 1 enter the band average (a sub-band of the B)
     int count;         // trials pushed by this call (window end = pushed + count)
     int grid_ctas;     // persistent grid size of the streaming kernel
     const FcCtrl* ctrl;
@@ -176,7 +186,8 @@ struct PairArgs {
 cudaError_t launch_stream_update(const PairArgs& a, cudaStream_t st);
 
 // A batch of sessions updated by one launch of the streaming kernel (passed by value as
-// the kernel's parameter block; units of session s are [unit_prefix[s], unit_prefix[s+1])).
+// the kernel's parameter block). The launch covers units a[s].u0 .. a[s].u0 + (unit_prefix[s+1]
+// - unit_prefix[s]) - 1 of session s; a session's push may be split over several launches.
 #define FC_MAX_BATCH 32
 struct StreamBatch {
     int nsess;
@@ -207,6 +218,7 @@ struct HerkArgs {
     int n, B, ntp, nchunks, W, count, ab_format, grid_ctas;
     long long P;
     uint32_t mask;
+    int fsel0, fsel1;     // bins entering the band average
     const FcCtrl* ctrl;
 };
 cudaError_t launch_pack_operands(const PackArgs& a, cudaStream_t st);
@@ -258,6 +270,27 @@ cudaError_t launch_xcor_pairs(const XcorArgs& a, cudaStream_t st);
 cudaError_t launch_xcor_update(const XcorArgs& a, cudaStream_t st);
 
 // Set the thread-local message returned by fc_last_error() (for entry points outside fc_api.cu).
+// Network post-processing (k_post.cu): radix-select state in device scratch.
+struct PostState {
+    unsigned int max_key;  // largest magnitude (IEEE bits)
+    unsigned int prefix;   // bits of the k-th largest magnitude found so far
+    unsigned int mask;     // bits of prefix already fixed
+    unsigned int pad_;
+    long long k_rem;       // edges at the final magnitude still to keep
+    long long k_total;     // edges to keep
+    unsigned long long hist[256];
+};
+size_t post_scratch_bytes(long long P);
+// Self-test: a bounded wait on an mbarrier nothing arrives at; sets ctrl->timeout.
+cudaError_t launch_wait_probe(FcCtrl* ctrl, unsigned long long limit_ns, cudaStream_t st);
+// Y[k] = M X[k] for count trials: M [n][C], X [count][C][N], Y [count][n][N].
+cudaError_t launch_project(const float* M, const float* X, float* Y, int n, int C, int N, int count,
+                           cudaStream_t st);
+// Kept normalized weights out[P], keep flags, degree[n] and strength[n] (both optional);
+// synchronizes the stream.
+cudaError_t launch_network_top(const float* w, long long P, int n, long long k, void* scratch, float* out,
+                               int* degree, float* strength, int num_sms, cudaStream_t stream);
+
 void fc_internal_set_error(const char* msg);
 
 // A streaming push split into pieces, for the serving engine (fc_server.cu): the trial is

@@ -130,6 +130,8 @@ extern "C" fc_status fc_window_networks_noalloc(const float* spectra, int n_tria
     pa.slots = n_trials;
     pa.n = n_nodes;
     pa.B = n_bins;
+    pa.fsel0 = 0;
+    pa.fsel1 = n_bins;
     pa.W = n_trials;
     pa.ntp = ntp;
     pa.P = P;

@@ -3,18 +3,25 @@
 // The paper's online pipeline adds every newly arriving trial to the network as it comes
 // (Methods 2.5; Results 3.2.3) and must keep up with the acquisition (Results 3.2.3: a
 // 500-sample block at 1,792 Hz leaves 280 ms). Here many sessions share one GPU: each
-// arriving trial of any session is a request; a worker thread takes, at every tick, the
-// oldest pending trial of each session that has one (oldest arrivals first across
-// sessions, at most max_batch sessions) and runs them through ONE launch of the
-// persistent streaming kernel (their small per-session kernels - validation, spectrum,
-// per-node sums, commit - around it). Trials that arrive while a launch runs join the
-// next tick; two launches may be in flight, so the host staging of the next batch
-// overlaps the device work of the current one. Session state stays resident; sessions
-// are admitted against a device-memory budget.
+// arriving trial of any session is a request. A worker thread runs ticks; every tick is
+// ONE launch of the persistent streaming kernel over a share of the state of up to 32
+// sessions, with each session's small kernels (validation, spectrum, per-node sums before
+// its first share of a trial; re-sum slice and commit after its last) around it on the
+// same stream.
 //
-// In plain mode (the comparison baseline) every trial is handled alone, in arrival
-// order, as a full-window FP32 recompute (FC_MODE_FULL), with no batching and no
-// streaming sums.
+// A launch carries at most `launch_blocks` state blocks (one tile pair x one bin, 106 KB
+// of HBM traffic each). A trial whose push is larger is split over several launches (its
+// units are walked in order; the window position only advances at the commit after the
+// last share), so a 5,000-node session's ~10 ms push does not hold back the trials of
+// small sessions that arrive meanwhile: the oldest unfinished push gets at least a quarter
+// of the budget, then pushes that fit the remaining budget go in whole, shortest first, and
+// what is left goes to the remaining pushes, oldest first. Trials that arrive while a
+// launch runs join the next tick; two launches may be in flight, so the host staging of
+// one overlaps the device work of the other. Session state stays resident; sessions are
+// admitted against a device-memory budget.
+//
+// In plain mode (the comparison baseline) every trial is handled alone, in arrival order,
+// as a full-window FP32 recompute (FC_MODE_FULL), with no batching and no streaming sums.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -29,6 +36,8 @@
 
 namespace {
 
+constexpr long long kDefaultLaunchBlocks = 65536;  // ~7 GB of state traffic, ~1.2 ms on GB300
+
 double now_ms() {
     using namespace std::chrono;
     static const steady_clock::time_point t0 = steady_clock::now();
@@ -37,8 +46,8 @@ double now_ms() {
 
 struct PendingTrial {
     std::vector<float> x;
-    double arrival;
-    long long seq;
+    double arrival = 0.0;
+    long long seq = 0;
 };
 
 struct SrvSession {
@@ -47,22 +56,40 @@ struct SrvSession {
     size_t bytes = 0;
     long long pair_bins = 0;
     size_t trial_floats = 0;
+    long long units = 0;  // streaming-kernel units of one push (tile pairs, all bins each)
     std::deque<PendingTrial> queue;
-    long long submitted = 0, completed = 0, in_flight = 0;
-    float* pinned[2] = {nullptr, nullptr};
-    float* pinned_scale = nullptr;  // the session's prescale, read back after its first pushes
+    long long submitted = 0, completed = 0;
+    long long in_flight = 0;  // trials taken from the queue and not yet retired
+    // the push in progress, whose units may span several launches (worker only)
+    bool active = false;
+    PendingTrial cur;
+    long long next_unit = 0;  // first unit not yet planned
+    // units of the push in progress already enqueued; nonzero: the device state holds a
+    // partly applied push (guarded by dev_mu)
+    long long partial = 0;
+    float* pinned[2] = {nullptr, nullptr};  // trial staging, by tick parity
+    FcCtrl* pinned_ctrl = nullptr;          // [2] control-block read-back, by tick parity
+    long long rejected_seen = 0;
     bool closing = false;
 };
 
-struct Item {
+struct Part {  // one session's share of a tick
     SrvSession* ss;
-    PendingTrial t;
-    int launch_sessions = 1;  // sessions that shared this trial's streaming-kernel launch
+    long long u0, nu;
+    bool start, finish, single;
+};
+
+struct Done {  // a trial whose last share is in this tick
+    SrvSession* ss;
+    long long seq;
+    double arrival;
+    int launch_sessions;
 };
 
 struct InFlight {
     cudaEvent_t ev = nullptr;
-    std::vector<Item> items;
+    int slot = 0;
+    std::vector<Done> done;
 };
 
 }  // namespace
@@ -72,8 +99,9 @@ struct fc_server {
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 152;
-    std::mutex mu;                  // sessions, queues, results, stats
-    std::mutex dev_mu;              // device work on sessions (worker enqueue vs API calls)
+    // lock order: dev_mu before mu
+    std::mutex mu;      // sessions, queues, plans, results, stats
+    std::mutex dev_mu;  // device work on sessions (worker enqueue / retire vs API calls)
     std::condition_variable cv_work, cv_done;
     std::map<int, SrvSession*> sessions;
     int next_id = 1;
@@ -95,170 +123,238 @@ fc_status sfail(fc_status st, const char* msg) {
     return st;
 }
 
-// Enqueue one batch on the server stream (called by the worker with dev_mu held).
-fc_status enqueue_batch(fc_server* sv, std::vector<Item>& items, InFlight& fl) {
+// Choose this tick's shares (worker, mu held). Starts the next queued trial of every idle
+// session, then fills the launch's block budget.
+std::vector<Part> plan_tick(fc_server* sv) {
+    std::vector<Part> plan;
+    std::vector<SrvSession*> cand;
+    for (auto& kv : sv->sessions) {
+        SrvSession* ss = kv.second;
+        if (!ss->active && !ss->queue.empty()) {
+            ss->cur = std::move(ss->queue.front());
+            ss->queue.pop_front();
+            ss->active = true;
+            ss->next_unit = 0;
+            ss->in_flight++;
+        }
+        if (ss->active && ss->next_unit < ss->units) cand.push_back(ss);
+    }
+    if (cand.empty()) return plan;
+    auto oldest_first = [](SrvSession* a, SrvSession* b) { return a->cur.arrival < b->cur.arrival; };
+    std::sort(cand.begin(), cand.end(), oldest_first);
+    if (sv->cfg.plain) {  // one trial, in arrival order, as a full-window recompute
+        SrvSession* ss = cand.front();
+        plan.push_back(Part{ss, 0, ss->units, true, true, true});
+        ss->next_unit = ss->units;
+        return plan;
+    }
+    const int max_batch = sv->cfg.max_batch > 0 ? std::min(sv->cfg.max_batch, FC_MAX_BATCH) : FC_MAX_BATCH;
+    const long long budget = sv->cfg.launch_blocks < 0
+                                 ? (1LL << 60)
+                                 : (sv->cfg.launch_blocks > 0 ? sv->cfg.launch_blocks : kDefaultLaunchBlocks);
+    long long left = budget;
+    auto rem_units = [](const SrvSession* ss) { return ss->units - ss->next_unit; };
+    auto take = [&](SrvSession* ss, long long nu) {
+        const bool single = ss->next_unit == 0 && fc_push_needs_single(ss->s);
+        if (single) nu = ss->units;  // first pushes (calibration) and the like run whole
+        plan.push_back(Part{ss, ss->next_unit, nu, ss->next_unit == 0, ss->next_unit + nu == ss->units, single});
+        ss->next_unit += nu;
+        left -= nu * ss->s->B;
+    };
+    // 1. the oldest unfinished push: at least a quarter of the budget (no starvation)
+    SrvSession* oldest = cand.front();
+    take(oldest, std::min(rem_units(oldest), std::max(1LL, (budget / 4) / oldest->s->B)));
+    // 2. whole pushes that fit, shortest first
+    std::vector<SrvSession*> by_size(cand.begin() + 1, cand.end());
+    std::stable_sort(by_size.begin(), by_size.end(), [&](const SrvSession* a, const SrvSession* b) {
+        return rem_units(a) * a->s->B < rem_units(b) * b->s->B;
+    });
+    for (SrvSession* ss : by_size) {
+        if ((int)plan.size() >= max_batch) break;
+        if (rem_units(ss) * ss->s->B <= left) take(ss, rem_units(ss));
+    }
+    // 3. the rest of the budget, oldest first (extending a share already planned)
+    for (SrvSession* ss : cand) {
+        const long long can = std::min(rem_units(ss), left / ss->s->B);
+        if (can <= 0) continue;
+        Part* mine = nullptr;
+        for (Part& p : plan)
+            if (p.ss == ss) mine = &p;
+        if (mine) {
+            if (mine->single) continue;
+            mine->nu += can;
+            ss->next_unit += can;
+            mine->finish = ss->next_unit == ss->units;
+            left -= can * ss->s->B;
+        } else if ((int)plan.size() < max_batch && !(ss->next_unit == 0 && fc_push_needs_single(ss->s))) {
+            take(ss, can);
+        }
+    }
+    return plan;
+}
+
+// Enqueue one tick on the server stream (worker, dev_mu held).
+fc_status enqueue_tick(fc_server* sv, const std::vector<Part>& plan, InFlight& fl) {
     const int slot = sv->parity;
     sv->parity ^= 1;
-    for (Item& it : items) {
-        SrvSession* ss = it.ss;
-        std::memcpy(ss->pinned[slot], it.t.x.data(), ss->trial_floats * sizeof(float));
+    fl.slot = slot;
+    for (const Part& p : plan) {
+        if (!p.start) continue;
+        SrvSession* ss = p.ss;
+        std::memcpy(ss->pinned[slot], ss->cur.x.data(), ss->trial_floats * sizeof(float));
         cudaError_t e = cudaMemcpyAsync(ss->s->x_stage, ss->pinned[slot], ss->trial_floats * sizeof(float),
                                         cudaMemcpyHostToDevice, sv->stream);
         if (e != cudaSuccess) return sfail(FC_ERR_CUDA, cudaGetErrorString(e));
     }
-    if (sv->cfg.plain) {
-        for (Item& it : items) {
-            fc_status st = fc_push_single(it.ss->s, it.ss->s->x_stage);
+    StreamBatch b;
+    b.nsess = 0;
+    b.unit_prefix[0] = 0;
+    for (const Part& p : plan) {
+        fc_session* s = p.ss->s;
+        if (p.single) {
+            fc_status st = fc_push_single(s, s->x_stage);
             if (st != FC_OK) return st;
+            continue;
         }
-    } else {
-        StreamBatch b;
-        b.nsess = 0;
-        b.unit_prefix[0] = 0;
-        std::vector<fc_session*> batched;
-        for (Item& it : items) {
-            fc_session* s = it.ss->s;
-            if (fc_push_needs_single(s)) {
-                fc_status st = fc_push_single(s, s->x_stage);
-                if (st != FC_OK) return st;
-                if (!s->calibrated) {
-                    // the push set the prescale on the device; read it back with the batch
-                    cudaError_t e = cudaMemcpyAsync(it.ss->pinned_scale, &s->ctrl->scale, sizeof(float),
-                                                    cudaMemcpyDeviceToHost, sv->stream);
-                    if (e != cudaSuccess) return sfail(FC_ERR_CUDA, cudaGetErrorString(e));
-                }
-                continue;
-            }
+        if (p.start) {
             fc_status st = fc_push_stage_pre(s, s->x_stage);
             if (st != FC_OK) return st;
-            const PairArgs pa = fc_push_stream_args(s);
-            b.a[b.nsess] = pa;
-            b.unit_prefix[b.nsess + 1] = b.unit_prefix[b.nsess] + pa.ntp * pa.groups;
-            ++b.nsess;
-            batched.push_back(s);
         }
-        for (Item& it : items)
-            if (std::find(batched.begin(), batched.end(), it.ss->s) != batched.end()) it.launch_sessions = b.nsess;
-        if (b.nsess > 0) {
-            cudaError_t e = launch_stream_batch(b, 2 * sv->num_sms, sv->stream);
-            if (e != cudaSuccess) return sfail(FC_ERR_CUDA, cudaGetErrorString(e));
-            fc_count_launch(batched[0]);
-            for (fc_session* s : batched) {
-                fc_status st = fc_push_stage_post(s);
+        PairArgs pa = fc_push_stream_args(s);
+        pa.u0 = (int)p.u0;
+        b.a[b.nsess] = pa;
+        b.unit_prefix[b.nsess + 1] = b.unit_prefix[b.nsess] + (int)p.nu;
+        ++b.nsess;
+    }
+    if (b.nsess > 0) {
+        cudaError_t e = launch_stream_batch(b, 2 * sv->num_sms, sv->stream);
+        if (e != cudaSuccess) return sfail(FC_ERR_CUDA, cudaGetErrorString(e));
+    }
+    for (const Part& p : plan) {
+        SrvSession* ss = p.ss;
+        if (!p.single) {
+            fc_count_launch(ss->s);
+            ss->partial = p.finish ? 0 : p.u0 + p.nu;
+            if (p.finish) {
+                fc_status st = fc_push_stage_post(ss->s);
                 if (st != FC_OK) return st;
             }
+        }
+        if (p.finish) {
+            // control block after the commit: prescale (calibration) and rejection count
+            cudaError_t e = cudaMemcpyAsync(&ss->pinned_ctrl[slot], ss->s->ctrl, sizeof(FcCtrl),
+                                            cudaMemcpyDeviceToHost, sv->stream);
+            if (e != cudaSuccess) return sfail(FC_ERR_CUDA, cudaGetErrorString(e));
         }
     }
     if (!sv->event_pool.empty()) {
         fl.ev = sv->event_pool.back();
         sv->event_pool.pop_back();
-    } else {
-        cudaEventCreateWithFlags(&fl.ev, cudaEventDisableTiming);
+    } else if (cudaEventCreateWithFlags(&fl.ev, cudaEventDisableTiming) != cudaSuccess) {
+        fl.ev = nullptr;
+        return sfail(FC_ERR_CUDA, "event creation failed");
     }
     cudaEventRecord(fl.ev, sv->stream);
-    fl.items = std::move(items);
     return FC_OK;
 }
 
 void retire(fc_server* sv, InFlight& fl) {
     cudaEventSynchronize(fl.ev);
     const double done = now_ms();
-    {
-        // a session whose prescale is now known joins the batched launches from its next trial
-        std::lock_guard<std::mutex> dk(sv->dev_mu);
-        for (Item& it : fl.items)
-            if (!it.ss->s->calibrated && *it.ss->pinned_scale != 0.f) it.ss->s->calibrated = true;
-    }
+    std::lock_guard<std::mutex> dk(sv->dev_mu);
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->event_pool.push_back(fl.ev);
-    for (Item& it : fl.items) {
+    for (const Done& d : fl.done) {
+        SrvSession* ss = d.ss;
+        const FcCtrl& c = ss->pinned_ctrl[fl.slot];
+        // a session whose prescale is known joins the batched launches from its next trial
+        if (!ss->s->calibrated && c.scale != 0.f) ss->s->calibrated = true;
         fc_result r;
-        r.session = it.ss->id;
-        r.seq = it.t.seq;
+        r.session = ss->id;
+        r.seq = d.seq;
         r.status = FC_OK;
-        r.arrival_ms = it.t.arrival;
+        if (c.rejected > ss->rejected_seen) r.status = FC_ERR_NONFINITE;
+        if (c.timeout) r.status = FC_ERR_TIMEOUT;
+        ss->rejected_seen = c.rejected;
+        r.arrival_ms = d.arrival;
         r.done_ms = done;
-        r.batch = it.launch_sessions;
+        r.batch = d.launch_sessions;
         sv->results.push_back(r);
-        it.ss->completed++;
-        it.ss->in_flight--;
+        ss->completed++;
+        ss->in_flight--;
         sv->stats.completed++;
-        sv->stats.pair_bin_updates += it.ss->pair_bins;
+        if (r.status == FC_OK) sv->stats.pair_bin_updates += ss->pair_bins;
     }
     sv->cv_done.notify_all();
 }
 
 void worker_main(fc_server* sv) {
     cudaSetDevice(sv->device);
-    const int max_batch = sv->cfg.plain ? 1 : (sv->cfg.max_batch > 0 ? std::min(sv->cfg.max_batch, FC_MAX_BATCH)
-                                                                       : FC_MAX_BATCH);
     for (;;) {
-        std::vector<Item> items;
+        std::vector<Part> plan;
+        InFlight fl;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
             auto has_work = [&]() {
-                for (auto& kv : sv->sessions)
-                    if (!kv.second->queue.empty()) return true;
+                for (auto& kv : sv->sessions) {
+                    const SrvSession* ss = kv.second;
+                    if (!ss->queue.empty() || (ss->active && ss->next_unit < ss->units)) return true;
+                }
                 return false;
             };
             if (sv->inflight.empty())
                 sv->cv_work.wait_for(lk, std::chrono::milliseconds(5), [&]() { return sv->stop || has_work(); });
             if (sv->stop && !has_work() && sv->inflight.empty()) break;
-            // oldest arrival first across sessions, one trial per session per launch
-            std::vector<SrvSession*> cand;
-            for (auto& kv : sv->sessions)
-                if (!kv.second->queue.empty()) cand.push_back(kv.second);
-            std::sort(cand.begin(), cand.end(), [](SrvSession* a, SrvSession* b) {
-                return a->queue.front().arrival < b->queue.front().arrival;
-            });
-            if ((int)cand.size() > max_batch) cand.resize(max_batch);
-            for (SrvSession* ss : cand) {
-                items.push_back(Item{ss, std::move(ss->queue.front())});
-                ss->queue.pop_front();
-                ss->in_flight++;
+            plan = plan_tick(sv);
+            int batched = 0;
+            for (const Part& p : plan) batched += p.single ? 0 : 1;
+            for (const Part& p : plan) {
+                if (!p.finish) continue;
+                fl.done.push_back(Done{p.ss, p.ss->cur.seq, p.ss->cur.arrival, p.single ? 1 : batched});
+                p.ss->active = false;  // its next trial may start next tick (ordered on the stream)
             }
         }
-        if (!items.empty()) {
-            InFlight fl;
-            const int n_items = (int)items.size();
+        if (!plan.empty()) {
             fc_status st;
             {
                 std::lock_guard<std::mutex> dk(sv->dev_mu);
-                st = enqueue_batch(sv, items, fl);
+                st = enqueue_tick(sv, plan, fl);
             }
             if (st != FC_OK) {
                 std::lock_guard<std::mutex> lk(sv->mu);
                 sv->worker_error = fc_last_error();
-                for (Item& it : items) it.ss->in_flight--;
+                for (const Done& d : fl.done) d.ss->in_flight--;
+                if (fl.ev) sv->event_pool.push_back(fl.ev);
                 sv->cv_done.notify_all();
                 continue;
             }
             {
                 std::lock_guard<std::mutex> lk(sv->mu);
                 sv->stats.launches++;
-                sv->stats.batched_trials += n_items;
+                sv->stats.batched_trials += (long long)plan.size();
             }
             sv->inflight.push_back(std::move(fl));
         }
         // keep at most two launches in flight; retire the oldest when idle or full
-        while (!sv->inflight.empty() && (sv->inflight.size() >= 2 || items.empty())) {
+        while (!sv->inflight.empty() && (sv->inflight.size() >= 2 || plan.empty())) {
             retire(sv, sv->inflight.front());
             sv->inflight.pop_front();
-            if (!items.empty()) break;
+            if (!plan.empty()) break;
         }
     }
-}
-
-void free_pinned(SrvSession* ss) {
-    for (int k = 0; k < 2; ++k)
-        if (ss->pinned[k]) cudaFreeHost(ss->pinned[k]);
-    if (ss->pinned_scale) cudaFreeHost(ss->pinned_scale);
-    ss->pinned[0] = ss->pinned[1] = ss->pinned_scale = nullptr;
 }
 
 SrvSession* find_session(fc_server* sv, int id) {
     auto it = sv->sessions.find(id);
     return it == sv->sessions.end() ? nullptr : it->second;
+}
+
+void free_pinned(SrvSession* ss) {
+    for (int k = 0; k < 2; ++k)
+        if (ss->pinned[k]) cudaFreeHost(ss->pinned[k]);
+    if (ss->pinned_ctrl) cudaFreeHost(ss->pinned_ctrl);
+    ss->pinned[0] = ss->pinned[1] = nullptr;
+    ss->pinned_ctrl = nullptr;
 }
 
 }  // namespace
@@ -338,18 +434,22 @@ fc_status fc_server_open(fc_server* sv, int n_nodes, int n_samples, double fs, f
     ss->bytes = need;
     ss->pair_bins = s->P * s->B;
     ss->trial_floats = (size_t)n_nodes * n_samples;
-    bool pinned_ok = cudaMallocHost(&ss->pinned_scale, sizeof(float)) == cudaSuccess;
+    ss->units = sv->cfg.plain ? 1 : (long long)s->ntp * s->stream_groups;
+    bool pinned_ok = cudaMallocHost(&ss->pinned_ctrl, 2 * sizeof(FcCtrl)) == cudaSuccess;
     for (int k = 0; k < 2 && pinned_ok; ++k)
         pinned_ok = cudaMallocHost(&ss->pinned[k], ss->trial_floats * sizeof(float)) == cudaSuccess;
     if (!pinned_ok) {
         free_pinned(ss);
-        fc_session_destroy(s);
+        {
+            std::lock_guard<std::mutex> dk(sv->dev_mu);
+            fc_session_destroy(s);
+        }
         delete ss;
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->used -= need;
         return sfail(FC_ERR_OUT_OF_MEMORY, "pinned staging allocation failed");
     }
-    *ss->pinned_scale = 0.f;
+    std::memset(ss->pinned_ctrl, 0, 2 * sizeof(FcCtrl));
     std::lock_guard<std::mutex> lk(sv->mu);
     ss->id = sv->next_id++;
     sv->sessions[ss->id] = ss;
@@ -359,12 +459,19 @@ fc_status fc_server_open(fc_server* sv, int n_nodes, int n_samples, double fs, f
 
 fc_status fc_server_submit(fc_server* sv, int session_id, const float* x, double arrival_ms) {
     if (!sv || !x) return sfail(FC_ERR_INVALID_ARG, "NULL argument");
+    size_t nf = 0;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        SrvSession* ss = find_session(sv, session_id);
+        if (!ss || ss->closing) return sfail(FC_ERR_INVALID_ARG, "unknown or closing session");
+        nf = ss->trial_floats;
+    }
+    PendingTrial t;
+    t.x.assign(x, x + nf);  // copied outside the lock
+    t.arrival = arrival_ms;
     std::lock_guard<std::mutex> lk(sv->mu);
     SrvSession* ss = find_session(sv, session_id);
     if (!ss || ss->closing) return sfail(FC_ERR_INVALID_ARG, "unknown or closing session");
-    PendingTrial t;
-    t.x.assign(x, x + ss->trial_floats);
-    t.arrival = arrival_ms;
     t.seq = ss->submitted++;
     ss->queue.push_back(std::move(t));
     sv->stats.submitted++;
@@ -407,15 +514,32 @@ fc_status fc_server_drain(fc_server* sv, int timeout_ms) {
 
 fc_status fc_server_get_network(fc_server* sv, int session_id, uint32_t metric, float* out, size_t out_len) {
     if (!sv || !out) return sfail(FC_ERR_INVALID_ARG, "NULL argument");
-    fc_session* s = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(sv->mu);
-        SrvSession* ss = find_session(sv, session_id);
-        if (!ss) return sfail(FC_ERR_INVALID_ARG, "unknown session");
-        s = ss->s;
+    // the network after the last trial whose push is fully enqueued: wait while the device
+    // state holds a partly applied push (its remaining shares follow within a few ticks)
+    const double t_end = now_ms() + 60000.0;
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> dk(sv->dev_mu);
+            fc_session* s = nullptr;
+            bool partial = false;
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                SrvSession* ss = find_session(sv, session_id);
+                if (!ss) return sfail(FC_ERR_INVALID_ARG, "unknown session");
+                s = ss->s;
+                partial = ss->partial != 0;
+            }
+            if (!partial) {
+                fc_status st = fc_get_network(s, metric, 1, out, out_len, 0, nullptr);
+                // a rejected trial was already reported through its fc_result; the session's
+                // one-time latch is consumed here and the network read again
+                if (st == FC_ERR_NONFINITE) st = fc_get_network(s, metric, 1, out, out_len, 0, nullptr);
+                return st;
+            }
+        }
+        if (now_ms() > t_end) return sfail(FC_ERR_TIMEOUT, "the session stayed in the middle of a push");
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
-    std::lock_guard<std::mutex> dk(sv->dev_mu);
-    return fc_get_network(s, metric, 1, out, out_len, 0, nullptr);
 }
 
 fc_status fc_server_close(fc_server* sv, int session_id) {

@@ -22,8 +22,11 @@
 #include <cuda_fp16.h>
 
 #include "fc_internal.h"
+#include "mbar.cuh"
 
 namespace {
+
+using namespace fcmbar;
 
 constexpr int TILE = 128;             // nodes per tile (M = N = 128)
 constexpr int CHUNK_BYTES = 16384;     // 128 rows x 128 bytes of K
@@ -31,38 +34,6 @@ constexpr int NOPS = 6;                // XR(a), XI(a), UR(a), UI(a), XR(b), UR(
 constexpr int STAGE_BYTES = NOPS * CHUNK_BYTES;
 constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 128;  // + barriers and the TMEM address
 constexpr uint32_t TMEM_COLS = 512;    // 4 accumulators x 128 FP32 columns
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (int i = 0; i < (1 << 22); ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
 
 // Shared-memory matrix descriptor: K-major, no swizzle; LBO = 128 B (next core matrix
 // along K), SBO = 1024 B (next 8-row group), descriptor version 1.
@@ -351,12 +322,12 @@ __global__ void k_herk_band(HerkArgs a) {
     if (c->bad) return;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.P) return;
-    const float invB = 1.0f / (float)a.B;
+    const float invB = 1.0f / (float)(a.fsel1 - a.fsel0);
     for (int m = 0; m < 3; ++m) {
         const int mi = m == 0 ? MI_COH : m == 1 ? MI_IMAGCOHY : MI_PLV;
         if (!(a.mask & (1u << mi))) continue;
         float s = 0.f;
-        for (int f = 0; f < a.B; ++f) s = __fadd_rn(s, a.bins_out[((size_t)f * 3 + m) * a.P + p]);
+        for (int f = a.fsel0; f < a.fsel1; ++f) s = __fadd_rn(s, a.bins_out[((size_t)f * 3 + m) * a.P + p]);
         a.net[(size_t)mi * a.P + p] = __fmul_rn(s, invB);
     }
 }

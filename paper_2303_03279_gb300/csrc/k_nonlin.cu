@@ -16,6 +16,8 @@
 #include "pair_common.cuh"
 #include "terms.cuh"
 
+#include <type_traits>
+
 namespace {
 
 using namespace fcpair;
@@ -58,6 +60,7 @@ __global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
         for (int k0 = 0; k0 < K; k0 += NK) {
             const int kn = min(NK, K - k0);
             __syncthreads();
+            bool any_tiny = false;
             for (int e = tid; e < kn * 2 * FC_T; e += 256) {
                 const int kk = e / (2 * FC_T), l = e % (2 * FC_T);
                 const int node = l < FC_T ? ta * FC_T + l : tb * FC_T + l - FC_T;
@@ -65,38 +68,48 @@ __global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
                 float2 X = make_float2(0.f, 0.f);
                 if (node < a.n) X = a.ring[((size_t)(trial % a.slots) * a.B + f) * a.n + node];
                 sx[kk][l] = X;
-                stiny[kk][l] = node_tiny(X) ? 1 : 0;
+                const bool tn = node_tiny(X);
+                stiny[kk][l] = tn ? 1 : 0;
+                any_tiny |= tn;
             }
-            __syncthreads();
+            // chunks without a tiny node (the rule) run a loop with no FP64 branch at all
+            const bool chunk_tiny = __syncthreads_or(any_tiny ? 1 : 0) != 0;
             if (!vmask) continue;
             float p_im[4] = {0.f, 0.f, 0.f, 0.f}, p_sq[4] = {0.f, 0.f, 0.f, 0.f}, p_abs[4] = {0.f, 0.f, 0.f, 0.f};
             float p_sqe[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int kk = 0; kk < kn; ++kk) {
-                const float2 xi = sx[kk][li];
-                const bool ti = stiny[kk][li] != 0;
+            auto chunk = [&](auto tiny_c) {
+                constexpr bool TINY = decltype(tiny_c)::value;
+                for (int kk = 0; kk < kn; ++kk) {
+                    const float2 xi = sx[kk][li];
+                    const bool ti = TINY && stiny[kk][li] != 0;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float2 xj = sx[kk][FC_T + lj0 + q];
-                    // Im(X_i X_j*) and its exact sign, as in pair_terms (terms.cuh)
-                    const float p = __fmul_rn(xi.y, xj.x), np = __fmul_rn(-xi.y, xj.x);
-                    const float qq = __fmul_rn(xi.x, xj.y), nq = __fmul_rn(-xi.x, xj.y);
-                    const float e = __fmaf_rn(xi.y, xj.x, np);
-                    const float nf = __fmaf_rn(-xi.x, xj.y, qq);
-                    const float d1 = __fadd_rn(p, nq), d2 = __fadd_rn(e, nf);
-                    float im = __fadd_rn(d1, d2);
-                    int sg = sign_of(d1 != 0.f ? d1 : d2);
-                    if (ti || stiny[kk][FC_T + lj0 + q]) im_sign_fp64(xi.x, xi.y, xj.x, xj.y, im, sg);
-                    s_sg[q] += sg;
-                    p_abs[q] = __fadd_rn(p_abs[q], fabsf(im));
-                    p_im[q] = __fadd_rn(p_im[q], im);
-                    // im^2 as an exact two-product (t + r): a lone nonzero term then gives
-                    // (sum |Im|)^2 - sum Im^2 = 0 exactly, as in the exact path
-                    float t, r;
-                    two_prod(im, im, t, r);
-                    p_sq[q] = __fadd_rn(p_sq[q], t);
-                    p_sqe[q] = __fadd_rn(p_sqe[q], r);
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 xj = sx[kk][FC_T + lj0 + q];
+                        // Im(X_i X_j*) and its exact sign, as in pair_terms (terms.cuh)
+                        const float p = __fmul_rn(xi.y, xj.x), np = __fmul_rn(-xi.y, xj.x);
+                        const float qq = __fmul_rn(xi.x, xj.y), nq = __fmul_rn(-xi.x, xj.y);
+                        const float e = __fmaf_rn(xi.y, xj.x, np);
+                        const float nf = __fmaf_rn(-xi.x, xj.y, qq);
+                        const float d1 = __fadd_rn(p, nq), d2 = __fadd_rn(e, nf);
+                        float im = __fadd_rn(d1, d2);
+                        int sg = sign_of(d1 != 0.f ? d1 : d2);
+                        if (TINY && (ti || stiny[kk][FC_T + lj0 + q])) im_sign_fp64(xi.x, xi.y, xj.x, xj.y, im, sg);
+                        s_sg[q] += sg;
+                        p_abs[q] = __fadd_rn(p_abs[q], fabsf(im));
+                        p_im[q] = __fadd_rn(p_im[q], im);
+                        // im^2 as an exact two-product (t + r): a lone nonzero term then gives
+                        // (sum |Im|)^2 - sum Im^2 = 0 exactly, as in the exact path
+                        float t, r;
+                        two_prod(im, im, t, r);
+                        p_sq[q] = __fadd_rn(p_sq[q], t);
+                        p_sqe[q] = __fadd_rn(p_sqe[q], r);
+                    }
                 }
-            }
+            };
+            if (chunk_tiny)
+                chunk(std::true_type{});
+            else
+                chunk(std::false_type{});
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 s_im[q] = df_add_f(s_im[q], p_im[q]);
@@ -104,7 +117,7 @@ __global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
                 s_abs[q] = df_add_f(s_abs[q], p_abs[q]);
             }
         }
-        if (vmask) {
+        if (vmask && f >= a.fsel0 && f < a.fsel1) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (!(vmask & (1u << q))) continue;

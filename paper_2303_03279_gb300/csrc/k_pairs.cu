@@ -14,6 +14,8 @@
 #include "terms.cuh"
 #include "pair_common.cuh"
 
+#include <type_traits>
+
 namespace {
 
 using namespace fcpair;
@@ -96,6 +98,7 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
         for (int k0 = 0; k0 < K; k0 += WK) {
             const int kn = min(WK, K - k0);
             __syncthreads();
+            bool any_tiny = false;
             for (int e = tid; e < WK * 2 * FC_T; e += 256) {
                 const int kk = e / (2 * FC_T), side = (e / FC_T) & 1, l = e % FC_T;
                 const int node = (side ? tb : ta) * FC_T + l;
@@ -107,10 +110,14 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
                 sn[kk][side][1][l] = X.y;
                 sn[kk][side][2][l] = u.x;
                 sn[kk][side][3][l] = u.y;
-                sn[kk][side][4][l] = node_tiny(X) ? 1.f : 0.f;
+                const bool tn = node_tiny(X);
+                sn[kk][side][4][l] = tn ? 1.f : 0.f;
+                any_tiny |= tn;
             }
-            __syncthreads();
-            if (vmask) {
+            // chunks without a tiny node (the rule) run a loop with no FP64 branch at all
+            const bool chunk_tiny = __syncthreads_or(any_tiny ? 1 : 0) != 0;
+            auto chunk = [&](auto tiny_c) {
+                constexpr bool TINY = decltype(tiny_c)::value;
                 for (int kk = 0; kk < kn; ++kk) {
                     const float (*r)[FC_T] = sn[kk][0];
                     const float (*cl)[FC_T] = sn[kk][1];
@@ -119,7 +126,7 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
                     for (int h = 0; h < 2; ++h) {
                         const int j = lj0 + 2 * h;
                         const float2 tj = *reinterpret_cast<const float2*>(&cl[4][j]);
-                        const PairTerms2 t = pair_terms2(rc, *reinterpret_cast<const float2*>(&cl[0][j]),
+                        const PairTerms2 t = pair_terms2<TINY>(rc, *reinterpret_cast<const float2*>(&cl[0][j]),
                                                          *reinterpret_cast<const float2*>(&cl[1][j]),
                                                          *reinterpret_cast<const float2*>(&cl[2][j]),
                                                          *reinterpret_cast<const float2*>(&cl[3][j]), tj.x != 0.f,
@@ -138,6 +145,12 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
                         s[2 * h + 1] += t.s1;
                     }
                 }
+            };
+            if (vmask) {
+                if (chunk_tiny)
+                    chunk(std::true_type{});
+                else
+                    chunk(std::false_type{});
             }
         }
         __syncthreads();  // sinv visible
@@ -170,7 +183,7 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
                     finalize_bin(v[q], s[q], inv_i, sinv[1][lj0 + q], kc, m);
                     if (bins_out) {
                         bins_out[(size_t)f * a.P + packed_index(gi, gj0 + q, a.n)] = m[bins_metric - 2];
-                    } else {
+                    } else if (f >= a.fsel0 && f < a.fsel1) {
 #pragma unroll
                         for (int mm = 0; mm < 7; ++mm) band[mm][q] = __fadd_rn(band[mm][q], m[mm]);
                     }
@@ -215,7 +228,7 @@ __global__ void k_band_reduce(PairArgs a) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.P) return;
     if (a.ctrl->bad) return;
-    const float invB = 1.0f / (float)a.B;
+    const float invB = 1.0f / (float)(a.fsel1 - a.fsel0);
     for (int m = 0; m < 7; ++m) {
         if (!(a.mask & (1u << (m + 2)))) continue;
         float s = 0.f;

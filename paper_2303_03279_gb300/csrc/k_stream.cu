@@ -22,10 +22,13 @@
 #include "fc_internal.h"
 #include "pair_common.cuh"
 #include "terms.cuh"
+#include "mbar.cuh"
+
 
 namespace {
 
 using namespace fcpair;
+using namespace fcmbar;
 
 constexpr uint32_t BLK_BYTES = FC_BLOCK_WORDS * 4;  // 53,248
 // per stage: 4 node sets (new row, new col, old row, old col negated) x 32 nodes of
@@ -35,45 +38,6 @@ constexpr int STAGE_WORDS = 4 * SET_WORDS + 2 * FC_T;
 constexpr int OFF_MBAR = 2 * BLK_BYTES;
 constexpr int OFF_STAGE = OFF_MBAR + 16;
 constexpr int SMEM_BYTES = OFF_STAGE + 2 * STAGE_WORDS * 4;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: false after ~2^22 polls (each poll may suspend the thread briefly).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (int i = 0; i < (1 << 22); ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
 
 struct Step {
     int u;   // unit index over the whole batch
@@ -128,9 +92,9 @@ __global__ void __launch_bounds__(256, 2) k_stream(const StreamBatch batch) {
         if (u >= units) return r;
         if (MULTI) {
             while (r.s + 1 < batch.nsess && u >= batch.unit_prefix[r.s + 1]) ++r.s;
-            r.lu = u - batch.unit_prefix[r.s];
+            r.lu = u - batch.unit_prefix[r.s] + sess(r.s).u0;
         } else {
-            r.lu = u;
+            r.lu = u + sess(0).u0;
         }
         const PairArgs& A = sess(r.s);
         r.f = A.groups == 1 ? 0 : (r.lu % A.groups) * A.group_bins;
@@ -311,7 +275,7 @@ __global__ void __launch_bounds__(256, 2) k_stream(const StreamBatch batch) {
                     }
                     if (h) { sg.z = s0; sg.w = s1; } else { sg.x = s0; sg.y = s1; }
                 }
-                if (a.finalize) {
+                if (a.finalize && cur.f >= a.fsel0 && cur.f < a.fsel1) {
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         if (!(vmask & (1u << (2 * h + e)))) continue;

@@ -94,7 +94,7 @@ __device__ __forceinline__ void finalize_bin(const df32* f, int sign, float inv_
 
 __device__ __forceinline__ void write_band(const PairArgs& a, int g, const float (*band)[4],
                                            int gi, int gj0, unsigned vmask, int nbins_group) {
-    const float invB = 1.0f / (float)a.B;
+    const float invB = 1.0f / (float)(a.fsel1 - a.fsel0);
     for (int m = 0; m < 7; ++m) {
         if (!(a.mask & (1u << (m + 2)))) continue;
         if (a.groups == 1) {

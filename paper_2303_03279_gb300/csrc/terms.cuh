@@ -49,6 +49,18 @@ __device__ __forceinline__ void im_sign_fp64(float ai, float bi, float aj, float
 
 __device__ __forceinline__ int sign_of(float t) { return (t > 0.f) - (t < 0.f); }
 
+// The same FP64 evaluation kept out of line: a call is never if-converted, so a kernel that
+// cannot tell tiny nodes apart in advance pays for it only when a node is tiny.
+struct ImSign {
+    float im;
+    int s;
+};
+static __device__ __noinline__ ImSign im_sign_fp64_call(float ai, float bi, float aj, float bj) {
+    ImSign v;
+    im_sign_fp64(ai, bi, aj, bj, v.im, v.s);
+    return v;
+}
+
 struct PairTerms {
     float re;  // Re(X_i X_j*)
     float im;  // Im(X_i X_j*), the correctly signed, nearly correctly rounded value
@@ -103,6 +115,9 @@ struct PairTerms2 {
 };
 
 // Packed form for pairs (i, j0) and (i, j1): aj = (a_j0, a_j1), bj = (b_j0, b_j1), ...
+// TINY = false: the caller knows that none of the nodes is tiny, so the FP64 branch is
+// not compiled in (it would otherwise be if-converted into the hot loop).
+template <bool TINY = true>
 __device__ __forceinline__ PairTerms2 pair_terms2(const RowConst& r, float2 aj, float2 bj, float2 uaj, float2 ubj,
                                                   bool tiny0, bool tiny1) {
     PairTerms2 t;
@@ -119,8 +134,16 @@ __device__ __forceinline__ PairTerms2 pair_terms2(const RowConst& r, float2 aj, 
     t.im = add2(d1, d2);
     t.s0 = sign_of(d1.x != 0.f ? d1.x : d2.x);
     t.s1 = sign_of(d1.y != 0.f ? d1.y : d2.y);
-    if (r.tiny || tiny0) im_sign_fp64(r.as, r.bs, aj.x, bj.x, t.im.x, t.s0);
-    if (r.tiny || tiny1) im_sign_fp64(r.as, r.bs, aj.y, bj.y, t.im.y, t.s1);
+    if (TINY && (r.tiny || tiny0)) {
+        const ImSign v = im_sign_fp64_call(r.as, r.bs, aj.x, bj.x);
+        t.im.x = v.im;
+        t.s0 = v.s;
+    }
+    if (TINY && (r.tiny || tiny1)) {
+        const ImSign v = im_sign_fp64_call(r.as, r.bs, aj.y, bj.y);
+        t.im.y = v.im;
+        t.s1 = v.s;
+    }
     t.ure = fma2(r.ua, uaj, mul2(r.ub, ubj));
     t.uim = fma2(r.ub, uaj, mul2(r.nua, ubj));
     return t;

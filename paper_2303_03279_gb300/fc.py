@@ -39,7 +39,7 @@ FC_PREC_FP32, FC_PREC_TF32, FC_PREC_BF16, FC_PREC_FP16 = 0, 1, 2, 3
 FC_MODE_STREAM, FC_MODE_FULL = 0, 1
 
 FC_K_NAMES = ("spectrum", "calibrate", "node", "stream", "window", "herk_tc", "band_reduce",
-              "cor", "xcor", "other")
+              "cor", "xcor", "project", "other")
 FC_ACC_FIELDS = {"csd_re": 0, "csd_im": 1, "u_re": 2, "u_im": 3, "abs": 4, "sq": 5, "sign": 6,
                  "psd": 7, "cor": 8, "xcor": 9}
 
@@ -70,8 +70,13 @@ class fc_kernel_time(C.Structure):
     _fields_ = [("launches", C.c_int), ("total_ms", C.c_double)]
 
 
+class fc_top_info(C.Structure):
+    _fields_ = [("max_abs", C.c_float), ("threshold", C.c_float), ("kept", C.c_longlong)]
+
+
 class fc_server_config(C.Structure):
-    _fields_ = [("hbm_budget", C.c_size_t), ("max_batch", C.c_int), ("plain", C.c_int)]
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_batch", C.c_int), ("plain", C.c_int),
+                ("launch_blocks", C.c_int)]
 
 
 class fc_result(C.Structure):
@@ -104,8 +109,16 @@ _SIGNATURES = [
     ("fc_get_network", C.c_int, [C.c_void_p, C.c_uint32, C.c_int, C.c_void_p, C.c_size_t, C.c_int,
                                  C.POINTER(C.c_int)]),
     ("fc_get_network_bins", C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_size_t, C.c_int]),
+    ("fc_get_network_top", C.c_int, [C.c_void_p, C.c_uint32, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_int, C.POINTER(fc_top_info)]),
     ("fc_get_xcor_lags", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]),
     ("fc_set_metric_mask", C.c_int, [C.c_void_p, C.c_uint32]),
+    ("fc_set_band", C.c_int, [C.c_void_p, C.c_double, C.c_double]),
+    ("fc_debug_wait_probe", C.c_int, [C.c_void_p, C.c_double]),
+    ("fc_set_projection", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
+    ("fc_session_snapshot_size", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    ("fc_session_snapshot", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    ("fc_session_restore", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     ("fc_sync", C.c_int, [C.c_void_p]),
     ("fc_session_info", C.c_int, [C.c_void_p, C.POINTER(fc_info)]),
     ("fc_last_error", C.c_char_p, []),
@@ -226,6 +239,28 @@ def fc_get_network_bins(s, metric: int, out):
     _check(_LIB.fc_get_network_bins(s, int(metric), p, nel, dev))
 
 
+def fc_get_network_top(s, metric: int, percent: float, weights=None, degree=None, strength=None) -> dict:
+    """Normalized strongest-edge network, node degree and strength (host numpy or device
+    tensors, all on the same side); returns the fc_top_info fields."""
+    outs = [o for o in (weights, degree, strength) if o is not None]
+    on_dev = bool(outs) and type(outs[0]).__module__.startswith("torch") and outs[0].is_cuda
+    si = fc_session_info(s)
+    ptrs = []
+    for o, dt, need in ((weights, np.float32, si.pairs), (degree, np.int32, si.n_nodes),
+                        (strength, np.float32, si.n_nodes)):
+        if o is None:
+            ptrs.append(None)
+            continue
+        p, dev, nel = _ptr(o, dt)
+        if nel < need or bool(dev) != on_dev:
+            raise ValueError("outputs: weights [P], degree [n], strength [n], all on the host or all on the device")
+        ptrs.append(p)
+    pw, pd, ps = ptrs
+    info = fc_top_info()
+    _check(load().fc_get_network_top(s, int(metric), float(percent), pw, pd, ps, 1 if on_dev else 0, C.byref(info)))
+    return {"max_abs": info.max_abs, "threshold": info.threshold, "kept": info.kept}
+
+
 def fc_get_xcor_lags(s, out):
     p, dev, nel = _ptr(out, np.int32)
     _check(_LIB.fc_get_xcor_lags(s, p, nel, dev))
@@ -233,6 +268,37 @@ def fc_get_xcor_lags(s, out):
 
 def fc_set_metric_mask(s, mask: int):
     _check(_LIB.fc_set_metric_mask(s, int(mask)))
+
+
+def fc_set_band(s, f_lo: float, f_hi: float):
+    _check(load().fc_set_band(s, float(f_lo), float(f_hi)))
+
+
+def fc_session_snapshot(s) -> np.ndarray:
+    """The session's state as a host byte array."""
+    n = C.c_size_t(0)
+    _check(load().fc_session_snapshot_size(s, C.byref(n)))
+    buf = np.empty(n.value, np.uint8)
+    _check(_LIB.fc_session_snapshot(s, C.c_void_p(buf.ctypes.data), buf.size))
+    return buf
+
+
+def fc_session_restore(s, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(load().fc_session_restore(s, C.c_void_p(buf.ctypes.data), buf.size))
+
+
+def fc_set_projection(s, op=None):
+    """op: [n_nodes][n_channels] float32 (numpy or CUDA tensor), or None to remove it."""
+    if op is None:
+        _check(load().fc_set_projection(s, None, 0, 0))
+        return
+    p, dev, _ = _ptr(op, np.float32)
+    _check(load().fc_set_projection(s, p, int(op.shape[1]), dev))
+
+
+def fc_debug_wait_probe(s, limit_ms: float):
+    _check(load().fc_debug_wait_probe(s, float(limit_ms)))
 
 
 def fc_sync(s):
@@ -308,8 +374,8 @@ def fc_server_now_ms() -> float:
     return float(load().fc_server_now_ms())
 
 
-def fc_server_create(hbm_budget: int = 0, max_batch: int = 0, plain: bool = False):
-    cfg = fc_server_config(int(hbm_budget), int(max_batch), 1 if plain else 0)
+def fc_server_create(hbm_budget: int = 0, max_batch: int = 0, plain: bool = False, launch_blocks: int = 0):
+    cfg = fc_server_config(int(hbm_budget), int(max_batch), 1 if plain else 0, int(launch_blocks))
     out = C.c_void_p()
     _check(load().fc_server_create(C.byref(cfg), C.byref(out)))
     return out

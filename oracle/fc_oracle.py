@@ -51,7 +51,7 @@ __all__ = [
     "pair_sums_dense", "pair_sums_pairs", "metrics_from_sums", "band_average",
     "spectral_networks_dense", "spectral_networks_pairs",
     "cor_trial", "cor_network", "xcor_trial_pair", "xcor_trial_dense", "xcor_network",
-    "window_trials", "networks_dense", "network_top", "project",
+    "window_trials", "networks_dense", "network_top", "project", "fir_design", "fir_filter_stream",
 ]
 
 
@@ -473,3 +473,60 @@ def project(op, x):
     if X.ndim == 2:
         return M @ X
     return np.stack([M @ xk for xk in X])
+
+
+# ---------------------------------------------------------------------------
+# FIR filtering of the incoming stream (upstream of the connectivity path)
+
+
+def fir_design(fs: float, kind: str, f_lo: float, f_hi: float, transition_hz: float, n_taps: int = 0):
+    """Linear-phase FIR taps by the window method with a Hamming window.
+
+    §2.4 (Noise Reduction plug-in): FIR low-, high- and band-pass filters are designed
+    on the fly from the cut-off frequencies, the transition bandwidth and the number of
+    taps; every filter has a linear phase. Here: odd length T (from the transition width,
+    T ~ 3.3 fs / transition for a Hamming window, when n_taps is 0), centre m = (T - 1) / 2,
+    ideal responses as differences of sinc low-passes, times the Hamming window
+    w[k] = 0.54 - 0.46 cos(2 pi k / (T - 1)), unscaled.
+    """
+    if n_taps <= 0:
+        n_taps = int(math.ceil(3.3 * fs / transition_hz))
+    if n_taps % 2 == 0:
+        n_taps += 1
+    m = (n_taps - 1) / 2.0
+    k = np.arange(n_taps, dtype=np.float64)
+
+    def lowpass(fc):  # ideal low-pass with cut-off fc (Hz), sampled at k - m
+        return 2.0 * fc / fs * np.sinc(2.0 * fc / fs * (k - m))
+
+    if kind == "lowpass":
+        h = lowpass(f_hi)
+    elif kind == "highpass":
+        h = -lowpass(f_lo)
+        h[int(m)] += 1.0
+    elif kind == "bandpass":
+        h = lowpass(f_hi) - lowpass(f_lo)
+    else:
+        raise ValueError(kind)
+    w = 0.54 - 0.46 * np.cos(2.0 * np.pi * k / (n_taps - 1)) if n_taps > 1 else np.ones(1)
+    return h * w
+
+
+def fir_filter_stream(h, blocks):
+    """Causal FIR filtering of a multichannel stream delivered in blocks.
+
+    §2.4: the filter runs as an FFT convolution on blocks, and overlap-add carries the
+    convolution tail across block boundaries, so the output is the filtered continuous
+    stream: y[c, t] = sum_k h[k] x[c, t - k] with x = 0 before the first sample. Written
+    here as the convolution of the concatenated stream (a library step), then cut back into
+    the blocks.
+    """
+    h = np.asarray(h, np.float64)
+    x = np.concatenate([np.asarray(b, np.float64) for b in blocks], axis=1)
+    y = np.stack([np.convolve(xc, h)[: x.shape[1]] for xc in x])
+    out, o = [], 0
+    for b in blocks:
+        L = np.asarray(b).shape[1]
+        out.append(y[:, o:o + L])
+        o += L
+    return out

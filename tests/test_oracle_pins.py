@@ -345,3 +345,43 @@ def test_projected_networks_of_a_permutation_are_permuted():
     b = O.networks_dense(O.project(M, x), 1000.0, 256, 1.0, 50.0, metrics=("COH", "PLI", "COR"))
     for m in ("COH", "PLI", "COR"):
         np.testing.assert_allclose(b[m], a[m][np.ix_(perm, perm)], atol=1e-12)
+
+
+# ------------------------------------------------------------------------------ FIR
+
+
+def test_fir_design_matches_scipy_firwin():
+    signal = pytest.importorskip("scipy.signal")
+    fs = 1000.0
+    for kind, lo, hi, T in (("lowpass", 0.0, 40.0, 101), ("highpass", 2.0, 0.0, 301), ("bandpass", 8.0, 30.0, 201)):
+        h = O.fir_design(fs, kind, lo, hi, 10.0, T)
+        cut = {"lowpass": hi, "highpass": lo, "bandpass": [lo, hi]}[kind]
+        ref = signal.firwin(T, cut, pass_zero={"lowpass": True, "highpass": False, "bandpass": False}[kind],
+                            window="hamming", scale=False, fs=fs)
+        np.testing.assert_allclose(h, ref, rtol=0, atol=1e-15)
+
+
+def test_fir_design_properties():
+    h = O.fir_design(600.0, "bandpass", 8.0, 12.0, 4.0)
+    T = h.size
+    assert T % 2 == 1 and T == 2 * (int(math.ceil(3.3 * 600 / 4.0)) // 2) + 1
+    np.testing.assert_allclose(h, h[::-1], atol=1e-17)  # symmetric: linear phase
+    lp = O.fir_design(1000.0, "lowpass", 0.0, 50.0, 10.0, 0)
+    ripple = 10 ** (-53 / 20)  # Hamming window: about -53 dB stop band / pass-band ripple
+    assert abs(lp.sum() - 1.0) < ripple  # unit DC gain up to the ripple
+    hp = O.fir_design(1000.0, "highpass", 2.0, 0.0, 2.0, 0)
+    assert abs(hp.sum()) < ripple  # DC in the stop band
+
+
+def test_fir_stream_blocks_equal_whole_stream_and_impulse_response():
+    rng = np.random.default_rng(4)
+    h = O.fir_design(500.0, "bandpass", 4.0, 40.0, 4.0, 63)
+    x = rng.standard_normal((3, 700))
+    blocks = [x[:, :250], x[:, 250:251], x[:, 251:700]]
+    y = np.concatenate(O.fir_filter_stream(h, blocks), axis=1)
+    direct = np.array([[sum(h[k] * x[c, t - k] for k in range(h.size) if t - k >= 0) for t in range(700)]
+                       for c in range(3)])
+    np.testing.assert_allclose(y, direct, atol=1e-12)
+    imp = np.zeros((1, 100))
+    imp[0, 0] = 1.0
+    np.testing.assert_allclose(O.fir_filter_stream(h, [imp])[0][0, :63], h, atol=1e-15)

@@ -381,6 +381,32 @@ fc_status fc_server_stats_get(fc_server* sv, fc_server_stats* st);
 /* Stop the worker, close every session, free everything. NULL is accepted. */
 fc_status fc_server_destroy(fc_server* sv);
 
+/* ---- FIR filtering of the incoming stream (upstream of the sessions) ------------- */
+/*
+ * Methods 2.4 (Noise Reduction plug-in): low-, high- and band-pass FIR filters designed on
+ * the fly from the cut-offs, the transition bandwidth and the number of taps, all with a
+ * linear phase, applied to the data blocks as they arrive with overlap-add across block
+ * boundaries. Design: window method - the ideal response (differences of sinc low-passes)
+ * times a Hamming window, odd length T (n_taps, rounded up to odd; 0: ceil(3.3 fs /
+ * transition_hz)), at most 8191, computed in FP64 on the host and applied in FP32.
+ * fc_fir_process filters one block x[n_channels][block_len] into y (host or device memory,
+ * both on the same side): y[c][t] = sum_k h[k] x[c][t - k] over the continuous stream, the
+ * state (the last T - 1 samples of every channel) carrying over between calls, so any
+ * division into blocks gives the same output (a delay of (T - 1) / 2 samples). Host buffers
+ * synchronize; device buffers are asynchronous on the given stream (NULL: the filter's own).
+ */
+typedef struct fc_fir fc_fir;
+typedef enum { FC_FIR_LOWPASS = 0, FC_FIR_HIGHPASS = 1, FC_FIR_BANDPASS = 2 } fc_fir_kind;
+/* lowpass uses f_hi, highpass f_lo, bandpass both; cut-offs inside (0, fs / 2). */
+fc_status fc_fir_create(int n_channels, double fs, fc_fir_kind kind, double f_lo, double f_hi,
+                        double transition_hz, int n_taps, void* stream, fc_fir** out);
+/* The FP64 taps (T of them; taps may be NULL to ask for T only). */
+fc_status fc_fir_get_taps(fc_fir* f, double* taps, int max_taps, int* n_taps);
+fc_status fc_fir_process(fc_fir* f, const float* x, float* y, int block_len, int on_device);
+/* Forget the stream so far (zero state). */
+fc_status fc_fir_reset(fc_fir* f);
+fc_status fc_fir_destroy(fc_fir* f);
+
 /* ---- allocation-free entry point ------------------------------------------------ */
 
 /* Size of the device scratch array behind fc_window_networks_noalloc (16 MiB). */

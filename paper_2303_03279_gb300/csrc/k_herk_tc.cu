@@ -185,10 +185,12 @@ __global__ void __launch_bounds__(128, 1) k_herk_tc(HerkArgs a) {
                     const uint64_t dui_a = smem_desc(base + 3 * CHUNK_BYTES + off);
                     const uint64_t dxr_b = smem_desc(base + 4 * CHUNK_BYTES + off);
                     const uint64_t dur_b = smem_desc(base + 5 * CHUNK_BYTES + off);
-                    mma<KIND>(tmem + 0 * TILE, dxr_a, dxr_b, idesc, acc);
-                    mma<KIND>(tmem + 1 * TILE, dxi_a, dxr_b, idesc, acc);
-                    mma<KIND>(tmem + 2 * TILE, dur_a, dur_b, idesc, acc);
-                    mma<KIND>(tmem + 3 * TILE, dui_a, dur_b, idesc, acc);
+                    // transposed products: D^T[j][i] (TMEM lane = column node j), so that the
+                    // epilogue's warp-wide stores run along j, contiguous in the packed triangle
+                    mma<KIND>(tmem + 0 * TILE, dxr_b, dxr_a, idesc, acc);
+                    mma<KIND>(tmem + 1 * TILE, dxr_b, dxi_a, idesc, acc);
+                    mma<KIND>(tmem + 2 * TILE, dur_b, dur_a, idesc, acc);
+                    mma<KIND>(tmem + 3 * TILE, dur_b, dui_a, idesc, acc);
                 }
                 mma_commit(&freeb[st]);  // the stage may be refilled once these MMAs have read it
                 ++consumed;
@@ -196,7 +198,8 @@ __global__ void __launch_bounds__(128, 1) k_herk_tc(HerkArgs a) {
             }
             mma_commit(accb);
         }
-        // epilogue: thread t owns TMEM lane t = row i of the tile pair
+        // epilogue: thread t owns TMEM lane t = column node j of the tile pair; TMEM columns
+        // are the row nodes i
         const bool ok = mbar_wait_bounded(accb, acc_phase);
         acc_phase ^= 1;
         fence_after();
@@ -205,21 +208,21 @@ __global__ void __launch_bounds__(128, 1) k_herk_tc(HerkArgs a) {
             if (tid == 0) atomicOr(&c->timeout, 1);
             break;
         }
-        const int i = ta * TILE + tid;
-        const float inv_i = i < a.n ? a.inv_psd[(size_t)f * a.n + i] : 0.f;
+        const int j = tb * TILE + tid;
+        const float inv_j = j < a.n ? a.inv_psd[(size_t)f * a.n + j] : 0.f;
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int j0 = 0; j0 < TILE; j0 += 16) {
+        for (int i0 = 0; i0 < TILE; i0 += 16) {
             float cre[16], cim[16], ure[16], uim[16];
-            tmem_ld16(lane_base + 0 * TILE + j0, cre);
-            tmem_ld16(lane_base + 1 * TILE + j0, cim);
-            tmem_ld16(lane_base + 2 * TILE + j0, ure);
-            tmem_ld16(lane_base + 3 * TILE + j0, uim);
-            if (i >= a.n) continue;
+            tmem_ld16(lane_base + 0 * TILE + i0, cre);
+            tmem_ld16(lane_base + 1 * TILE + i0, cim);
+            tmem_ld16(lane_base + 2 * TILE + i0, ure);
+            tmem_ld16(lane_base + 3 * TILE + i0, uim);
+            if (j >= a.n) continue;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const int j = tb * TILE + j0 + q;
-                if (j <= i || j >= a.n) continue;
-                const float inv_j = a.inv_psd[(size_t)f * a.n + j];
+                const int i = ta * TILE + i0 + q;
+                if (j <= i || i >= a.n) continue;
+                const float inv_i = a.inv_psd[(size_t)f * a.n + i];
                 const float r = __fmul_rn(__fmul_rn(cre[q], inv_i), inv_j);
                 const float m = __fmul_rn(__fmul_rn(cim[q], inv_i), inv_j);
                 const long long p = packed_index(i, j, a.n);

@@ -40,7 +40,10 @@ __global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
     const unsigned vmask = pair_mask(ta, tb, li, lj0, a.n);
     const int gi = ta * FC_T + li, gj0 = tb * FC_T + lj0;
 
-    __shared__ float2 sx[NK][2 * FC_T];
+    // planar: [trial][node] real parts, imaginary parts, tiny flags (two adjacent column
+    // nodes load as one packed operand)
+    __shared__ __align__(16) float sa[NK][2 * FC_T];
+    __shared__ __align__(16) float sb[NK][2 * FC_T];
     __shared__ unsigned char stiny[NK][2 * FC_T];
 
     float band[7][4];
@@ -67,7 +70,8 @@ __global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
                 const long long trial = start + k0 + kk;
                 float2 X = make_float2(0.f, 0.f);
                 if (node < a.n) X = a.ring[((size_t)(trial % a.slots) * a.B + f) * a.n + node];
-                sx[kk][l] = X;
+                sa[kk][l] = X.x;
+                sb[kk][l] = X.y;
                 const bool tn = node_tiny(X);
                 stiny[kk][l] = tn ? 1 : 0;
                 any_tiny |= tn;
@@ -75,34 +79,47 @@ __global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
             // chunks without a tiny node (the rule) run a loop with no FP64 branch at all
             const bool chunk_tiny = __syncthreads_or(any_tiny ? 1 : 0) != 0;
             if (!vmask) continue;
-            float p_im[4] = {0.f, 0.f, 0.f, 0.f}, p_sq[4] = {0.f, 0.f, 0.f, 0.f}, p_abs[4] = {0.f, 0.f, 0.f, 0.f};
-            float p_sqe[4] = {0.f, 0.f, 0.f, 0.f};
+            // FP32 partial sums of this chunk, two column pairs per packed lane pair
+            float2 p_im[2], p_sq[2], p_abs[2], p_sqe[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) p_im[h] = p_sq[h] = p_abs[h] = p_sqe[h] = make_float2(0.f, 0.f);
             auto chunk = [&](auto tiny_c) {
                 constexpr bool TINY = decltype(tiny_c)::value;
                 for (int kk = 0; kk < kn; ++kk) {
-                    const float2 xi = sx[kk][li];
+                    const float ai = sa[kk][li], bi = sb[kk][li];
                     const bool ti = TINY && stiny[kk][li] != 0;
+                    const float2 bi2 = f2(bi), nbi2 = f2(-bi), ai2 = f2(ai), nai2 = f2(-ai);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float2 xj = sx[kk][FC_T + lj0 + q];
-                        // Im(X_i X_j*) and its exact sign, as in pair_terms (terms.cuh)
-                        const float p = __fmul_rn(xi.y, xj.x), np = __fmul_rn(-xi.y, xj.x);
-                        const float qq = __fmul_rn(xi.x, xj.y), nq = __fmul_rn(-xi.x, xj.y);
-                        const float e = __fmaf_rn(xi.y, xj.x, np);
-                        const float nf = __fmaf_rn(-xi.x, xj.y, qq);
-                        const float d1 = __fadd_rn(p, nq), d2 = __fadd_rn(e, nf);
-                        float im = __fadd_rn(d1, d2);
-                        int sg = sign_of(d1 != 0.f ? d1 : d2);
-                        if (TINY && (ti || stiny[kk][FC_T + lj0 + q])) im_sign_fp64(xi.x, xi.y, xj.x, xj.y, im, sg);
-                        s_sg[q] += sg;
-                        p_abs[q] = __fadd_rn(p_abs[q], fabsf(im));
-                        p_im[q] = __fadd_rn(p_im[q], im);
-                        // im^2 as an exact two-product (t + r): a lone nonzero term then gives
-                        // (sum |Im|)^2 - sum Im^2 = 0 exactly, as in the exact path
-                        float t, r;
-                        two_prod(im, im, t, r);
-                        p_sq[q] = __fadd_rn(p_sq[q], t);
-                        p_sqe[q] = __fadd_rn(p_sqe[q], r);
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = FC_T + lj0 + 2 * h;
+                        const float2 aj = *reinterpret_cast<const float2*>(&sa[kk][j]);
+                        const float2 bj = *reinterpret_cast<const float2*>(&sb[kk][j]);
+                        // Im(X_i X_j*) and its exact sign, as in pair_terms2 (terms.cuh)
+                        const float2 p = mul2(bi2, aj), np = mul2(nbi2, aj);
+                        const float2 qq = mul2(ai2, bj), nq = mul2(nai2, bj);
+                        const float2 e = fma2(bi2, aj, np);
+                        const float2 nf = fma2(nai2, bj, qq);
+                        // scalar: an add that takes a raw packed product is never fused
+                        const float2 d1 = make_float2(__fadd_rn(p.x, nq.x), __fadd_rn(p.y, nq.y));
+                        const float2 d2 = add2(e, nf);
+                        float2 im = add2(d1, d2);
+                        int sg0 = sign_of(d1.x != 0.f ? d1.x : d2.x);
+                        int sg1 = sign_of(d1.y != 0.f ? d1.y : d2.y);
+                        if (TINY) {
+                            if (ti || stiny[kk][j]) im_sign_fp64(ai, bi, aj.x, bj.x, im.x, sg0);
+                            if (ti || stiny[kk][j + 1]) im_sign_fp64(ai, bi, aj.y, bj.y, im.y, sg1);
+                        }
+                        s_sg[2 * h] += sg0;
+                        s_sg[2 * h + 1] += sg1;
+                        p_abs[h] = make_float2(__fadd_rn(p_abs[h].x, fabsf(im.x)), __fadd_rn(p_abs[h].y, fabsf(im.y)));
+                        p_im[h] = add2(p_im[h], im);
+                        // im^2 as an exact two-product (t + r), scalar: the products feed additions;
+                        // a lone nonzero term then gives (sum |Im|)^2 - sum Im^2 = 0 exactly
+                        float2 t, r;
+                        two_prod(im.x, im.x, t.x, r.x);
+                        two_prod(im.y, im.y, t.y, r.y);
+                        p_sq[h] = make_float2(__fadd_rn(p_sq[h].x, t.x), __fadd_rn(p_sq[h].y, t.y));
+                        p_sqe[h] = add2(p_sqe[h], r);
                     }
                 }
             };
@@ -112,9 +129,13 @@ __global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
                 chunk(std::false_type{});
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                s_im[q] = df_add_f(s_im[q], p_im[q]);
-                s_sq[q] = df_add_f(df_add_f(s_sq[q], p_sq[q]), p_sqe[q]);
-                s_abs[q] = df_add_f(s_abs[q], p_abs[q]);
+                const float pim = (q & 1) ? p_im[q >> 1].y : p_im[q >> 1].x;
+                const float psq = (q & 1) ? p_sq[q >> 1].y : p_sq[q >> 1].x;
+                const float pse = (q & 1) ? p_sqe[q >> 1].y : p_sqe[q >> 1].x;
+                const float pab = (q & 1) ? p_abs[q >> 1].y : p_abs[q >> 1].x;
+                s_im[q] = df_add_f(s_im[q], pim);
+                s_sq[q] = df_add_f(df_add_f(s_sq[q], psq), pse);
+                s_abs[q] = df_add_f(s_abs[q], pab);
             }
         }
         if (vmask && f >= a.fsel0 && f < a.fsel1) {

@@ -114,6 +114,12 @@ _SIGNATURES = [
     ("fc_get_xcor_lags", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]),
     ("fc_set_metric_mask", C.c_int, [C.c_void_p, C.c_uint32]),
     ("fc_set_band", C.c_int, [C.c_void_p, C.c_double, C.c_double]),
+    ("fc_fir_create", C.c_int, [C.c_int, C.c_double, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
+                                C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("fc_fir_get_taps", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    ("fc_fir_process", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
+    ("fc_fir_reset", C.c_int, [C.c_void_p]),
+    ("fc_fir_destroy", C.c_int, [C.c_void_p]),
     ("fc_debug_wait_probe", C.c_int, [C.c_void_p, C.c_double]),
     ("fc_set_projection", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     ("fc_session_snapshot_size", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
@@ -299,6 +305,43 @@ def fc_set_projection(s, op=None):
 
 def fc_debug_wait_probe(s, limit_ms: float):
     _check(load().fc_debug_wait_probe(s, float(limit_ms)))
+
+
+FIR_KINDS = {"lowpass": 0, "highpass": 1, "bandpass": 2}
+
+
+def fc_fir_create(n_channels: int, fs: float, kind, f_lo: float, f_hi: float, transition_hz: float = 0.0,
+                  n_taps: int = 0, stream=None):
+    k = FIR_KINDS[kind] if isinstance(kind, str) else int(kind)
+    out = C.c_void_p()
+    _check(load().fc_fir_create(int(n_channels), float(fs), k, float(f_lo), float(f_hi), float(transition_hz),
+                                int(n_taps), C.c_void_p(int(stream)) if stream is not None else None, C.byref(out)))
+    return out
+
+
+def fc_fir_get_taps(f) -> np.ndarray:
+    n = C.c_int(0)
+    _check(load().fc_fir_get_taps(f, None, 0, C.byref(n)))
+    taps = np.empty(n.value, np.float64)
+    _check(_LIB.fc_fir_get_taps(f, C.c_void_p(taps.ctypes.data), n.value, C.byref(n)))
+    return taps
+
+
+def fc_fir_process(f, x, y):
+    """x, y: [n_channels][block_len] float32, both numpy or both CUDA tensors."""
+    px, dx, _ = _ptr(x, np.float32)
+    py, dy, _ = _ptr(y, np.float32)
+    if dx != dy or tuple(x.shape) != tuple(y.shape):
+        raise ValueError("x and y: same shape, both on the host or both on the device")
+    _check(load().fc_fir_process(f, px, py, int(x.shape[1]), dx))
+
+
+def fc_fir_reset(f):
+    _check(load().fc_fir_reset(f))
+
+
+def fc_fir_destroy(f):
+    _check(load().fc_fir_destroy(f))
 
 
 def fc_sync(s):

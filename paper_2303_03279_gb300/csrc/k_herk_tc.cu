@@ -30,10 +30,12 @@ using namespace fcmbar;
 
 constexpr int TILE = 128;             // nodes per tile (M = N = 128)
 constexpr int CHUNK_BYTES = 16384;     // 128 rows x 128 bytes of K
-constexpr int NOPS = 6;                // XR(a), XI(a), UR(a), UI(a), XR(b), UR(b)
-constexpr int STAGE_BYTES = NOPS * CHUNK_BYTES;
-constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 128;  // + barriers and the TMEM address
-constexpr uint32_t TMEM_COLS = 512;    // 4 accumulators x 128 FP32 columns
+constexpr int PHASE_OPS = 3;           // operand blocks per chunk of one phase (see k_herk_tc)
+constexpr int STAGE_BYTES = PHASE_OPS * CHUNK_BYTES;
+constexpr int NSTAGE = 4;              // chunk stages in flight
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 512 + 4 * 512;  // + barriers, TMEM address, 4 x 1/sqrt(PSD) rows
+constexpr uint32_t TMEM_COLS = 512;    // 2 phase buffers x 2 accumulators x 128 FP32 columns
+constexpr int THREADS = 160;           // warps 0-3: epilogue (TMEM lanes 32w..32w+31); warp 4: loads + MMAs
 
 // Shared-memory matrix descriptor: K-major, no swizzle; LBO = 128 B (next core matrix
 // along K), SBO = 1024 B (next 8-row group), descriptor version 1.
@@ -94,17 +96,29 @@ __device__ __forceinline__ const unsigned char* op_block(const HerkArgs& a, int 
     return a.ops + ((((size_t)tile * a.B + f) * 4 + kind) * a.nchunks + chunk) * (size_t)CHUNK_BYTES;
 }
 
+// Per (128-node tile pair, bin) unit, two phases, each a pair of transposed products
+// D^T[j][i] (TMEM lane = column node j of tile b, TMEM column = row node i of tile a):
+//   phase A (CSD):     Re = XR_b XR_a^T,  Im = XR_b XI_a^T   -> COH, IMAGCOHY
+//   phase B (phasors): Re = UR_b UR_a^T,  Im = UR_b UI_a^T   -> PLV
+// Phase p accumulates in TMEM columns [256 p, 256 p + 256), so the epilogue of one phase
+// runs while the tensor cores work on the next (warp-specialized: warp 4 lane 0 streams
+// the operand chunks of the CTA's phase sequence through NSTAGE shared-memory stages and
+// issues the MMAs; warps 0-3 drain TMEM). Every wait is bounded; a timeout is recorded in
+// the control block.
 template <int KIND>
-__global__ void __launch_bounds__(128, 1) k_herk_tc(HerkArgs a) {
+__global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     FcCtrl* c = const_cast<FcCtrl*>(a.ctrl);
     if (c->bad) return;
     const int units = a.ntp * a.B;
     if ((int)blockIdx.x >= units) return;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * STAGE_BYTES);  // [2]
-    uint64_t* freeb = full + 2;                                            // [2]
-    uint64_t* accb = full + 4;                                             // [1]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 6);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);  // [NSTAGE]
+    uint64_t* freeb = full + NSTAGE;                                             // [NSTAGE]
+    uint64_t* accf = freeb + NSTAGE;                                             // [2] MMAs -> epilogue
+    uint64_t* acce = accf + 2;                                                   // [2] epilogue -> MMAs
+    uint64_t* drain = acce + 2;                                                  // [1]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    float* sinv_all = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES + 512);  // [4][128] per epilogue warp
     const int tid = threadIdx.x, warp = tid >> 5;
 
     if (warp == 0) {
@@ -114,130 +128,167 @@ __global__ void __launch_bounds__(128, 1) k_herk_tc(HerkArgs a) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
-        mbar_init(&freeb[0], 1);
-        mbar_init(&freeb[1], 1);
-        mbar_init(accb, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&freeb[s], 1);
+        }
+        mbar_init(&accf[0], 1);
+        mbar_init(&accf[1], 1);
+        mbar_init(&acce[0], 4);  // one arrival per epilogue warp
+        mbar_init(&acce[1], 4);
+        mbar_init(drain, 1);
+        fence_mbar_init();
     }
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = make_idesc(KIND == 1 ? 2u : (a.ab_format == 1 ? 1u : 0u), TILE, TILE);
     const long long wend = c->pushed + a.count;
     const int K = (int)(wend - ((a.W > 0 && wend > a.W) ? wend - a.W : 0));
     const float inv_K = 1.0f / (float)K;
-
-    uint32_t full_phase[2] = {0, 0}, free_phase[2] = {0, 0}, acc_phase = 0;
-    int loads = 0;       // chunk loads issued (stage = loads % 2); load s = chunk s of this CTA's sequence
-    int consumed = 0;    // chunks consumed by MMAs
+    // this CTA's units: blockIdx.x + k gridDim.x; its phase sequence: 2 per unit
+    const int my_units = (units - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int nphase = 2 * my_units;
     bool failed = false;
-    const long long seq_len = (long long)((units - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x) * a.nchunks;
 
-    // the CTA's chunk sequence: position s -> unit blockIdx.x + (s / nchunks) * gridDim.x, chunk s % nchunks
-    auto issue_next_load = [&]() {  // thread 0 only
-        if (loads >= seq_len) return;
-        const int u = (int)blockIdx.x + (loads / a.nchunks) * (int)gridDim.x;
-        const int ch = loads % a.nchunks;
-        const int tp = u / a.B, f = u % a.B;
-        const int ta = a.tile_a[tp], tb = a.tile_b[tp];
-        const int st = loads & 1;
-        if (loads >= 2) {  // the stage's previous MMAs must be done reading it
-            if (!mbar_wait_bounded(&freeb[st], free_phase[st])) failed = true;
-            free_phase[st] ^= 1;
-        }
-        unsigned char* dst = smem + st * STAGE_BYTES;
-        mbar_expect_tx(&full[st], STAGE_BYTES);
-        bulk_g2s(dst + 0 * CHUNK_BYTES, op_block(a, ta, f, 0, ch), CHUNK_BYTES, &full[st]);
-        bulk_g2s(dst + 1 * CHUNK_BYTES, op_block(a, ta, f, 1, ch), CHUNK_BYTES, &full[st]);
-        bulk_g2s(dst + 2 * CHUNK_BYTES, op_block(a, ta, f, 2, ch), CHUNK_BYTES, &full[st]);
-        bulk_g2s(dst + 3 * CHUNK_BYTES, op_block(a, ta, f, 3, ch), CHUNK_BYTES, &full[st]);
-        bulk_g2s(dst + 4 * CHUNK_BYTES, op_block(a, tb, f, 0, ch), CHUNK_BYTES, &full[st]);
-        bulk_g2s(dst + 5 * CHUNK_BYTES, op_block(a, tb, f, 2, ch), CHUNK_BYTES, &full[st]);
-        ++loads;
-    };
-
-    int u = blockIdx.x;
-    if (tid == 0) {
-        issue_next_load();
-        issue_next_load();
-    }
-    while (u < units) {
-        const int tp = u / a.B, f = u % a.B;
-        const int ta = a.tile_a[tp], tb = a.tile_b[tp];
-        const int nu = u + (int)gridDim.x;
-        if (tid == 0) {
-            for (int ch = 0; ch < a.nchunks; ++ch) {
-                const int st = consumed & 1;
-                if (!mbar_wait_bounded(&full[st], full_phase[st])) failed = true;
-                full_phase[st] ^= 1;
-                fence_after();
-                const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
-#pragma unroll
-                for (int ks = 0; ks < 4; ++ks) {
-                    const uint32_t acc = (ch > 0 || ks > 0) ? 1u : 0u;
-                    const uint32_t off = ks * 256;
-                    const uint64_t dxr_a = smem_desc(base + 0 * CHUNK_BYTES + off);
-                    const uint64_t dxi_a = smem_desc(base + 1 * CHUNK_BYTES + off);
-                    const uint64_t dur_a = smem_desc(base + 2 * CHUNK_BYTES + off);
-                    const uint64_t dui_a = smem_desc(base + 3 * CHUNK_BYTES + off);
-                    const uint64_t dxr_b = smem_desc(base + 4 * CHUNK_BYTES + off);
-                    const uint64_t dur_b = smem_desc(base + 5 * CHUNK_BYTES + off);
-                    // transposed products: D^T[j][i] (TMEM lane = column node j), so that the
-                    // epilogue's warp-wide stores run along j, contiguous in the packed triangle
-                    mma<KIND>(tmem + 0 * TILE, dxr_b, dxr_a, idesc, acc);
-                    mma<KIND>(tmem + 1 * TILE, dxr_b, dxi_a, idesc, acc);
-                    mma<KIND>(tmem + 2 * TILE, dur_b, dur_a, idesc, acc);
-                    mma<KIND>(tmem + 3 * TILE, dur_b, dui_a, idesc, acc);
+    if (warp == 4) {
+        // ---------------------------------------------------------- loads + MMAs
+        if ((tid & 31) == 0) {
+            const uint32_t idesc = make_idesc(KIND == 1 ? 2u : (a.ab_format == 1 ? 1u : 0u), TILE, TILE);
+            const long long nchunk_total = (long long)nphase * a.nchunks;
+            uint32_t full_ph[NSTAGE], free_ph[NSTAGE];
+            for (int s = 0; s < NSTAGE; ++s) full_ph[s] = free_ph[s] = 0;
+            uint32_t acce_ph[2] = {0, 0};
+            long long loads = 0;
+            auto issue_load = [&]() {  // chunk `loads` of the sequence into stage loads % NSTAGE
+                if (loads >= nchunk_total) return;
+                const int st = (int)(loads % NSTAGE);
+                if (loads >= NSTAGE) {  // the MMAs of the chunk that used this stage have read it
+                    if (!mbar_wait_bounded(&freeb[st], free_ph[st])) failed = true;
+                    free_ph[st] ^= 1;
                 }
-                mma_commit(&freeb[st]);  // the stage may be refilled once these MMAs have read it
-                ++consumed;
-                issue_next_load();       // keep two chunks in flight along the sequence
-            }
-            mma_commit(accb);
-        }
-        // epilogue: thread t owns TMEM lane t = column node j of the tile pair; TMEM columns
-        // are the row nodes i
-        const bool ok = mbar_wait_bounded(accb, acc_phase);
-        acc_phase ^= 1;
-        fence_after();
-        const int fail_any = __syncthreads_or((!ok || failed) ? 1 : 0);
-        if (fail_any) {
-            if (tid == 0) atomicOr(&c->timeout, 1);
-            break;
-        }
-        const int j = tb * TILE + tid;
-        const float inv_j = j < a.n ? a.inv_psd[(size_t)f * a.n + j] : 0.f;
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int i0 = 0; i0 < TILE; i0 += 16) {
-            float cre[16], cim[16], ure[16], uim[16];
-            tmem_ld16(lane_base + 0 * TILE + i0, cre);
-            tmem_ld16(lane_base + 1 * TILE + i0, cim);
-            tmem_ld16(lane_base + 2 * TILE + i0, ure);
-            tmem_ld16(lane_base + 3 * TILE + i0, uim);
-            if (j >= a.n) continue;
+                const long long ph = loads / a.nchunks;
+                const int ch = (int)(loads % a.nchunks);
+                const int u = (int)blockIdx.x + (int)(ph >> 1) * (int)gridDim.x;
+                const int tp = u / a.B, f = u % a.B;
+                const int ta = a.tile_a[tp], tb = a.tile_b[tp];
+                const int k0 = (ph & 1) ? 2 : 0;  // phase A: X operands, phase B: U operands
+                unsigned char* dst = smem + st * STAGE_BYTES;
+                mbar_expect_tx(&full[st], STAGE_BYTES);
+                bulk_g2s(dst + 0 * CHUNK_BYTES, op_block(a, tb, f, k0, ch), CHUNK_BYTES, &full[st]);
+                bulk_g2s(dst + 1 * CHUNK_BYTES, op_block(a, ta, f, k0, ch), CHUNK_BYTES, &full[st]);
+                bulk_g2s(dst + 2 * CHUNK_BYTES, op_block(a, ta, f, k0 + 1, ch), CHUNK_BYTES, &full[st]);
+                ++loads;
+            };
+            for (int s = 0; s < NSTAGE - 1; ++s) issue_load();
+            long long consumed = 0;
+            for (int ph = 0; ph < nphase && !failed; ++ph) {
+                const int b = ph & 1;
+                if (ph >= 2) {  // the epilogue has drained this TMEM half
+                    if (!mbar_wait_bounded(&acce[b], acce_ph[b])) {
+                        failed = true;
+                        break;
+                    }
+                    acce_ph[b] ^= 1;
+                    fence_after();
+                }
+                const uint32_t d = tmem + (uint32_t)(b * 2 * TILE);
+                for (int ch = 0; ch < a.nchunks; ++ch) {
+                    const int st = (int)(consumed % NSTAGE);
+                    if (!mbar_wait_bounded(&full[st], full_ph[st])) {
+                        failed = true;
+                        break;
+                    }
+                    full_ph[st] ^= 1;
+                    fence_after();
+                    const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int i = ta * TILE + i0 + q;
-                if (j <= i || i >= a.n) continue;
-                const float inv_i = a.inv_psd[(size_t)f * a.n + i];
-                const float r = __fmul_rn(__fmul_rn(cre[q], inv_i), inv_j);
-                const float m = __fmul_rn(__fmul_rn(cim[q], inv_i), inv_j);
-                const long long p = packed_index(i, j, a.n);
-                float* out = a.bins_out + (size_t)f * 3 * a.P;
-                out[p] = sqrtf(__fmaf_rn(r, r, __fmul_rn(m, m)));
-                out[a.P + p] = m;
-                out[2 * a.P + p] = __fmul_rn(sqrtf(__fmaf_rn(ure[q], ure[q], __fmul_rn(uim[q], uim[q]))), inv_K);
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint32_t acc = (ch > 0 || ks > 0) ? 1u : 0u;
+                        const uint32_t off = ks * 256;
+                        const uint64_t d_b = smem_desc(base + 0 * CHUNK_BYTES + off);   // XR_b or UR_b
+                        const uint64_t d_ar = smem_desc(base + 1 * CHUNK_BYTES + off);  // XR_a or UR_a
+                        const uint64_t d_ai = smem_desc(base + 2 * CHUNK_BYTES + off);  // XI_a or UI_a
+                        mma<KIND>(d, d_b, d_ar, idesc, acc);
+                        mma<KIND>(d + TILE, d_b, d_ai, idesc, acc);
+                    }
+                    mma_commit(&freeb[st]);  // the stage may be refilled once these MMAs have read it
+                    ++consumed;
+                    issue_load();            // refills the stage of the previous chunk
+                }
+                if (failed) break;
+                mma_commit(&accf[b]);
+            }
+            // let every MMA and copy issued land before the CTA ends
+            mma_commit(drain);
+            mbar_wait_bounded(drain, 0);
+            for (long long l = consumed; l < loads; ++l) {
+                const int st = (int)(l % NSTAGE);
+                mbar_wait_bounded(&full[st], full_ph[st]);
+                full_ph[st] ^= 1;
             }
         }
-        fence_before();
-        __syncthreads();  // TMEM free for the next unit's MMAs
-        fence_after();
-        u = nu;
+    } else {
+        // ---------------------------------------------------------- epilogue (warps 0-3)
+        uint32_t accf_ph[2] = {0, 0};
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        float* sinv = sinv_all + warp * TILE;  // this warp's copy: no barrier across warps
+        for (int ph = 0; ph < nphase; ++ph) {
+            const int b = ph & 1;
+            const int u = (int)blockIdx.x + (ph >> 1) * (int)gridDim.x;
+            const int tp = u / a.B, f = u % a.B;
+            const int ta = a.tile_a[tp], tb = a.tile_b[tp];
+            const int j = tb * TILE + tid;  // this thread's TMEM lane: column node j
+            if (b == 0) {  // 1/sqrt(PSD) of tile a's nodes, staged by this warp for itself
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < TILE / 32; ++r) {
+                    const int i = ta * TILE + r * 32 + (tid & 31);
+                    sinv[r * 32 + (tid & 31)] = i < a.n ? a.inv_psd[(size_t)f * a.n + i] : 0.f;
+                }
+                __syncwarp();
+            }
+            // warp-uniform outcome: the TMEM loads below are warp-collective
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accf[b], accf_ph[b]) ? 1 : 0) != 0;
+            accf_ph[b] ^= 1;
+            if (!ok) {
+                failed = true;
+                break;
+            }
+            fence_after();
+            const uint32_t col = (uint32_t)(b * 2 * TILE);
+            const float inv_j = (b == 0 && j < a.n) ? a.inv_psd[(size_t)f * a.n + j] : 0.f;
+            float* out = a.bins_out + (size_t)f * 3 * a.P;
+            for (int i0 = 0; i0 < TILE; i0 += 16) {
+                float vre[16], vim[16];
+                tmem_ld16(lane_base + col + i0, vre);
+                tmem_ld16(lane_base + col + TILE + i0, vim);
+                if (j >= a.n) continue;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int i = ta * TILE + i0 + q;
+                    if (j <= i || i >= a.n) continue;
+                    const long long p = packed_index(i, j, a.n);
+                    if (b == 0) {
+                        const float inv_i = sinv[i0 + q];
+                        const float r = __fmul_rn(__fmul_rn(vre[q], inv_i), inv_j);
+                        const float m = __fmul_rn(__fmul_rn(vim[q], inv_i), inv_j);
+                        out[p] = sqrtf(__fmaf_rn(r, r, __fmul_rn(m, m)));
+                        out[a.P + p] = m;
+                    } else {
+                        out[2 * a.P + p] = __fmul_rn(sqrtf(__fmaf_rn(vre[q], vre[q], __fmul_rn(vim[q], vim[q]))), inv_K);
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if ((tid & 31) == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
+        }
     }
-    __syncthreads();
+    fence_before();
+    const int fail_any = __syncthreads_or(failed ? 1 : 0);
+    fence_after();
+    if (fail_any && tid == 0) atomicOr(&c->timeout, 1);
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
@@ -349,11 +400,11 @@ cudaError_t launch_herk_tc(const HerkArgs& a, cudaStream_t st) {
     if (a.ab_format == 2) {
         e = cudaFuncSetAttribute(k_herk_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        k_herk_tc<1><<<ctas, 128, SMEM_BYTES, st>>>(a);
+        k_herk_tc<1><<<ctas, THREADS, SMEM_BYTES, st>>>(a);
     } else {
         e = cudaFuncSetAttribute(k_herk_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        k_herk_tc<0><<<ctas, 128, SMEM_BYTES, st>>>(a);
+        k_herk_tc<0><<<ctas, THREADS, SMEM_BYTES, st>>>(a);
     }
     return cudaGetLastError();
 }

@@ -144,7 +144,9 @@ __global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
                 if (!(vmask & (1u << q))) continue;
                 // PLI, USPLI, WPLI, DSWPLI (metric slots 3..6)
                 band[3][q] = __fadd_rn(band[3][q], __fmul_rn((float)abs(s_sg[q]), kc.inv_K));
-                band[4][q] = __fadd_rn(band[4][q], __fmul_rn((float)((long long)s_sg[q] * s_sg[q] - K), kc.inv_KK1));
+                const float usn = K <= 46340 ? (float)(s_sg[q] * s_sg[q] - K)
+                                             : (float)((long long)s_sg[q] * s_sg[q] - K);
+                band[4][q] = __fadd_rn(band[4][q], __fmul_rn(usn, kc.inv_KK1));
                 const float sim = df_to_f(s_im[q]);
                 const float sab = df_to_f(s_abs[q]);
                 band[5][q] = __fadd_rn(band[5][q], sab > 0.f ? __fdividef(fabsf(sim), sab) : 0.f);

@@ -84,7 +84,10 @@ __device__ __forceinline__ void finalize_bin(const df32* f, int sign, float inv_
     const float ure = df_to_f(f[2]), uim = df_to_f(f[3]);
     out[2] = __fmul_rn(mag_from_sq(__fmaf_rn(ure, ure, __fmul_rn(uim, uim))), kc.inv_K);
     out[3] = __fmul_rn((float)abs(sign), kc.inv_K);
-    out[4] = __fmul_rn((float)((long long)sign * sign - kc.K), kc.inv_KK1);
+    // S^2 - K converted with one rounding; in 32 bits while it fits (|S| <= K <= 46340),
+    // which keeps the conversion off the FP64 pipe, the same value either way
+    const float usn = kc.K <= 46340 ? (float)(sign * sign - kc.K) : (float)((long long)sign * sign - kc.K);
+    out[4] = __fmul_rn(usn, kc.inv_KK1);
     const float sabs = df_to_f(f[4]);
     out[5] = (sabs > 0.f) ? __fdividef(fabsf(df_to_f(f[1])), sabs) : 0.f;
     const float num = df_sq_minus(f[1], f[5]);

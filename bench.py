@@ -342,6 +342,51 @@ def serving_leg(fc, plain, duration_s, seed, saturate=False):
             "windows": [s.window for s in trace], "rates_per_s": [round(s.rate_hz, 2) for s in trace]}
 
 
+CASES = {
+    # small, self-contained launches for profiler captures (a few GB at most)
+    "meg_bf16_window": dict(n=306, N=1000, fs=1000.0, band=(1.0, 100.0, 1024), W=100, prec="bf16", pushes=0,
+                            desc="306 MEG-shaped channels, one bulk push of 100 x 1000 samples, 101 bins, BF16 "
+                                 "tensor-core full window"),
+    "window_1024_fp32": dict(n=1024, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=100, prec="fp32", pushes=3,
+                             desc="1024 nodes, W = 100, 40 bins, full-window FP32 recompute: bulk fill + 3 pushes"),
+    "window_1024_bf16": dict(n=1024, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=100, prec="bf16", pushes=3,
+                             desc="1024 nodes, W = 100, 40 bins, BF16 tensor-core full window: bulk fill + 3 pushes"),
+}
+
+
+def run_case(args):
+    """One small named case (the profiler captures' workloads); prints its timing per push."""
+    import torch
+    from paper_2303_03279_gb300 import fc
+    from synth import meg_pink_trials, white_trials
+
+    c = CASES[args.case]
+    fc.load()
+    n, N, W = c["n"], c["N"], c["W"]
+    if args.case.startswith("meg"):
+        x = meg_pink_trials(3, W + c["pushes"], n, N)
+        x = x[0] if isinstance(x, tuple) else x
+    else:
+        x = white_trials(5, W + c["pushes"], n, N)
+    x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+    prec = {"fp32": fc.FC_PREC_FP32, "bf16": fc.FC_PREC_BF16}[c["prec"]]
+    with fc.Session(n, N, c["fs"], c["band"], "hann", fc.FC_SPECTRAL_METRICS, W, mode=fc.FC_MODE_FULL,
+                    precision=prec) as s:
+        fc.fc_push_trials(s.handle, x[:W].contiguous(), W)
+        fc.fc_sync(s.handle)
+        fc.fc_set_profiling(s.handle, True)
+        fc.fc_kernel_times(s.handle, reset=True)
+        t0 = time.perf_counter()
+        for k in range(c["pushes"]):
+            fc.fc_push_trial(s.handle, x[W + k])
+        fc.fc_sync(s.handle)
+        dt = (time.perf_counter() - t0) * 1000.0 / max(1, c["pushes"])
+        kt = fc.fc_kernel_times(s.handle, reset=True)
+    print(json.dumps({"case": args.case, "description": c["desc"], "ms_per_push": dt if c["pushes"] else None,
+                      "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in kt.items() if v[0]}}))
+    return 0
+
+
 def run_sweep(args):
     """Secondary sweep shaped like the paper's performance evaluation (Results 3.1: fs = nfft
     = 600 Hz, 8-12 Hz = 4 bins, storage mode off so that every evaluation recomputes the
@@ -620,6 +665,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cpu-all-core", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="print the paper-style performance sweep instead")
+    ap.add_argument("--case", choices=sorted(CASES), help="run one small named case (profiler captures)")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -627,6 +673,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.sweep:
         return run_sweep(args)
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args, w, args.workload)
     return run_ours(args, w, args.workload)

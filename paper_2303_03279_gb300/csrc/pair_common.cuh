@@ -68,6 +68,12 @@ __device__ __forceinline__ float df_sq_minus(df32 x, df32 s) {
     return __fadd_rn(__fsub_rn(ph, s.hi), __fsub_rn(pl, s.lo));
 }
 
+// Exact float of an integer |v| < 2^22 on the FP32 pipe: v added to the integer image of
+// 1.5 * 2^23 lands in the mantissa (unit spacing there), and subtracting 1.5 * 2^23 leaves v.
+__device__ __forceinline__ float small_int_to_float(int v) {
+    return __fsub_rn(__int_as_float(0x4B400000 + v), 12582912.0f);
+}
+
 // Per-bin metrics from the sums of one pair-bin (Supplementary Information 1).
 //   f[0..5]: CSD re, CSD im (= sum Im), phasor re, phasor im, sum |Im|, sum Im^2.
 //   out[0..6]: COH, IMAGCOHY, PLV, PLI, USPLI, WPLI, DSWPLI.
@@ -83,10 +89,17 @@ __device__ __forceinline__ void finalize_bin(const df32* f, int sign, float inv_
     out[1] = cim;
     const float ure = df_to_f(f[2]), uim = df_to_f(f[3]);
     out[2] = __fmul_rn(mag_from_sq(__fmaf_rn(ure, ure, __fmul_rn(uim, uim))), kc.inv_K);
-    out[3] = __fmul_rn((float)abs(sign), kc.inv_K);
-    // S^2 - K converted with one rounding; in 32 bits while it fits (|S| <= K <= 46340),
-    // which keeps the conversion off the FP64 pipe, the same value either way
-    const float usn = kc.K <= 46340 ? (float)(sign * sign - kc.K) : (float)((long long)sign * sign - kc.K);
+    // |S| and S^2 - K as floats, exactly: FP32-pipe arithmetic while |S^2 - K| < 2^22
+    // (K <= 2048), else integer conversions (one rounding, as for any K)
+    float pli_n, usn;
+    if (kc.K <= 2048) {
+        pli_n = small_int_to_float(abs(sign));
+        usn = small_int_to_float(sign * sign - kc.K);
+    } else {
+        pli_n = (float)abs(sign);
+        usn = kc.K <= 46340 ? (float)(sign * sign - kc.K) : (float)((long long)sign * sign - kc.K);
+    }
+    out[3] = __fmul_rn(pli_n, kc.inv_K);
     out[4] = __fmul_rn(usn, kc.inv_KK1);
     const float sabs = df_to_f(f[4]);
     out[5] = (sabs > 0.f) ? __fdividef(fabsf(df_to_f(f[1])), sabs) : 0.f;

@@ -4,7 +4,8 @@
 // Per trial k and node i: z_i = (x_i - mean x_i) / ||x_i - mean x_i|| (0 for a constant
 // node), so COR_k(i, j) = z_i . z_j. The network is the mean over the window's trials.
 // The products form a symmetric rank-N update (SYRK) over the upper triangle: 64 x 64
-// node tiles, 4 x 4 register micro-tiles, samples staged through shared memory. Each
+// node tiles, 4 x 4 register micro-tiles, samples staged through swizzled, double-buffered
+// shared memory. Each
 // trial's dot product is summed in FP32 in a fixed order (per 32-sample chunk, then
 // across chunks) and the per-trial values enter a double-float running sum, so the
 // value subtracted when a trial leaves the window has exactly the bits that were added.
@@ -56,24 +57,69 @@ __device__ __forceinline__ void tile_of(int tp, int nt, int& ta, int& tb) {
     tb = a + r;
 }
 
-// Dot products z_i^k . z_j^k of one trial for this thread's 4 x 4 pairs.
+// Shared tiles [t][row], unpadded, rows XOR-swizzled by the sample's 4-group: the staging
+// stores (4 rows x 8 float4 per warp) hit 32 distinct banks and the compute's float4 reads
+// of 4 consecutive rows stay aligned and in order.
+__device__ __forceinline__ int swz(int t, int r) { return r ^ (((t >> 2) & 7) << 2); }
+
+// This thread's share of one chunk of one tile: rows (tid >> 3) and (tid >> 3) + 32, samples
+// t0 + 4 (tid & 7) .. + 3 (float4 along the row when N % 4 == 0).
+__device__ __forceinline__ void load_chunk(const float* __restrict__ z, int n, int N, int tile, int t0, float4 v[2]) {
+    const int tid = threadIdx.x, t = t0 + 4 * (tid & 7);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int row = tile * CT + (tid >> 3) + 32 * q;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row < n) {
+            const float* zr = z + (size_t)row * N;
+            if ((N & 3) == 0 && t + 3 < N) {
+                x = *reinterpret_cast<const float4*>(zr + t);
+            } else {
+                if (t < N) x.x = zr[t];
+                if (t + 1 < N) x.y = zr[t + 1];
+                if (t + 2 < N) x.z = zr[t + 2];
+                if (t + 3 < N) x.w = zr[t + 3];
+            }
+        }
+        v[q] = x;
+    }
+}
+__device__ __forceinline__ void store_chunk(float (*S)[CT], const float4 v[2]) {
+    const int tid = threadIdx.x, t = 4 * (tid & 7);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int r = (tid >> 3) + 32 * q;
+        S[t + 0][swz(t + 0, r)] = v[q].x;
+        S[t + 1][swz(t + 1, r)] = v[q].y;
+        S[t + 2][swz(t + 2, r)] = v[q].z;
+        S[t + 3][swz(t + 3, r)] = v[q].w;
+    }
+}
+
+// Dot products z_i^k . z_j^k of one trial for this thread's 4 x 4 pairs: FP32 per 32-sample
+// chunk, the chunks added in order. Chunks are double-buffered: the next chunk is read into
+// registers while this one is multiplied.
 __device__ __forceinline__ void trial_dots(const float* __restrict__ z, int n, int N, int ta, int tb,
-                                           float (*As)[CT + 4], float (*Bs)[CT + 4], float d[4][4]) {
+                                           float (*As)[CK][CT], float (*Bs)[CK][CT], float d[4][4]) {
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int q = 0; q < 4; ++q) d[r][q] = 0.f;
-    for (int t0 = 0; t0 < N; t0 += CK) {
-        __syncthreads();
-        for (int e = tid; e < CT * CK; e += 256) {
-            const int r = e / CK, t = e % CK;
-            const int ni = ta * CT + r, nj = tb * CT + r;
-            const bool tv = t0 + t < N;
-            As[t][r] = (ni < n && tv) ? z[(size_t)ni * N + t0 + t] : 0.f;
-            Bs[t][r] = (nj < n && tv) ? z[(size_t)nj * N + t0 + t] : 0.f;
+    const int nchunk = (N + CK - 1) / CK;
+    float4 va[2], vb[2];
+    load_chunk(z, n, N, ta, 0, va);
+    load_chunk(z, n, N, tb, 0, vb);
+    __syncthreads();  // the previous user of the buffers is done
+    store_chunk(As[0], va);
+    store_chunk(Bs[0], vb);
+    __syncthreads();
+    for (int ch = 0; ch < nchunk; ++ch) {
+        const int cb = ch & 1;
+        if (ch + 1 < nchunk) {
+            load_chunk(z, n, N, ta, (ch + 1) * CK, va);
+            load_chunk(z, n, N, tb, (ch + 1) * CK, vb);
         }
-        __syncthreads();
         float p[4][4];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -81,8 +127,8 @@ __device__ __forceinline__ void trial_dots(const float* __restrict__ z, int n, i
             for (int q = 0; q < 4; ++q) p[r][q] = 0.f;
 #pragma unroll 8
         for (int t = 0; t < CK; ++t) {
-            const float4 ra = *reinterpret_cast<const float4*>(&As[t][ty * 4]);
-            const float4 rb = *reinterpret_cast<const float4*>(&Bs[t][tx * 4]);
+            const float4 ra = *reinterpret_cast<const float4*>(&As[cb][t][swz(t, ty * 4)]);
+            const float4 rb = *reinterpret_cast<const float4*>(&Bs[cb][t][swz(t, tx * 4)]);
             const float av[4] = {ra.x, ra.y, ra.z, ra.w};
             const float bv[4] = {rb.x, rb.y, rb.z, rb.w};
 #pragma unroll
@@ -94,6 +140,11 @@ __device__ __forceinline__ void trial_dots(const float* __restrict__ z, int n, i
         for (int r = 0; r < 4; ++r)
 #pragma unroll
             for (int q = 0; q < 4; ++q) d[r][q] = __fadd_rn(d[r][q], p[r][q]);
+        if (ch + 1 < nchunk) {  // the other buffer was last read before the previous barrier
+            store_chunk(As[cb ^ 1], va);
+            store_chunk(Bs[cb ^ 1], vb);
+        }
+        __syncthreads();
     }
 }
 
@@ -107,21 +158,22 @@ __global__ void __launch_bounds__(256) k_cor_update(CorArgs a) {
     int ta, tb;
     tile_of(blockIdx.x, nt, ta, tb);
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    __shared__ __align__(16) float As[CK][CT + 4];
-    __shared__ __align__(16) float Bs[CK][CT + 4];
+    __shared__ __align__(16) float As[2][CK][CT];
+    __shared__ __align__(16) float Bs[2][CK][CT];
 
-    long long idx[4][4];
-    bool ok[4][4];
+    // pair (i, j) of micro-tile entry (r, q); recomputed where needed to spare registers
+    const int i0 = ta * CT + ty * 4, j0 = tb * CT + tx * 4;
     df32 acc[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int i = ta * CT + ty * 4 + r, j = tb * CT + tx * 4 + q;
-            ok[r][q] = i < j && j < a.n;
-            idx[r][q] = ok[r][q] ? packed_index(i, j, a.n) : 0;
+            const int i = i0 + r, j = j0 + q;
             acc[r][q] = df_make(0.f, 0.f);
-            if (a.mode == 0 && ok[r][q]) acc[r][q] = df_make(a.cor_acc[idx[r][q]], a.cor_acc[a.P + idx[r][q]]);
+            if (a.mode == 0 && i < j && j < a.n) {
+                const long long id = packed_index(i, j, a.n);
+                acc[r][q] = df_make(a.cor_acc[id], a.cor_acc[a.P + id]);
+            }
         }
     float d[4][4];
     if (a.mode == 0) {
@@ -154,10 +206,12 @@ __global__ void __launch_bounds__(256) k_cor_update(CorArgs a) {
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            if (!ok[r][q]) continue;
-            a.cor_acc[idx[r][q]] = acc[r][q].hi;
-            a.cor_acc[a.P + idx[r][q]] = acc[r][q].lo;
-            if (a.finalize) a.net[idx[r][q]] = __fmul_rn(df_to_f(acc[r][q]), invK);
+            const int i = i0 + r, j = j0 + q;
+            if (!(i < j && j < a.n)) continue;
+            const long long id = packed_index(i, j, a.n);
+            a.cor_acc[id] = acc[r][q].hi;
+            a.cor_acc[a.P + id] = acc[r][q].lo;
+            if (a.finalize) a.net[id] = __fmul_rn(df_to_f(acc[r][q]), invK);
         }
 }
 

@@ -321,7 +321,8 @@ __global__ void __launch_bounds__(256, 2) k_stream(const StreamBatch batch) {
         const int timed_out = __syncthreads_or(arrived ? 0 : 1);
         if (timed_out) {
             if (tid == 0) atomicOr(&const_cast<FcCtrl*>(a.ctrl)->timeout, 1);
-            // let the other stage's copy land before leaving (bounded)
+            // let both stages' copies land before leaving (bounded)
+            mbar_wait_bounded(&mbar[st], parity);
             mbar_wait_bounded(&mbar[st ^ 1], ((it + 1) >> 1) & 1);
             return;
         }

@@ -14,6 +14,8 @@
 // length-L transform is done as a complex length-M = L/2 transform plus the standard
 // even/odd split (forward) or merge (inverse). Twiddles come from a host-built FP64 table
 // rounded to FP32 (tw[k] = exp(-2 pi i k / L), k < L/2).
+#include <climits>
+
 #include "df32.cuh"
 #include "fc_internal.h"
 
@@ -187,6 +189,118 @@ __global__ void k_xcor_pairs(XcorArgs a, long long n_items, long long first_tria
     }
 }
 
+// Register form for transforms of M = 32 E points (E = 2 .. 64, trials up to 2,048
+// samples): lane l holds elements l + 32 r, r < E. The inverse transform runs as radix-2
+// decimation in frequency on natural-order input: spans of 32 or more pair registers of
+// the same lane, shorter spans pair lanes through __shfl_xor_sync; twiddles come from a
+// per-block copy of the table in shared memory. The output lands in bit-reversed order,
+// which the scan over lags reads through the bit reversal of each position. No shared
+// memory holds data and no barrier runs between the stages.
+template <int E>
+__global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_items, long long first_trial,
+                                                       int n_trials) {
+    constexpr int M = 32 * E;
+    __shared__ float2 stw[M];  // tw[k] = e^{-2 pi i k / L}, k < M
+    const FcCtrl* c = a.ctrl;
+    if (c->bad) return;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) stw[k] = a.tw[k];
+    __syncthreads();
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (item >= n_items) return;
+    const long long p = item / n_trials;
+    const long long trial = c->pushed + first_trial + item % n_trials;
+    if (trial < 0) return;  // window not yet full
+    int i, j;
+    unpack_pair(p, a.n, i, j);
+    const int slot = (int)(trial % a.slots);
+    const float2* Zi = a.spec + ((size_t)slot * a.n + i) * (M + 1);
+    const float2* Zj = a.spec + ((size_t)slot * a.n + j) * (M + 1);
+    // Y[k] = E[k] + i O[k], E = (P[k] + conj P[M-k]) / 2, O = (P[k] - conj P[M-k]) e^{+2 pi i k/L} / 2
+    float2 x[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int k = lane + 32 * r;
+        const float2 pk = cmul(Zi[k], cconj(Zj[k]));
+        const float2 pm = cconj(cmul(Zi[M - k], cconj(Zj[M - k])));
+        const float2 e = make_float2(0.5f * __fadd_rn(pk.x, pm.x), 0.5f * __fadd_rn(pk.y, pm.y));
+        const float2 dd = csub(pk, pm);
+        const float2 w = cconj(stw[k]);  // e^{+2 pi i k / L}
+        const float2 o = cmul(make_float2(0.5f * dd.x, 0.5f * dd.y), w);
+        x[r] = make_float2(__fsub_rn(e.x, o.y), __fadd_rn(e.y, o.x));
+    }
+    // inverse transform (e^{+2 pi i ...}), decimation in frequency
+#pragma unroll
+    for (int h = M / 2; h >= 32; h >>= 1) {  // partner in this lane's registers
+        constexpr int dummy = 0;
+        (void)dummy;
+        const int hr = h / 32;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            if ((r % (2 * hr)) >= hr) continue;
+            const int e = lane + 32 * r;
+            const float2 u = x[r], v = x[r + hr];
+            const float2 w = cconj(stw[(e % h) * (M / h)]);
+            x[r] = cadd(u, v);
+            x[r + hr] = cmul(csub(u, v), w);
+        }
+    }
+#pragma unroll
+    for (int h = (M / 2 < 16 ? M / 2 : 16); h >= 1; h >>= 1) {  // partner in lane ^ h
+        const bool upper = (lane & h) != 0;
+        const float2 w = cconj(stw[(lane % h) * (M / h)]);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const float2 mine = x[r];
+            const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, mine.x, h),
+                                             __shfl_xor_sync(0xffffffffu, mine.y, h));
+            x[r] = upper ? cmul(csub(other, mine), w) : cadd(mine, other);
+        }
+    }
+    // position e holds y[bitrev(e)]; r[2m] = Re y[m] / M, r[2m+1] = Im y[m] / M
+    int bits = 0;
+    while ((1 << bits) < M) ++bits;
+    float best = -INFINITY;
+    int best_tau = 0;
+    const float invM = 1.0f / (float)M;
+    const int L = 2 * M;
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int m = bitrev(lane + 32 * r, bits);
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+            const int idx = 2 * m + part;
+            const int tau = idx <= a.N - 1 ? idx : (idx >= L - (a.N - 1) ? idx - L : INT_MIN);
+            if (tau == INT_MIN) continue;
+            const float v = __fmul_rn(part ? x[r].y : x[r].x, invM);
+            if (better(v, tau, best, best_tau)) {
+                best = v;
+                best_tau = tau;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int ot = __shfl_xor_sync(0xffffffffu, best_tau, o);
+        if (better(ov, ot, best, best_tau)) {
+            best = ov;
+            best_tau = ot;
+        }
+    }
+    if (lane == 0) {
+        const float ei = a.energy[(size_t)slot * a.n + i], ej = a.energy[(size_t)slot * a.n + j];
+        const float den = __fmul_rn(sqrtf(ei), sqrtf(ej));
+        float v = 0.f;
+        int lag = 0;
+        if (den > 0.f) {
+            v = __fdiv_rn(best, den);
+            lag = best_tau;
+        }
+        a.vals[(size_t)slot * a.P + p] = v;
+        if (trial == c->pushed + a.count - 1) a.lag[p] = lag;
+    }
+}
+
 // ------------------------------------------------------------------ network update
 __global__ void k_xcor_update(XcorArgs a) {
     const FcCtrl* c = a.ctrl;
@@ -246,7 +360,17 @@ cudaError_t launch_xcor_pairs(const XcorArgs& a, cudaStream_t st) {
         cudaError_t e = cudaFuncSetAttribute(k_xcor_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    (void)M;
+    // register form for M = 64 .. 2048 (8 warps per block), shared-memory form otherwise
+    const unsigned rb = (unsigned)((items + 7) / 8);
+    switch (M) {
+        case 64: k_xcor_pairs_reg<2><<<rb, 256, 0, st>>>(a, items, first, n_trials); return cudaGetLastError();
+        case 128: k_xcor_pairs_reg<4><<<rb, 256, 0, st>>>(a, items, first, n_trials); return cudaGetLastError();
+        case 256: k_xcor_pairs_reg<8><<<rb, 256, 0, st>>>(a, items, first, n_trials); return cudaGetLastError();
+        case 512: k_xcor_pairs_reg<16><<<rb, 256, 0, st>>>(a, items, first, n_trials); return cudaGetLastError();
+        case 1024: k_xcor_pairs_reg<32><<<rb, 256, 0, st>>>(a, items, first, n_trials); return cudaGetLastError();
+        case 2048: k_xcor_pairs_reg<64><<<rb, 256, 0, st>>>(a, items, first, n_trials); return cudaGetLastError();
+        default: break;
+    }
     k_xcor_pairs<<<(unsigned)((items + wpb - 1) / wpb), wpb * 32, sm, st>>>(a, items, first, n_trials);
     return cudaGetLastError();
 }

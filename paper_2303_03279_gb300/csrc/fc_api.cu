@@ -205,6 +205,7 @@ CorArgs cor_args(fc_session* s, const float* x, int count, int write_from, int m
     a.P = s->P;
     a.mode = mode;
     a.finalize = (s->mask & FC_COR) ? 1 : 0;
+    a.groups = 1;
     a.ctrl = s->ctrl;
     return a;
 }
@@ -246,8 +247,28 @@ fc_status stage_spectra(fc_session* s, const float* x, int count, int write_from
 fc_status stage_time_metrics(fc_session* s, const float* x, int count, int write_from, int mode) {
     if (s->time_mask & FC_COR) {
         CorArgs ca = cor_args(s, x, count, write_from, mode);
+        if (mode == 1) {
+            // few tile pairs: split the window's trials over several CTAs per tile pair
+            const int nt = (s->n + 63) / 64, ntp_cor = nt * (nt + 1) / 2;
+            const long long k_est = s->W > 0 ? std::min<long long>(s->W, s->enqueued + count) : s->enqueued + count;
+            const int G = (int)std::max<long long>(1, std::min<long long>({(2LL * s->num_sms + ntp_cor - 1) / ntp_cor,
+                                                                          k_est, 64}));
+            if (G > 1) {
+                const size_t need = (size_t)G * 2 * s->P;
+                if (s->cor_part_len < need) {
+                    if (s->cor_part) cudaFree(s->cor_part);
+                    s->cor_part = nullptr;
+                    s->cor_part_len = 0;
+                    CK(cudaMalloc(&s->cor_part, need * sizeof(float)));
+                    s->cor_part_len = need;
+                }
+                ca.groups = G;
+                ca.part = s->cor_part;
+            }
+        }
         LAUNCH(FC_K_COR, launch_cor_normalize(ca, s->stream));
         LAUNCH(FC_K_COR, launch_cor_update(ca, s->stream));
+        if (ca.groups > 1) LAUNCH(FC_K_COR, launch_cor_combine(ca, s->stream));
     }
     if (s->time_mask & FC_XCOR) {
         XcorArgs xa = xcor_args(s, x, count, write_from, mode);
@@ -697,6 +718,7 @@ fc_status fc_session_destroy(fc_session* s) {
     if (s->post_scratch) cudaFree(s->post_scratch);
     if (s->proj) cudaFree(s->proj);
     if (s->proj_in) cudaFree(s->proj_in);
+    if (s->cor_part) cudaFree(s->cor_part);
     delete s;
     return FC_OK;
 }

@@ -90,6 +90,8 @@ struct fc_session {
     size_t dense_scratch_len;
     void* post_scratch;     // network post-processing: select state, ties, flags, outputs
     size_t post_scratch_len;
+    float* cor_part;        // COR full-window trial-group partial sums (allocated on demand)
+    size_t cor_part_len;
     float* proj;            // source projection M [n][proj_C] (NULL: none)
     int proj_C;
     float* proj_in;         // staged sensor trials [proj_in_trials][proj_C][N]
@@ -245,10 +247,13 @@ struct CorArgs {
     long long P;
     int mode;           // 0 = stream add/subtract, 1 = full recompute of the window
     int finalize;
+    int groups;         // mode 1: the window's trials split over this many CTAs per tile pair
+    float* part;        // groups > 1: per-group double-float sums [groups][2][P]
     const FcCtrl* ctrl;
 };
 cudaError_t launch_cor_normalize(const CorArgs& a, cudaStream_t st);
 cudaError_t launch_cor_update(const CorArgs& a, cudaStream_t st);
+cudaError_t launch_cor_combine(const CorArgs& a, cudaStream_t st);
 
 struct XcorArgs {
     const float* x;     // [count][n][N]

@@ -193,7 +193,11 @@ __global__ void __launch_bounds__(256) k_cor_update(CorArgs a) {
                 for (int q = 0; q < 4; ++q) acc[r][q] = df_add_f(acc[r][q], -d[r][q]);
         }
     } else {
-        for (long long k = start; k < end; ++k) {
+        // this CTA's share of the window's trials (several groups when tile pairs are few)
+        const int tg = (K + a.groups - 1) / a.groups;
+        const long long k0 = start + (long long)blockIdx.y * tg;
+        const long long k1 = k0 + tg < end ? k0 + tg : end;
+        for (long long k = k0; k < k1; ++k) {
             trial_dots(a.zring + (size_t)(k % a.slots) * a.n * a.N, a.n, a.N, ta, tb, As, Bs, d);
 #pragma unroll
             for (int r = 0; r < 4; ++r)
@@ -202,6 +206,7 @@ __global__ void __launch_bounds__(256) k_cor_update(CorArgs a) {
         }
     }
     const float invK = 1.0f / (float)K;
+    const bool partial = a.mode == 1 && a.groups > 1;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -209,13 +214,40 @@ __global__ void __launch_bounds__(256) k_cor_update(CorArgs a) {
             const int i = i0 + r, j = j0 + q;
             if (!(i < j && j < a.n)) continue;
             const long long id = packed_index(i, j, a.n);
+            if (partial) {
+                a.part[(2 * (size_t)blockIdx.y) * a.P + id] = acc[r][q].hi;
+                a.part[(2 * (size_t)blockIdx.y + 1) * a.P + id] = acc[r][q].lo;
+                continue;
+            }
             a.cor_acc[id] = acc[r][q].hi;
             a.cor_acc[a.P + id] = acc[r][q].lo;
             if (a.finalize) a.net[id] = __fmul_rn(df_to_f(acc[r][q]), invK);
         }
 }
 
+// Sum of the trial groups' double-float partial sums, in group order.
+__global__ void k_cor_combine(CorArgs a) {
+    const FcCtrl* c = a.ctrl;
+    if (c->bad) return;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.P) return;
+    const long long end = c->pushed + a.count;
+    const long long start = (a.W > 0 && end > a.W) ? end - a.W : 0;
+    const int K = (int)(end - start);
+    df32 acc = df_make(0.f, 0.f);
+    for (int g = 0; g < a.groups; ++g)
+        acc = df_add_df(acc, df_make(a.part[(2 * (size_t)g) * a.P + p], a.part[(2 * (size_t)g + 1) * a.P + p]));
+    a.cor_acc[p] = acc.hi;
+    a.cor_acc[a.P + p] = acc.lo;
+    if (a.finalize) a.net[p] = __fmul_rn(df_to_f(acc), 1.0f / (float)K);
+}
+
 }  // namespace
+
+cudaError_t launch_cor_combine(const CorArgs& a, cudaStream_t st) {
+    k_cor_combine<<<(unsigned)((a.P + 255) / 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_cor_normalize(const CorArgs& a, cudaStream_t st) {
     const long long warps = (long long)(a.count - a.write_from) * a.n;
@@ -226,6 +258,7 @@ cudaError_t launch_cor_normalize(const CorArgs& a, cudaStream_t st) {
 
 cudaError_t launch_cor_update(const CorArgs& a, cudaStream_t st) {
     const int nt = (a.n + CT - 1) / CT;
-    k_cor_update<<<nt * (nt + 1) / 2, 256, 0, st>>>(a);
+    if (a.groups < 1 || (a.groups > 1 && (a.mode != 1 || !a.part))) return cudaErrorInvalidValue;
+    k_cor_update<<<dim3(nt * (nt + 1) / 2, a.mode == 1 ? a.groups : 1), 256, 0, st>>>(a);
     return cudaGetLastError();
 }

@@ -1,0 +1,49 @@
+"""XCOR across transform lengths: every register-resident size (transforms of 64 .. 2048
+points) and the shared-memory kernel beyond, against the oracle (values within 1e-5; the
+reported lag attains the maximum within 1e-5)."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import white_trials
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2303_03279_gb300 import fc  # noqa: E402
+from _fc_helpers import assert_close  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fc.load()
+
+
+# N -> transform length L = next power of two >= 2N - 1, complex size M = L / 2
+@pytest.mark.parametrize("N", [20, 40, 70, 130, 300, 600, 1500, 3000])
+def test_xcor_matches_oracle_at_every_transform_length(N):
+    n, K = 24, 3
+    x = white_trials(100 + N, K, n, N)
+    # a shifted copy gives a known lag
+    x[:, 1, :] = np.roll(x[:, 0, :], 5)
+    with fc.Session(n, N, 1000.0, (1.0, 50.0, max(64, 1 << (N - 1).bit_length())), "hann", fc.FC_XCOR, K) as s:
+        s.push(x)
+        got = s.network("XCOR", packed=True)[0]
+        lags = s.xcor_lags()
+    val, _ = O.xcor_network(x)
+    iu = np.triu_indices(n, 1)
+    assert_close(got, val[iu], what=f"XCOR N={N}")
+    # the newest trial's lags attain the maximum
+    last = x[-1].astype(np.float64)
+    for p in range(0, len(iu[0]), 7):
+        i, j = iu[0][p], iu[1][p]
+        v, _ = O.xcor_trial_pair(last[i], last[j])
+        xi, xj = last[i] - last[i].mean(), last[j] - last[j].mean()
+        tau = int(lags[p])
+        r = np.dot(xi[tau:], xj[:N - tau]) if tau >= 0 else np.dot(xi[:N + tau], xj[-tau:])
+        assert r / math.sqrt(np.dot(xi, xi) * np.dot(xj, xj)) >= v - 1e-5, (N, i, j)

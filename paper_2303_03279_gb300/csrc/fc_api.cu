@@ -451,30 +451,54 @@ fc_status fc_push_single(fc_session* s, const float* xdev) {
     return push_one_stream(s, xdev, true);
 }
 
-fc_status fc_push_stage_pre(fc_session* s, const float* xdev) {
-    const long long nx = (long long)s->n * s->N;
-    LAUNCH(FC_K_OTHER, launch_validate(xdev, nx, s->ctrl, s->stream));
-    fc_status st = stage_spectra(s, xdev, 1, 0);
-    if (st != FC_OK) return st;
-    NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, push_node_mode(s), s->ctrl, 1};
-    LAUNCH(FC_K_NODE, launch_node(na, s->stream));
-    return FC_OK;
-}
-
 PairArgs fc_push_stream_args(fc_session* s) {
     PairArgs pa = pair_args(s, true, 1);
     pa.finalize = (s->mask & FC_SPECTRAL_METRICS) ? 1 : 0;
     return pa;
 }
 
-fc_status fc_push_stage_post(fc_session* s) {
-    PairArgs pa = fc_push_stream_args(s);
-    if (pa.finalize && pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
-    fc_status st = stage_resum_slice(s);
-    if (st != FC_OK) return st;
-    CommitArgs ca{s->ctrl, 1};
-    LAUNCH(FC_K_OTHER, launch_commit(ca, s->stream));
-    s->enqueued += 1;
+// The same stages for several sessions at once (one launch per stage for all of them);
+// every session must be one fc_push_needs_single declines, all on the stream st.
+fc_status fc_push_batch_pre(fc_session* const* ss, const float* const* x, int count, cudaStream_t st) {
+    if (count <= 0) return FC_OK;
+    if (count > FC_MAX_BATCH) return fail(FC_ERR_INVALID_ARG, "batch of %d sessions (at most %d)", count, FC_MAX_BATCH);
+    PreBatch b;
+    b.nsess = count;
+    b.val_prefix[0] = 0;
+    b.spec_prefix[0] = 0;
+    b.node_prefix[0] = 0;
+    for (int i = 0; i < count; ++i) {
+        fc_session* s = ss[i];
+        b.sp[i] = spectrum_args(s, x[i], 1, 0);
+        b.nd[i] = NodeArgs{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, push_node_mode(s), s->ctrl, 1};
+        b.val_prefix[i + 1] = b.val_prefix[i] + (long long)s->n * s->N;
+        b.spec_prefix[i + 1] = b.spec_prefix[i] + ((s->n + 31) / 32) * ((s->B + 31) / 32);
+        b.node_prefix[i + 1] = b.node_prefix[i] + s->B * s->n;
+    }
+    fc_session* s = ss[0];  // launches are counted (and timed) on the first session
+    LAUNCH(FC_K_OTHER, launch_validate_batch(b, st));
+    LAUNCH(FC_K_SPECTRUM, launch_spectrum_batch(b, st));
+    LAUNCH(FC_K_NODE, launch_node_batch(b, st));
+    return FC_OK;
+}
+
+fc_status fc_push_batch_post(fc_session* const* ss, FcCtrl* const* snap, int count, cudaStream_t st) {
+    if (count <= 0) return FC_OK;
+    if (count > FC_MAX_BATCH) return fail(FC_ERR_INVALID_ARG, "batch of %d sessions (at most %d)", count, FC_MAX_BATCH);
+    CommitBatch b;
+    b.nsess = count;
+    for (int i = 0; i < count; ++i) {
+        fc_session* s = ss[i];
+        PairArgs pa = fc_push_stream_args(s);
+        if (pa.finalize && pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
+        fc_status r = stage_resum_slice(s);
+        if (r != FC_OK) return r;
+        b.ctrl[i] = s->ctrl;
+        b.snap[i] = snap ? snap[i] : nullptr;
+    }
+    fc_session* s = ss[0];
+    LAUNCH(FC_K_OTHER, launch_commit_batch(b, st));
+    for (int i = 0; i < count; ++i) ss[i]->enqueued += 1;
     return FC_OK;
 }
 

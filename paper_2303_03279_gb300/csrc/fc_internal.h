@@ -236,6 +236,29 @@ struct CommitArgs {
 };
 cudaError_t launch_commit(const CommitArgs& a, cudaStream_t st);
 
+// Several sessions' one-trial pushes in one launch per stage (serving): validation,
+// spectrum and per-node sums of up to FC_MAX_BATCH sessions; the sessions' elements / CTAs
+// follow each other (prefix sums), the work per session is that of the single kernels.
+struct PreBatch {
+    int nsess;
+    long long val_prefix[FC_MAX_BATCH + 1];  // trial samples to validate
+    int spec_prefix[FC_MAX_BATCH + 1];       // spectrum CTAs (32 nodes x 32 bins each)
+    int node_prefix[FC_MAX_BATCH + 1];       // node-bin elements
+    SpectrumArgs sp[FC_MAX_BATCH];
+    NodeArgs nd[FC_MAX_BATCH];
+};
+cudaError_t launch_validate_batch(const PreBatch& b, cudaStream_t st);
+cudaError_t launch_spectrum_batch(const PreBatch& b, cudaStream_t st);
+cudaError_t launch_node_batch(const PreBatch& b, cudaStream_t st);
+// Commit of several sessions' one-trial pushes; snap[s] (host memory reachable from the
+// device, may be NULL) receives session s's control block after its commit.
+struct CommitBatch {
+    int nsess;
+    FcCtrl* ctrl[FC_MAX_BATCH];
+    FcCtrl* snap[FC_MAX_BATCH];
+};
+cudaError_t launch_commit_batch(const CommitBatch& b, cudaStream_t st);
+
 // time-domain metrics
 struct CorArgs {
     const float* x;     // [count][n][N] raw trials
@@ -298,16 +321,19 @@ cudaError_t launch_network_top(const float* w, long long P, int n, long long k, 
 
 void fc_internal_set_error(const char* msg);
 
-// A streaming push split into pieces, for the serving engine (fc_server.cu): the trial is
-// already in s->x_stage (device). pre: validate, spectrum, per-node sums; the pair update
-// is batched across sessions (launch_stream_batch with fc_push_stream_args); post: band
-// reduction (if any), commit, bookkeeping. Sessions that are uncalibrated, due for a
-// re-sum, hold COR/XCOR or are in full mode take fc_push_single instead.
+// Streaming pushes of several sessions split into stages, for the serving engine
+// (fc_server.cu): each trial is already on the device (x[i]). pre: validation, spectrum and
+// per-node sums of all sessions, one launch per stage; the pair update is batched across
+// sessions (launch_stream_batch with fc_push_stream_args); post: band reduction (if any),
+// the drift re-sum slice, then one commit of all sessions with bookkeeping. Every session
+// runs on the stream st; snap[i] (device-visible host memory, or NULL) receives session
+// i's control block after its commit. Sessions that are uncalibrated, hold COR/XCOR or are
+// in full mode take fc_push_single instead.
 bool fc_push_needs_single(fc_session* s);
 fc_status fc_push_single(fc_session* s, const float* xdev);
-fc_status fc_push_stage_pre(fc_session* s, const float* xdev);
 PairArgs fc_push_stream_args(fc_session* s);
-fc_status fc_push_stage_post(fc_session* s);
+fc_status fc_push_batch_pre(fc_session* const* ss, const float* const* x, int count, cudaStream_t st);
+fc_status fc_push_batch_post(fc_session* const* ss, FcCtrl* const* snap, int count, cudaStream_t st);
 void fc_count_launch(fc_session* s);
 size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode mode);
 int fc_band_bins(double fs, fc_band band, int* first);

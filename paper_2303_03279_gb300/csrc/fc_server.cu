@@ -69,6 +69,7 @@ struct SrvSession {
     long long partial = 0;
     float* pinned[2] = {nullptr, nullptr};  // trial staging, by tick parity
     FcCtrl* pinned_ctrl = nullptr;          // [2] control-block read-back, by tick parity
+    FcCtrl* pinned_ctrl_dev = nullptr;      // the same memory as the device addresses it
     long long rejected_seen = 0;
     bool closing = false;
 };
@@ -206,20 +207,30 @@ fc_status enqueue_tick(fc_server* sv, const std::vector<Part>& plan, InFlight& f
                                         cudaMemcpyHostToDevice, sv->stream);
         if (e != cudaSuccess) return sfail(FC_ERR_CUDA, cudaGetErrorString(e));
     }
+    // singles (calibrating first pushes and the like) run whole, each on its own
+    for (const Part& p : plan) {
+        if (!p.single) continue;
+        fc_status st = fc_push_single(p.ss->s, p.ss->s->x_stage);
+        if (st != FC_OK) return st;
+    }
+    // validation, spectra and per-node sums of every push that starts: one launch each
+    fc_session* pre_s[FC_MAX_BATCH];
+    const float* pre_x[FC_MAX_BATCH];
+    int npre = 0;
+    for (const Part& p : plan) {
+        if (p.single || !p.start) continue;
+        pre_s[npre] = p.ss->s;
+        pre_x[npre] = p.ss->s->x_stage;
+        ++npre;
+    }
+    fc_status pst = fc_push_batch_pre(pre_s, pre_x, npre, sv->stream);
+    if (pst != FC_OK) return pst;
     StreamBatch b;
     b.nsess = 0;
     b.unit_prefix[0] = 0;
     for (const Part& p : plan) {
         fc_session* s = p.ss->s;
-        if (p.single) {
-            fc_status st = fc_push_single(s, s->x_stage);
-            if (st != FC_OK) return st;
-            continue;
-        }
-        if (p.start) {
-            fc_status st = fc_push_stage_pre(s, s->x_stage);
-            if (st != FC_OK) return st;
-        }
+        if (p.single) continue;
         PairArgs pa = fc_push_stream_args(s);
         pa.u0 = (int)p.u0;
         b.a[b.nsess] = pa;
@@ -230,23 +241,29 @@ fc_status enqueue_tick(fc_server* sv, const std::vector<Part>& plan, InFlight& f
         cudaError_t e = launch_stream_batch(b, 2 * sv->num_sms, sv->stream);
         if (e != cudaSuccess) return sfail(FC_ERR_CUDA, cudaGetErrorString(e));
     }
+    // drift re-sum slices, then one commit of every push that finishes; the commit also
+    // writes each control block (prescale, rejection count) to the session's pinned slot
+    fc_session* post_s[FC_MAX_BATCH];
+    FcCtrl* post_snap[FC_MAX_BATCH];
+    int npost = 0;
     for (const Part& p : plan) {
         SrvSession* ss = p.ss;
-        if (!p.single) {
-            fc_count_launch(ss->s);
-            ss->partial = p.finish ? 0 : p.u0 + p.nu;
-            if (p.finish) {
-                fc_status st = fc_push_stage_post(ss->s);
-                if (st != FC_OK) return st;
-            }
-        }
-        if (p.finish) {
-            // control block after the commit: prescale (calibration) and rejection count
+        if (p.single) {
             cudaError_t e = cudaMemcpyAsync(&ss->pinned_ctrl[slot], ss->s->ctrl, sizeof(FcCtrl),
                                             cudaMemcpyDeviceToHost, sv->stream);
             if (e != cudaSuccess) return sfail(FC_ERR_CUDA, cudaGetErrorString(e));
+            continue;
+        }
+        fc_count_launch(ss->s);
+        ss->partial = p.finish ? 0 : p.u0 + p.nu;
+        if (p.finish) {
+            post_s[npost] = ss->s;
+            post_snap[npost] = ss->pinned_ctrl_dev + slot;
+            ++npost;
         }
     }
+    pst = fc_push_batch_post(post_s, post_snap, npost, sv->stream);
+    if (pst != FC_OK) return pst;
     if (!sv->event_pool.empty()) {
         fl.ev = sv->event_pool.back();
         sv->event_pool.pop_back();
@@ -355,6 +372,7 @@ void free_pinned(SrvSession* ss) {
     if (ss->pinned_ctrl) cudaFreeHost(ss->pinned_ctrl);
     ss->pinned[0] = ss->pinned[1] = nullptr;
     ss->pinned_ctrl = nullptr;
+    ss->pinned_ctrl_dev = nullptr;
 }
 
 }  // namespace
@@ -435,7 +453,8 @@ fc_status fc_server_open(fc_server* sv, int n_nodes, int n_samples, double fs, f
     ss->pair_bins = s->P * s->B;
     ss->trial_floats = (size_t)n_nodes * n_samples;
     ss->units = sv->cfg.plain ? 1 : (long long)s->ntp * s->stream_groups;
-    bool pinned_ok = cudaMallocHost(&ss->pinned_ctrl, 2 * sizeof(FcCtrl)) == cudaSuccess;
+    bool pinned_ok = cudaHostAlloc(&ss->pinned_ctrl, 2 * sizeof(FcCtrl), cudaHostAllocMapped) == cudaSuccess &&
+                     cudaHostGetDevicePointer(&ss->pinned_ctrl_dev, ss->pinned_ctrl, 0) == cudaSuccess;
     for (int k = 0; k < 2 && pinned_ok; ++k)
         pinned_ok = cudaMallocHost(&ss->pinned[k], ss->trial_floats * sizeof(float)) == cudaSuccess;
     if (!pinned_ok) {

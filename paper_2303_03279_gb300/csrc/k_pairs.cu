@@ -21,10 +21,9 @@ namespace {
 using namespace fcpair;
 
 // ------------------------------------------------------------------------------- node
-__global__ void k_node(NodeArgs a) {
+__device__ __forceinline__ void node_elem(const NodeArgs& a, int e) {
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= a.B * a.n) return;
     const int f = e / a.n, i = e % a.n;
     double s;
@@ -47,6 +46,17 @@ __global__ void k_node(NodeArgs a) {
     }
     a.psd[e] = s;
     a.inv_psd[e] = (s > 0.0) ? (float)(1.0 / sqrt(s)) : 0.f;
+}
+
+__global__ void k_node(NodeArgs a) { node_elem(a, blockIdx.x * blockDim.x + threadIdx.x); }
+
+// Several sessions: their node-bin elements follow each other (node_prefix).
+__global__ void k_node_batch(PreBatch b) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b.nsess <= 0 || e >= b.node_prefix[b.nsess]) return;
+    int s = 0;
+    while (s + 1 < b.nsess && e >= b.node_prefix[s + 1]) ++s;
+    node_elem(b.nd[s], e - b.node_prefix[s]);
 }
 
 // ---------------------------------------------------------------- full-window sums
@@ -276,6 +286,13 @@ __global__ void k_df_planes(const float* acc2, long long P, double* out) {
 cudaError_t launch_node(const NodeArgs& a, cudaStream_t st) {
     const int total = a.B * a.n;
     k_node<<<(total + 255) / 256, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_node_batch(const PreBatch& b, cudaStream_t st) {
+    const int total = b.nsess > 0 ? b.node_prefix[b.nsess] : 0;
+    if (total <= 0) return cudaSuccess;
+    k_node_batch<<<(total + 255) / 256, 256, 0, st>>>(b);
     return cudaGetLastError();
 }
 

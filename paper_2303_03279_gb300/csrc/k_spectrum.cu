@@ -10,6 +10,8 @@
 // put a 1e-3 relative error into every spectrum and hence into every metric.
 #include "fc_internal.h"
 
+#include <algorithm>
+
 namespace {
 
 // ---------------------------------------------------------------- validation
@@ -24,17 +26,30 @@ __global__ void k_validate(const float* __restrict__ x, long long count, FcCtrl*
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctrl->bad, 1);
 }
 
+// Several sessions' trials: blockIdx.y = session, its blocks stride over its samples.
+__global__ void k_validate_batch(PreBatch b) {
+    const int s = blockIdx.y;
+    const long long count = b.val_prefix[s + 1] - b.val_prefix[s];
+    const float* x = b.sp[s].x;
+    int bad = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        bad |= !isfinite(x[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&b.sp[s].ctrl->bad, 1);
+}
+
 // ---------------------------------------------------------------- spectrum
 // CTA: 32 nodes x 32 bins of one trial. Thread (ty, tx): node ty, bins 4tx..4tx+3.
 constexpr int SP_NODES = 32;
 constexpr int SP_BINS = 32;
 constexpr int SP_CHUNK = 64;
 
-__global__ void __launch_bounds__(256) k_spectrum(SpectrumArgs a) {
+// One CTA's tile (node block bx, bin block by, trial write_from + bz); CTA-uniform exits.
+__device__ __forceinline__ void spectrum_tile(const SpectrumArgs& a, int bx, int by, int bz) {
     if (a.ctrl->bad) return;
-    const int trial = a.write_from + blockIdx.z;
-    const int node0 = blockIdx.x * SP_NODES;
-    const int bin0 = blockIdx.y * SP_BINS;
+    const int trial = a.write_from + bz;
+    const int node0 = bx * SP_NODES;
+    const int bin0 = by * SP_BINS;
     const int tid = threadIdx.x;
     const int ty = tid >> 3, tx = tid & 7;
     __shared__ float xs[SP_NODES][SP_CHUNK + 1];
@@ -94,6 +109,22 @@ __global__ void __launch_bounds__(256) k_spectrum(SpectrumArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(256) k_spectrum(SpectrumArgs a) {
+    spectrum_tile(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// One trial of each of several sessions: the sessions' CTAs follow each other
+// (spec_prefix), each CTA computes the same tile as k_spectrum would.
+__global__ void __launch_bounds__(256) k_spectrum_batch(PreBatch b) {
+    const int cta = blockIdx.x;
+    int s = 0;
+    while (s + 1 < b.nsess && cta >= b.spec_prefix[s + 1]) ++s;
+    const SpectrumArgs& a = b.sp[s];
+    const int l = cta - b.spec_prefix[s];
+    const int gx = (a.n + SP_NODES - 1) / SP_NODES;
+    spectrum_tile(a, l % gx, l / gx, 0);
+}
+
 // ---------------------------------------------------------------- calibration
 // One-time power-of-two prescale: after the first accepted spectra the largest
 // |re|, |im| is brought into [1, 2). Every metric is a ratio invariant to a common
@@ -138,15 +169,26 @@ __global__ void k_calibrate(SpectrumArgs a, int phase) {
     }
 }
 
-__global__ void k_commit(CommitArgs a) {
-    FcCtrl* c = a.ctrl;
+__device__ __forceinline__ void commit(FcCtrl* c, int count) {
     if (c->bad) {
-        c->rejected += a.count;
+        c->rejected += count;
         c->bad_latched = 1;
         c->bad = 0;
     } else {
-        c->pushed += a.count;
+        c->pushed += count;
     }
+}
+
+__global__ void k_commit(CommitArgs a) { commit(a.ctrl, a.count); }
+
+// One-trial commits of several sessions; each control block is then copied to the
+// session's host snapshot (prescale and rejection count for the host).
+__global__ void k_commit_batch(CommitBatch b) {
+    const int s = threadIdx.x;
+    if (s >= b.nsess) return;
+    FcCtrl* c = b.ctrl[s];
+    commit(c, 1);
+    if (b.snap[s]) *b.snap[s] = *c;
 }
 
 }  // namespace
@@ -173,6 +215,30 @@ cudaError_t launch_calibrate(const SpectrumArgs& a, cudaStream_t st, int phase) 
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
     k_calibrate<<<(unsigned)blocks, 256, 0, st>>>(a, phase);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_batch(const PreBatch& b, cudaStream_t st) {
+    if (b.nsess <= 0) return cudaSuccess;
+    long long most = 0;
+    for (int s = 0; s < b.nsess; ++s) most = std::max(most, b.val_prefix[s + 1] - b.val_prefix[s]);
+    long long blocks = (most + 255) / 256;
+    blocks = std::min(blocks, std::max(1LL, 152LL * 16 / b.nsess));
+    if (blocks < 1) blocks = 1;
+    k_validate_batch<<<dim3((unsigned)blocks, b.nsess), 256, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum_batch(const PreBatch& b, cudaStream_t st) {
+    const int ctas = b.nsess > 0 ? b.spec_prefix[b.nsess] : 0;
+    if (ctas <= 0) return cudaSuccess;
+    k_spectrum_batch<<<ctas, 256, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_commit_batch(const CommitBatch& b, cudaStream_t st) {
+    if (b.nsess <= 0) return cudaSuccess;
+    k_commit_batch<<<1, 32, 0, st>>>(b);
     return cudaGetLastError();
 }
 

@@ -88,23 +88,16 @@ __global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
                 for (int kk = 0; kk < kn; ++kk) {
                     const float ai = sa[kk][li], bi = sb[kk][li];
                     const bool ti = TINY && stiny[kk][li] != 0;
-                    const float2 bi2 = f2(bi), nbi2 = f2(-bi), ai2 = f2(ai), nai2 = f2(-ai);
+                    const float2 bi2 = f2(bi), ai2 = f2(ai), nai2 = f2(-ai);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int j = FC_T + lj0 + 2 * h;
                         const float2 aj = *reinterpret_cast<const float2*>(&sa[kk][j]);
                         const float2 bj = *reinterpret_cast<const float2*>(&sb[kk][j]);
                         // Im(X_i X_j*) and its exact sign, as in pair_terms2 (terms.cuh)
-                        const float2 p = mul2(bi2, aj), np = mul2(nbi2, aj);
-                        const float2 qq = mul2(ai2, bj), nq = mul2(nai2, bj);
-                        const float2 e = fma2(bi2, aj, np);
-                        const float2 nf = fma2(nai2, bj, qq);
-                        // scalar: an add that takes a raw packed product is never fused
-                        const float2 d1 = make_float2(__fadd_rn(p.x, nq.x), __fadd_rn(p.y, nq.y));
-                        const float2 d2 = add2(e, nf);
-                        float2 im = add2(d1, d2);
-                        int sg0 = sign_of(d1.x != 0.f ? d1.x : d2.x);
-                        int sg1 = sign_of(d1.y != 0.f ? d1.y : d2.y);
+                        float2 im = kahan_im2(bi2, ai2, nai2, aj, bj);
+                        int sg0 = sign_of(im.x);
+                        int sg1 = sign_of(im.y);
                         if (TINY) {
                             if (ti || stiny[kk][j]) im_sign_fp64(ai, bi, aj.x, bj.x, im.x, sg0);
                             if (ti || stiny[kk][j + 1]) im_sign_fp64(ai, bi, aj.y, bj.y, im.y, sg1);

@@ -229,12 +229,6 @@ __global__ void __launch_bounds__(256, 2) k_stream(const StreamBatch batch) {
                 }
                 int s0 = h ? sg.z : sg.x, s1 = h ? sg.w : sg.y;
                 if (upd) {
-                    const int* tn = reinterpret_cast<const int*>(Sn_c) + 4 * FC_T;
-                    const PairTerms2 n = pair_terms2(rn, *reinterpret_cast<const float2*>(Sn_c + j),
-                                                     *reinterpret_cast<const float2*>(Sn_c + FC_T + j),
-                                                     *reinterpret_cast<const float2*>(Sn_c + 2 * FC_T + j),
-                                                     *reinterpret_cast<const float2*>(Sn_c + 3 * FC_T + j),
-                                                     tn[j] != 0, tn[j + 1] != 0);
                     // leaving trial against its negated columns: exact negated terms
                     PairTerms2 o;
                     if (sub) {
@@ -248,6 +242,12 @@ __global__ void __launch_bounds__(256, 2) k_stream(const StreamBatch batch) {
                         o.re = o.im = o.ure = o.uim = make_float2(0.f, 0.f);
                         o.s0 = o.s1 = 0;
                     }
+                    const int* tn = reinterpret_cast<const int*>(Sn_c) + 4 * FC_T;
+                    const PairTerms2 n = pair_terms2(rn, *reinterpret_cast<const float2*>(Sn_c + j),
+                                                     *reinterpret_cast<const float2*>(Sn_c + FC_T + j),
+                                                     *reinterpret_cast<const float2*>(Sn_c + 2 * FC_T + j),
+                                                     *reinterpret_cast<const float2*>(Sn_c + 3 * FC_T + j),
+                                                     tn[j] != 0, tn[j + 1] != 0);
                     acc2_ff(vh[0], vl[0], n.re, o.re);
                     acc2_ff(vh[1], vl[1], n.im, o.im);
                     acc2_ff(vh[2], vl[2], n.ure, o.ure);

@@ -12,18 +12,21 @@
 // with explicit rounding intrinsics, so the subtracted value has exactly the bits that
 // were added. Every step is sign-symmetric, so the terms of (X_i, -X_j) are the exact
 // negations of those of (X_i, X_j): the streaming kernel subtracts a trial by staging
-// its column spectra negated. The scalar and the packed (two pairs per instruction)
-// forms perform the same correctly rounded operations lane by lane.
+// its column spectra negated. The packed form computes two pairs per instruction with
+// correctly rounded operations lane by lane.
 //
-// Exact sign of b_i a_j - a_i b_j from FP32 operands: p = fl(b_i a_j), q = fl(a_i b_j).
-// Rounding is monotone, so p > q implies b_i a_j > a_i b_j (and likewise for <). If
-// p == q the sign is that of e - f with e = b_i a_j - p and f = a_i b_j - q, both exact
-// FMA residuals; a rounded difference keeps the sign of the exact one. The residuals are
-// exact when both factors of each product are 0 or at least 2^-50 in magnitude (the
-// residual's last bit is then >= 2^-146, inside the subnormal range). A node with a
-// nonzero component below 2^-50 is flagged when its spectra are staged and its pairs
-// take an FP64 evaluation instead (FP32 x FP32 products are exact in FP64 and one
-// rounded subtraction keeps the sign).
+// Im = b_i a_j - a_i b_j by Kahan's 2x2 determinant algorithm: w = fl(a_i b_j),
+// e = w - a_i b_j (exact, one FMA), f = fl(b_i a_j - w) (one FMA), im = fl(f + e).
+// Jeannerod, Louvet and Muller (Math. Comp. 82, 2013) prove |im - Im| <= 2u |Im| without
+// underflow, so im is 0 exactly when Im is and otherwise has its sign: the sign counts are
+// exact. Directly: Im = F + e with F = b_i a_j - w; if |F| < ulp(w), F has at most 24
+// significant bits, so f = F and im = fl(Im); otherwise |e| <= ulp(w) / 2 <= |F| / 2, so
+// |Im| >= |F| / 2, far above the rounding error of f (<= u |F|). Both steps need exact residuals and no inexact subnormal result,
+// which holds when every factor is 0 or at least 2^-50 in magnitude (each product is then a
+// multiple of 2^-146, inside the subnormal grid). A node with a nonzero component below
+// 2^-50 is flagged when its spectra are staged and its pairs take an FP64 evaluation
+// instead (FP32 x FP32 products are exact in FP64 and one rounded subtraction keeps the
+// sign).
 #pragma once
 
 #include "df32.cuh"
@@ -49,6 +52,18 @@ __device__ __forceinline__ void im_sign_fp64(float ai, float bi, float aj, float
 
 __device__ __forceinline__ int sign_of(float t) { return (t > 0.f) - (t < 0.f); }
 
+// Packed Kahan determinant for two column nodes: Im(X_i X_j*) = b_i a_j - a_i b_j with
+// bi = (b_i, b_i), ai = (a_i, a_i), nai = (-a_i, -a_i). Every add takes FMA results, never a
+// raw product (a packed add of a packed product may be contracted into one FMA). Negating
+// the column spectra negates every intermediate exactly, so the terms of (X_i, -X_j) are
+// the exact negations of those of (X_i, X_j).
+__device__ __forceinline__ float2 kahan_im2(float2 bi, float2 ai, float2 nai, float2 aj, float2 bj) {
+    const float2 nw = mul2(nai, bj);              // -fl(a_i b_j)
+    const float2 f = fma2(bi, aj, nw);            // fl(b_i a_j - w)
+    const float2 me = fma2(ai, bj, nw);           // a_i b_j - w, exact
+    return fma2(me, make_float2(-1.f, -1.f), f);  // fl(f - me)
+}
+
 // The same FP64 evaluation kept out of line: a call is never if-converted, so a kernel that
 // cannot tell tiny nodes apart in advance pays for it only when a node is tiny.
 struct ImSign {
@@ -61,36 +76,9 @@ static __device__ __noinline__ ImSign im_sign_fp64_call(float ai, float bi, floa
     return v;
 }
 
-struct PairTerms {
-    float re;  // Re(X_i X_j*)
-    float im;  // Im(X_i X_j*), the correctly signed, nearly correctly rounded value
-    int sgn;   // sign(Im(X_i X_j*)) in {-1, 0, 1}, exact
-    float ure; // Re(u_i u_j*)
-    float uim; // Im(u_i u_j*)
-};
-
-// Scalar form; tiny = node_tiny(X_i) || node_tiny(X_j).
-__device__ __forceinline__ PairTerms pair_terms(float2 Xi, float2 Xj, float2 ui, float2 uj, bool tiny) {
-    PairTerms t;
-    const float ai = Xi.x, bi = Xi.y, aj = Xj.x, bj = Xj.y;
-    t.re = __fmaf_rn(ai, aj, __fmul_rn(bi, bj));
-    const float p = __fmul_rn(bi, aj), np = __fmul_rn(-bi, aj);
-    const float q = __fmul_rn(ai, bj), nq = __fmul_rn(-ai, bj);
-    const float e = __fmaf_rn(bi, aj, np);   // b_i a_j - p
-    const float nf = __fmaf_rn(-ai, bj, q);  // -(a_i b_j - q)
-    const float d1 = __fadd_rn(p, nq);       // fl(p - q)
-    const float d2 = __fadd_rn(e, nf);       // fl(e - f)
-    t.im = __fadd_rn(d1, d2);
-    t.sgn = sign_of(d1 != 0.f ? d1 : d2);
-    if (tiny) im_sign_fp64(ai, bi, aj, bj, t.im, t.sgn);
-    t.ure = __fmaf_rn(ui.x, uj.x, __fmul_rn(ui.y, uj.y));
-    t.uim = __fmaf_rn(ui.y, uj.x, __fmul_rn(-ui.x, uj.y));
-    return t;
-}
-
 // Row-node constants of the packed form (one node i against two column nodes).
 struct RowConst {
-    float2 a, b, na, nb, ua, ub, nua;
+    float2 a, b, na, ua, ub, nua;
     float as, bs;  // scalar a_i, b_i for the FP64 path
     bool tiny;
 };
@@ -99,7 +87,6 @@ __device__ __forceinline__ RowConst row_const(float a, float b, float ua, float 
     r.a = f2(a);
     r.b = f2(b);
     r.na = f2(-a);
-    r.nb = f2(-b);
     r.ua = f2(ua);
     r.ub = f2(ub);
     r.nua = f2(-ua);
@@ -122,18 +109,9 @@ __device__ __forceinline__ PairTerms2 pair_terms2(const RowConst& r, float2 aj, 
                                                   bool tiny0, bool tiny1) {
     PairTerms2 t;
     t.re = fma2(r.a, aj, mul2(r.b, bj));
-    const float2 p = mul2(r.b, aj), np = mul2(r.nb, aj);
-    const float2 q = mul2(r.a, bj), nq = mul2(r.na, bj);
-    const float2 e = fma2(r.b, aj, np);
-    const float2 nf = fma2(r.na, bj, q);
-    // fl(p) - fl(q) in scalar form: a packed add whose operand is a packed product can be
-    // fused by the backend into one FMA (which would drop the rounding of the product);
-    // the scalar round-to-nearest add is never contracted.
-    const float2 d1 = make_float2(__fadd_rn(p.x, nq.x), __fadd_rn(p.y, nq.y));
-    const float2 d2 = add2(e, nf);
-    t.im = add2(d1, d2);
-    t.s0 = sign_of(d1.x != 0.f ? d1.x : d2.x);
-    t.s1 = sign_of(d1.y != 0.f ? d1.y : d2.y);
+    t.im = kahan_im2(r.b, r.a, r.na, aj, bj);
+    t.s0 = sign_of(t.im.x);
+    t.s1 = sign_of(t.im.y);
     if (TINY && (r.tiny || tiny0)) {
         const ImSign v = im_sign_fp64_call(r.as, r.bs, aj.x, bj.x);
         t.im.x = v.im;

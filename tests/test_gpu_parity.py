@@ -266,6 +266,39 @@ def test_zero_and_identical_channels():
         _check_against_gpu_spectra(s, 5)
 
 
+@pytest.mark.parametrize("mode,prec", [("stream", "fp32"), ("full", "fp32"), ("full", "bf16")])
+def test_sign_exact_where_im_is_within_rounding_of_zero(mode, prec):
+    """Channels that are real multiples of others: Im(X_i X_j*) of their FP32 spectra is a
+    few ulps from zero (or exactly zero) with either sign, the hardest input for the exact
+    sign. Sign sums must equal the FP64 evaluation on the same spectra: per bin and signed
+    (streaming accumulators), per bin in magnitude (FP32 per-bin PLI), over the band (PLI)."""
+    n, N, K = 48, 200, 6
+    x = white_trials(11, K, n, N)
+    rng = np.random.default_rng(5)
+    c = rng.uniform(0.3, 3.0, 24) * rng.choice([-1.0, 1.0], 24)
+    x[:, 24:] = (x[:, :24].astype(np.float64) * c[None, :, None]).astype(np.float32)
+    kw = dict(mode=fc.FC_MODE_STREAM if mode == "stream" else fc.FC_MODE_FULL,
+              precision=fc.FC_PREC_FP32 if prec == "fp32" else fc.FC_PREC_BF16)
+    with _session(n, N, 200.0, (1.0, 60.0, 256), K, **kw) as s:
+        for k in range(K):
+            s.push(x[k])
+        X = window_spectra(s, K)
+        iu = np.triu_indices(n, 1)
+        sums = O.pair_sums_pairs(X, *iu)
+        copies = packed_index(np.arange(24), np.arange(24) + 24, n)
+        # the copies' products really are at the rounding level (and not all exactly zero)
+        rel = np.abs(np.imag(sums["csd"][copies])) / np.abs(sums["csd"][copies])
+        assert np.median(rel) < 1e-5 and np.any(sums["sign"][copies] != 0)
+        if mode == "stream":
+            sg = s.accumulators("sign").reshape(s.B, -1)
+            assert np.array_equal(sg.astype(np.int64), sums["sign"].T)
+        if prec == "fp32":  # per-bin values exist for FP32 sessions only
+            pli_b = s.network_bins("PLI").astype(np.float64)
+            assert np.array_equal(np.rint(pli_b * K).astype(np.int64), np.abs(sums["sign"]).T)
+        names = ("PLI", "USPLI", "WPLI", "DSWPLI") if prec == "bf16" else SPECTRAL
+        _check_against_gpu_spectra(s, K, names=names)
+
+
 def test_nonfinite_trial_is_rejected_and_state_kept():
     n, N, W = 34, 64, 3
     x = white_trials(8, 5, n, N)

@@ -159,6 +159,32 @@ __device__ __forceinline__ void acc2_d(float2& hi, float2& lo, float2 yh, float2
     fast_two_sum2(s, add2(add2(lo, e), yl), hi, lo);
 }
 
+// Lazy running sums for many terms in a row: hi takes the rounded sum, lo collects the exact
+// TwoSum errors (and the low parts of double-word terms) in FP32, with no renormalization
+// (7 ops for 2 lanes instead of 10). The identity hi + sum(errors) = sum(terms) is exact, so
+// after k terms hi + lo is off by at most about k^2 u^2 of the summed magnitudes (u = 2^-24,
+// the FP32 rounding of lo); renorm2 brings the pair back to a normalized double word.
+__device__ __forceinline__ void acc2_f_lazy(float2& hi, float2& lo, float2 y) {
+    float2 s, e;
+    two_sum2(hi, y, s, e);
+    hi = s;
+    lo = add2(lo, e);
+}
+
+__device__ __forceinline__ void acc2_d_lazy(float2& hi, float2& lo, float2 yh, float2 yl) {
+    float2 s, e;
+    two_sum2(hi, yh, s, e);
+    hi = s;
+    lo = add2(lo, add2(e, yl));
+}
+
+__device__ __forceinline__ void renorm2(float2& hi, float2& lo) {
+    float2 s, e;
+    two_sum2(hi, lo, s, e);
+    hi = s;
+    lo = e;
+}
+
 // Running-sum update (hi, lo) += y1 + y2 for two float terms: two TwoSums into the
 // leading part, their errors folded into lo, one renormalization (17 ops for 2 lanes).
 __device__ __forceinline__ void acc2_ff(float2& hi, float2& lo, float2 y1, float2 y2) {

@@ -64,7 +64,9 @@ constexpr int WK = 16;     // trials staged per chunk
 constexpr int NODE_W = 5;  // staged words per node: a, b, Re u, Im u, tiny flag
 
 // Thread: row node li of tile ta against columns lj0 .. lj0 + 3 of tile tb, as two packed
-// column pairs (FP32x2 lanes), double-float running sums per lane (acc2_f / acc2_d).
+// column pairs (FP32x2 lanes), double-float running sums per lane: lazy TwoSum updates
+// (acc2_f_lazy / acc2_d_lazy) renormalized after every chunk of WK trials, which keeps the
+// error of a sum of K terms within about (WK + 1) K u^2 of their summed magnitudes.
 __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, float* bins_out) {
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
@@ -141,20 +143,25 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
                                                          *reinterpret_cast<const float2*>(&cl[2][j]),
                                                          *reinterpret_cast<const float2*>(&cl[3][j]), tj.x != 0.f,
                                                          tj.y != 0.f);
-                        acc2_f(vh[h][0], vl[h][0], t.re);
-                        acc2_f(vh[h][1], vl[h][1], t.im);
-                        acc2_f(vh[h][2], vl[h][2], t.ure);
-                        acc2_f(vh[h][3], vl[h][3], t.uim);
-                        acc2_f(vh[h][4], vl[h][4], make_float2(fabsf(t.im.x), fabsf(t.im.y)));
+                        acc2_f_lazy(vh[h][0], vl[h][0], t.re);
+                        acc2_f_lazy(vh[h][1], vl[h][1], t.im);
+                        acc2_f_lazy(vh[h][2], vl[h][2], t.ure);
+                        acc2_f_lazy(vh[h][3], vl[h][3], t.uim);
+                        acc2_f_lazy(vh[h][4], vl[h][4], make_float2(fabsf(t.im.x), fabsf(t.im.y)));
                         // im^2 as an exact two-product, scalar: the product feeds additions
                         float2 p2, e2;
                         two_prod(t.im.x, t.im.x, p2.x, e2.x);
                         two_prod(t.im.y, t.im.y, p2.y, e2.y);
-                        acc2_d(vh[h][5], vl[h][5], p2, e2);
+                        acc2_d_lazy(vh[h][5], vl[h][5], p2, e2);
                         s[2 * h] += t.s0;
                         s[2 * h + 1] += t.s1;
                     }
                 }
+                // back to normalized double words once per chunk of WK terms
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int k = 0; k < FC_NFIELD; ++k) renorm2(vh[h][k], vl[h][k]);
             };
             if (vmask) {
                 if (chunk_tiny)

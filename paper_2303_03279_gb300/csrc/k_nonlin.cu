@@ -80,15 +80,16 @@ __global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
             const bool chunk_tiny = __syncthreads_or(any_tiny ? 1 : 0) != 0;
             if (!vmask) continue;
             // FP32 partial sums of this chunk, two column pairs per packed lane pair
-            float2 p_im[2], p_sq[2], p_abs[2], p_sqe[2];
+            float2 p_im[2], p_sq[2], p_abs[2], p_sqe[2], p_pos[2], p_neg[2];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) p_im[h] = p_sq[h] = p_abs[h] = p_sqe[h] = make_float2(0.f, 0.f);
+            for (int h = 0; h < 2; ++h)
+                p_im[h] = p_sq[h] = p_abs[h] = p_sqe[h] = p_pos[h] = p_neg[h] = make_float2(0.f, 0.f);
             auto chunk = [&](auto tiny_c) {
                 constexpr bool TINY = decltype(tiny_c)::value;
                 for (int kk = 0; kk < kn; ++kk) {
                     const float ai = sa[kk][li], bi = sb[kk][li];
-                    const bool ti = TINY && stiny[kk][li] != 0;
                     const float2 bi2 = f2(bi), ai2 = f2(ai), nai2 = f2(-ai);
+                    const bool ti = TINY && stiny[kk][li] != 0;
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int j = FC_T + lj0 + 2 * h;
@@ -96,14 +97,17 @@ __global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
                         const float2 bj = *reinterpret_cast<const float2*>(&sb[kk][j]);
                         // Im(X_i X_j*) and its exact sign, as in pair_terms2 (terms.cuh)
                         float2 im = kahan_im2(bi2, ai2, nai2, aj, bj);
-                        int sg0 = sign_of(im.x);
-                        int sg1 = sign_of(im.y);
                         if (TINY) {
+                            int sg0 = sign_of(im.x), sg1 = sign_of(im.y);
                             if (ti || stiny[kk][j]) im_sign_fp64(ai, bi, aj.x, bj.x, im.x, sg0);
                             if (ti || stiny[kk][j + 1]) im_sign_fp64(ai, bi, aj.y, bj.y, im.y, sg1);
+                            s_sg[2 * h] += sg0;
+                            s_sg[2 * h + 1] += sg1;
+                        } else {
+                            // sign tallies as exact small FP32 counts (at most NK per chunk)
+                            p_pos[h] = add2(p_pos[h], make_float2(im.x > 0.f ? 1.f : 0.f, im.y > 0.f ? 1.f : 0.f));
+                            p_neg[h] = add2(p_neg[h], make_float2(im.x < 0.f ? 1.f : 0.f, im.y < 0.f ? 1.f : 0.f));
                         }
-                        s_sg[2 * h] += sg0;
-                        s_sg[2 * h + 1] += sg1;
                         p_abs[h] = make_float2(__fadd_rn(p_abs[h].x, fabsf(im.x)), __fadd_rn(p_abs[h].y, fabsf(im.y)));
                         p_im[h] = add2(p_im[h], im);
                         // im^2 as an exact two-product (t + r), scalar: the products feed additions;
@@ -126,6 +130,9 @@ __global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
                 const float psq = (q & 1) ? p_sq[q >> 1].y : p_sq[q >> 1].x;
                 const float pse = (q & 1) ? p_sqe[q >> 1].y : p_sqe[q >> 1].x;
                 const float pab = (q & 1) ? p_abs[q >> 1].y : p_abs[q >> 1].x;
+                const float pps = (q & 1) ? p_pos[q >> 1].y : p_pos[q >> 1].x;
+                const float png = (q & 1) ? p_neg[q >> 1].y : p_neg[q >> 1].x;
+                s_sg[q] += (int)pps - (int)png;
                 s_im[q] = df_add_f(s_im[q], pim);
                 s_sq[q] = df_add_f(df_add_f(s_sq[q], psq), pse);
                 s_abs[q] = df_add_f(s_abs[q], pab);

@@ -33,9 +33,10 @@ constexpr int CHUNK_BYTES = 16384;     // 128 rows x 128 bytes of K
 constexpr int PHASE_OPS = 3;           // operand blocks per chunk of one phase (see k_herk_tc)
 constexpr int STAGE_BYTES = PHASE_OPS * CHUNK_BYTES;
 constexpr int NSTAGE = 4;              // chunk stages in flight
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 512 + 4 * 512;  // + barriers, TMEM address, 4 x 1/sqrt(PSD) rows
+constexpr int EPI_WARPS = 8;           // epilogue warps: lane quarter w % 4, row nodes 64 (w / 4) ..
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 512 + EPI_WARPS * 512;  // + barriers, TMEM address, 1/sqrt(PSD) rows per epilogue warp
 constexpr uint32_t TMEM_COLS = 512;    // 2 phase buffers x 2 accumulators x 128 FP32 columns
-constexpr int THREADS = 160;           // warps 0-3: epilogue (TMEM lanes 32w..32w+31); warp 4: loads + MMAs
+constexpr int THREADS = 32 * EPI_WARPS + 32;  // warps 0-7: epilogue; warp 8: loads + MMAs
 
 // Shared-memory matrix descriptor: K-major, no swizzle; LBO = 128 B (next core matrix
 // along K), SBO = 1024 B (next 8-row group), descriptor version 1.
@@ -101,9 +102,10 @@ __device__ __forceinline__ const unsigned char* op_block(const HerkArgs& a, int 
 //   phase A (CSD):     Re = XR_b XR_a^T,  Im = XR_b XI_a^T   -> COH, IMAGCOHY
 //   phase B (phasors): Re = UR_b UR_a^T,  Im = UR_b UI_a^T   -> PLV
 // Phase p accumulates in TMEM columns [256 p, 256 p + 256), so the epilogue of one phase
-// runs while the tensor cores work on the next (warp-specialized: warp 4 lane 0 streams
+// runs while the tensor cores work on the next (warp-specialized: warp 8 lane 0 streams
 // the operand chunks of the CTA's phase sequence through NSTAGE shared-memory stages and
-// issues the MMAs; warps 0-3 drain TMEM). Every wait is bounded; a timeout is recorded in
+// issues the MMAs; warps 0-7 drain TMEM, two per lane quarter, each over half of the row
+// nodes). Every wait is bounded; a timeout is recorded in
 // the control block.
 template <int KIND>
 __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
     uint64_t* acce = accf + 2;                                                   // [2] epilogue -> MMAs
     uint64_t* drain = acce + 2;                                                  // [1]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
-    float* sinv_all = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES + 512);  // [4][128] per epilogue warp
+    float* sinv_all = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES + 512);  // [EPI_WARPS][128]
     const int tid = threadIdx.x, warp = tid >> 5;
 
     if (warp == 0) {
@@ -134,8 +136,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
         }
         mbar_init(&accf[0], 1);
         mbar_init(&accf[1], 1);
-        mbar_init(&acce[0], 4);  // one arrival per epilogue warp
-        mbar_init(&acce[1], 4);
+        mbar_init(&acce[0], EPI_WARPS);  // one arrival per epilogue warp
+        mbar_init(&acce[1], EPI_WARPS);
         mbar_init(drain, 1);
         fence_mbar_init();
     }
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
     const int nphase = 2 * my_units;
     bool failed = false;
 
-    if (warp == 4) {
+    if (warp == EPI_WARPS) {
         // ---------------------------------------------------------- loads + MMAs
         if ((tid & 31) == 0) {
             const uint32_t idesc = make_idesc(KIND == 1 ? 2u : (a.ab_format == 1 ? 1u : 0u), TILE, TILE);
@@ -229,20 +231,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
             }
         }
     } else {
-        // ---------------------------------------------------------- epilogue (warps 0-3)
+        // ---------------------------------------------------------- epilogue (warps 0-7)
         uint32_t accf_ph[2] = {0, 0};
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        const int quarter = warp & 3, rhalf = warp >> 2;  // TMEM lanes 32 quarter ..; rows 64 rhalf ..
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         float* sinv = sinv_all + warp * TILE;  // this warp's copy: no barrier across warps
         for (int ph = 0; ph < nphase; ++ph) {
             const int b = ph & 1;
             const int u = (int)blockIdx.x + (ph >> 1) * (int)gridDim.x;
             const int tp = u / a.B, f = u % a.B;
             const int ta = a.tile_a[tp], tb = a.tile_b[tp];
-            const int j = tb * TILE + tid;  // this thread's TMEM lane: column node j
+            const int j = tb * TILE + quarter * 32 + (tid & 31);  // this thread's TMEM lane: column node j
             if (b == 0) {  // 1/sqrt(PSD) of tile a's nodes, staged by this warp for itself
                 __syncwarp();
-#pragma unroll
-                for (int r = 0; r < TILE / 32; ++r) {
+                for (int r = 2 * rhalf; r < 2 * rhalf + 2; ++r) {  // the rows this warp reads
                     const int i = ta * TILE + r * 32 + (tid & 31);
                     sinv[r * 32 + (tid & 31)] = i < a.n ? a.inv_psd[(size_t)f * a.n + i] : 0.f;
                 }
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
             const uint32_t col = (uint32_t)(b * 2 * TILE);
             const float inv_j = (b == 0 && j < a.n) ? a.inv_psd[(size_t)f * a.n + j] : 0.f;
             float* out = a.bins_out + (size_t)f * 3 * a.P;
-            for (int i0 = 0; i0 < TILE; i0 += 16) {
+            for (int i0 = rhalf * (TILE / 2); i0 < (rhalf + 1) * (TILE / 2); i0 += 16) {
                 float vre[16], vim[16];
                 tmem_ld16(lane_base + col + i0, vre);
                 tmem_ld16(lane_base + col + TILE + i0, vim);

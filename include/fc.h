@@ -161,6 +161,23 @@ fc_status fc_push_trials(fc_session* s, const float* x, int count, int x_on_devi
 fc_status fc_get_network(fc_session* s, uint32_t metric, int packed_upper, float* out,
                          size_t out_len, int out_on_device, int* k_used);
 
+/* Start reading one metric's packed band-averaged network out[P] (the values after every
+ * push enqueued so far) into host memory and return without waiting. The plane is first
+ * copied on the device (4 P bytes at device bandwidth, on the session's stream), then moved
+ * to `out` on a separate copy stream, so the transfer overlaps the pushes that follow.
+ * Single host trials pushed with fc_push_trial are likewise copied in on their own stream
+ * into alternating device buffers, so a loop of push, read-async, wait-for-the-previous
+ * keeps the compute stream busy. `out` must stay valid until fc_network_wait returns for
+ * it and should be page-locked (pinned) for the copy to overlap. At most two reads are in
+ * flight: starting a third first waits for the oldest. Rejected trials are reported by the
+ * synchronizing calls (fc_sync, fc_get_network), not here.
+ * Errors: FC_ERR_NOT_READY before the first push, FC_ERR_INVALID_ARG, FC_ERR_CUDA. */
+fc_status fc_get_network_async(fc_session* s, uint32_t metric, float* out, size_t out_len);
+
+/* Wait until the oldest read started by fc_get_network_async has landed in host memory
+ * (FC_OK at once when none is in flight). */
+fc_status fc_network_wait(fc_session* s);
+
 /* Per-bin values of one spectral metric, out[n_bins][P] (packed upper per bin). */
 /* Post-processing of the current band-averaged network of one metric, as the paper
  * presents its networks (Results 3.1.2, 3.2.2: normalized by the maximum edge weight;

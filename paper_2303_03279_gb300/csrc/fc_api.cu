@@ -406,6 +406,17 @@ fc_status push_bulk(fc_session* s, const float* x, int count, bool write_acc) {
     return FC_OK;
 }
 
+// Streams and events of the pipelined host I/O, created on first use.
+fc_status ensure_io(fc_session* s) {
+    if (s->in_stream) return FC_OK;
+    CK(cudaStreamCreateWithFlags(&s->in_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&s->out_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b)
+        for (cudaEvent_t* e : {&s->ev_in[b], &s->ev_used[b], &s->ev_snap[b], &s->ev_out[b]})
+            CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return FC_OK;
+}
+
 fc_status ensure_stage(fc_session* s, int count) {
     if (count <= s->stage_trials) return FC_OK;
     void* p;
@@ -735,6 +746,8 @@ fc_status fc_session_destroy(fc_session* s) {
     if (!s) return FC_OK;
     cudaSetDevice(s->device);
     cudaStreamSynchronize(s->stream);
+    if (s->in_stream) cudaStreamSynchronize(s->in_stream);
+    if (s->out_stream) cudaStreamSynchronize(s->out_stream);
     drain_timings(s);
     free_all(s);
     if (s->own_stream) cudaStreamDestroy(s->stream);
@@ -743,6 +756,14 @@ fc_status fc_session_destroy(fc_session* s) {
     if (s->proj) cudaFree(s->proj);
     if (s->proj_in) cudaFree(s->proj_in);
     if (s->cor_part) cudaFree(s->cor_part);
+    for (int b = 0; b < 2; ++b) {
+        if (s->x_in[b]) cudaFree(s->x_in[b]);
+        if (s->snap[b]) cudaFree(s->snap[b]);
+        for (cudaEvent_t e : {s->ev_in[b], s->ev_used[b], s->ev_snap[b], s->ev_out[b]})
+            if (e) cudaEventDestroy(e);
+    }
+    if (s->in_stream) cudaStreamDestroy(s->in_stream);
+    if (s->out_stream) cudaStreamDestroy(s->out_stream);
     delete s;
     return FC_OK;
 }
@@ -773,6 +794,23 @@ fc_status fc_push_trials(fc_session* s, const float* x, int count, int x_on_devi
         if (st != FC_OK) return st;
         LAUNCH(FC_K_PROJECT, launch_project(s->proj, xin, s->x_stage, s->n, s->proj_C, s->N, count, s->stream));
         xd = s->x_stage;
+    } else if (!x_on_device && count == 1) {
+        // one host trial: copied on the input stream into the buffer the push before last
+        // used, while the compute stream may still be busy with the previous push
+        fc_status st = ensure_io(s);
+        if (st != FC_OK) return st;
+        const int b = s->in_flip;
+        s->in_flip ^= 1;
+        if (!s->x_in[b]) CK(cudaMalloc(&s->x_in[b], per * sizeof(float)));
+        if (s->used_valid[b]) CK(cudaStreamWaitEvent(s->in_stream, s->ev_used[b], 0));
+        CK(cudaMemcpyAsync(s->x_in[b], x, per * sizeof(float), cudaMemcpyHostToDevice, s->in_stream));
+        CK(cudaEventRecord(s->ev_in[b], s->in_stream));
+        CK(cudaStreamWaitEvent(s->stream, s->ev_in[b], 0));
+        st = s->cfg.mode == FC_MODE_FULL ? push_bulk(s, s->x_in[b], 1, false) : push_one_stream(s, s->x_in[b], true);
+        if (st != FC_OK) return st;
+        CK(cudaEventRecord(s->ev_used[b], s->stream));
+        s->used_valid[b] = true;
+        return FC_OK;
     } else if (!x_on_device) {
         fc_status st = ensure_stage(s, count);
         if (st != FC_OK) return st;
@@ -837,6 +875,43 @@ fc_status fc_get_network(fc_session* s, uint32_t metric, int packed_upper, float
         if (!out_on_device) CK(cudaMemcpyAsync(out, dst, need * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
     }
     if (!out_on_device) CK(cudaStreamSynchronize(s->stream));
+    return FC_OK;
+}
+
+fc_status fc_get_network_async(fc_session* s, uint32_t metric, float* out, size_t out_len) {
+    if (!s || !out) return fail(FC_ERR_INVALID_ARG, "NULL session or output");
+    const int mi = metric_index(metric);
+    if (mi < 0) return fail(FC_ERR_INVALID_ARG, "metric must be a single FC_* bit");
+    if (!(s->mask & metric)) return fail(FC_ERR_INVALID_ARG, "metric 0x%x is not in the session mask", metric);
+    if (out_len < (size_t)s->P) return fail(FC_ERR_INVALID_ARG, "out_len %zu < %lld", out_len, (long long)s->P);
+    CK(cudaSetDevice(s->device));
+    if (s->enqueued == 0) return fail(FC_ERR_NOT_READY, "no trial has been pushed");
+    fc_status st = ensure_io(s);
+    if (st != FC_OK) return st;
+    if (s->out_count == 2) {
+        st = fc_network_wait(s);
+        if (st != FC_OK) return st;
+    }
+    const int b = s->out_head;
+    const size_t bytes = (size_t)s->P * sizeof(float);
+    if (!s->snap[b]) CK(cudaMalloc(&s->snap[b], bytes));
+    CK(cudaMemcpyAsync(s->snap[b], s->net + (size_t)mi * s->P, bytes, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaEventRecord(s->ev_snap[b], s->stream));
+    CK(cudaStreamWaitEvent(s->out_stream, s->ev_snap[b], 0));
+    CK(cudaMemcpyAsync(out, s->snap[b], bytes, cudaMemcpyDeviceToHost, s->out_stream));
+    CK(cudaEventRecord(s->ev_out[b], s->out_stream));
+    s->out_head ^= 1;
+    s->out_count += 1;
+    return FC_OK;
+}
+
+fc_status fc_network_wait(fc_session* s) {
+    if (!s) return fail(FC_ERR_INVALID_ARG, "NULL session");
+    if (s->out_count == 0) return FC_OK;
+    CK(cudaSetDevice(s->device));
+    const int oldest = (s->out_head + 2 - s->out_count) & 1;
+    CK(cudaEventSynchronize(s->ev_out[oldest]));
+    s->out_count -= 1;
     return FC_OK;
 }
 

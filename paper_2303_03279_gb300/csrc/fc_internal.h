@@ -134,6 +134,20 @@ struct fc_session {
     fc_kernel_time ktime[FC_K_COUNT];
     std::vector<void*> allocations;
     std::vector<std::pair<void*, size_t>> state_bufs;  // persistent state, in allocation order
+
+    // pipelined host I/O (created on first use): single host trials are copied in on
+    // in_stream into alternating buffers; async network reads leave on out_stream from a
+    // device snapshot of the plane
+    cudaStream_t in_stream = nullptr, out_stream = nullptr;
+    float* x_in[2] = {nullptr, nullptr};
+    cudaEvent_t ev_in[2] = {nullptr, nullptr};    // the copy into x_in[b] has landed
+    cudaEvent_t ev_used[2] = {nullptr, nullptr};  // the push that read x_in[b] is done
+    bool used_valid[2] = {false, false};
+    int in_flip = 0;
+    float* snap[2] = {nullptr, nullptr};          // [P] each
+    cudaEvent_t ev_snap[2] = {nullptr, nullptr};  // snapshot b taken (compute stream)
+    cudaEvent_t ev_out[2] = {nullptr, nullptr};   // snapshot b landed in host memory
+    int out_head = 0, out_count = 0;
 };
 
 // ---------------------------------------------------------------------------------

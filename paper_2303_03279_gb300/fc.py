@@ -108,6 +108,8 @@ _SIGNATURES = [
     ("fc_push_trials", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     ("fc_get_network", C.c_int, [C.c_void_p, C.c_uint32, C.c_int, C.c_void_p, C.c_size_t, C.c_int,
                                  C.POINTER(C.c_int)]),
+    ("fc_get_network_async", C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_size_t]),
+    ("fc_network_wait", C.c_int, [C.c_void_p]),
     ("fc_get_network_bins", C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_size_t, C.c_int]),
     ("fc_get_network_top", C.c_int, [C.c_void_p, C.c_uint32, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_int, C.POINTER(fc_top_info)]),
@@ -238,6 +240,19 @@ def fc_get_network(s, metric: int, packed_upper: int, out) -> int:
     k = C.c_int(0)
     _check(_LIB.fc_get_network(s, int(metric), int(packed_upper), p, nel, dev, C.byref(k) if not dev else None))
     return k.value
+
+
+def fc_get_network_async(s, metric: int, out):
+    """Start reading the packed network into host memory `out` (numpy; pinned memory lets
+    the copy overlap later pushes); fc_network_wait waits for the oldest read."""
+    p, dev, nel = _ptr(out, np.float32)
+    if dev:
+        raise ValueError("fc_get_network_async reads into host memory")
+    _check(_LIB.fc_get_network_async(s, int(metric), p, nel))
+
+
+def fc_network_wait(s):
+    _check(_LIB.fc_network_wait(s))
 
 
 def fc_get_network_bins(s, metric: int, out):

@@ -131,7 +131,10 @@ fc_status fc_config_default(fc_config* cfg);
 /* Create a session (Methods 2.4/2.5 settings: nodes, samples, sampling rate, band, taper,
  * metrics, number of trials to average).
  *   n_nodes >= 2, 1 <= n_samples <= band.nfft, fs > 0, the band selects >= 1 bin;
- *   metric_mask: nonzero subset of FC_ALL_METRICS;
+ *   metric_mask: nonzero subset of FC_ALL_METRICS; the state of a family is allocated
+ *     only when the mask holds one of its metrics (spectral: spectra ring and pair sums;
+ *     COR: normalized-trial ring and its split-TF32 operand ring; XCOR: spectra ring and
+ *     per-trial values), and only those metrics are computed per push;
  *   window: W >= 0 trials (0 = cumulative; FC_MODE_FULL needs W >= 1);
  *   cfg: NULL for defaults. *out receives the handle; on failure *out is NULL and nothing
  *   stays allocated. Errors: FC_ERR_INVALID_ARG, FC_ERR_OUT_OF_MEMORY, FC_ERR_CUDA. */
@@ -240,7 +243,8 @@ fc_status fc_get_xcor_lags(fc_session* s, int32_t* out, size_t out_len, int out_
 
 /* Switch the set of finalized metrics (Results 3.2.3: metrics switched on the fly). The
  * accumulators are shared, so a switch recomputes only the networks. Time-domain bits
- * (COR, XCOR) can only be kept or removed, not added after creation. */
+ * (COR, XCOR) can only be kept or removed, not added after creation; spectral bits cannot
+ * be added to a session created without any (it holds no spectra or pair sums). */
 fc_status fc_set_metric_mask(fc_session* s, uint32_t metric_mask);
 
 /* Wait for the session's stream; reports a pending FC_ERR_NONFINITE. */

@@ -246,12 +246,33 @@ fc_status stage_spectra(fc_session* s, const float* x, int count, int write_from
 
 fc_status stage_time_metrics(fc_session* s, const float* x, int count, int write_from, int mode) {
     if (s->time_mask & FC_COR) {
+        // normalized trials -> split-TF32 operand ring -> per-trial Gram products on the
+        // tensor cores, added to (mode 0: and the leaving trial's subtracted from) the sums
         CorArgs ca = cor_args(s, x, count, write_from, mode);
+        CorTcArgs ta{};
+        ta.zring = s->zring;
+        ta.ops = s->cor_ops;
+        ta.n = s->n;
+        ta.N = s->N;
+        ta.nt = s->cor_nt;
+        ta.ntp = s->cor_ntp;
+        ta.nchunks = s->cor_nchunks;
+        ta.slots = s->slots;
+        ta.W = s->W;
+        ta.P = s->P;
+        ta.count = count;
+        ta.write_from = write_from;
+        ta.mode = mode;
+        ta.groups = 1;
+        ta.cor_acc = s->cor_acc;
+        ta.net = ca.net;
+        ta.finalize = ca.finalize;
+        ta.grid_ctas = s->num_sms;
+        ta.ctrl = s->ctrl;
         if (mode == 1) {
             // few tile pairs: split the window's trials over several CTAs per tile pair
-            const int nt = (s->n + 63) / 64, ntp_cor = nt * (nt + 1) / 2;
             const long long k_est = s->W > 0 ? std::min<long long>(s->W, s->enqueued + count) : s->enqueued + count;
-            const int G = (int)std::max<long long>(1, std::min<long long>({(2LL * s->num_sms + ntp_cor - 1) / ntp_cor,
+            const int G = (int)std::max<long long>(1, std::min<long long>({(s->num_sms + s->cor_ntp - 1) / s->cor_ntp,
                                                                           k_est, 64}));
             if (G > 1) {
                 const size_t need = (size_t)G * 2 * s->P;
@@ -262,13 +283,14 @@ fc_status stage_time_metrics(fc_session* s, const float* x, int count, int write
                     CK(cudaMalloc(&s->cor_part, need * sizeof(float)));
                     s->cor_part_len = need;
                 }
-                ca.groups = G;
-                ca.part = s->cor_part;
+                ca.groups = ta.groups = G;
+                ca.part = ta.part = s->cor_part;
             }
         }
         LAUNCH(FC_K_COR, launch_cor_normalize(ca, s->stream));
-        LAUNCH(FC_K_COR, launch_cor_update(ca, s->stream));
-        if (ca.groups > 1) LAUNCH(FC_K_COR, launch_cor_combine(ca, s->stream));
+        LAUNCH(FC_K_COR, launch_cor_tc_pack(ta, s->stream));
+        LAUNCH(FC_K_COR, launch_cor_tc(ta, s->stream));
+        if (ta.groups > 1) LAUNCH(FC_K_COR, launch_cor_combine(ca, s->stream));
     }
     if (s->time_mask & FC_XCOR) {
         XcorArgs xa = xcor_args(s, x, count, write_from, mode);
@@ -370,16 +392,19 @@ fc_status stage_resum_slice(fc_session* s) {
 fc_status push_one_stream(fc_session* s, const float* x, bool finalize) {
     const long long nx = (long long)s->n * s->N;
     LAUNCH(FC_K_OTHER, launch_validate(x, nx, s->ctrl, s->stream));
-    fc_status st = stage_spectra(s, x, 1, 0);
-    if (st != FC_OK) return st;
-    NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, push_node_mode(s), s->ctrl, 1};
-    LAUNCH(FC_K_NODE, launch_node(na, s->stream));
-    PairArgs pa = pair_args(s, true, 1);
-    pa.finalize = (finalize && (s->mask & FC_SPECTRAL_METRICS)) ? 1 : 0;
-    LAUNCH(FC_K_STREAM, launch_stream_update(pa, s->stream));
-    if (pa.finalize && pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
-    st = stage_resum_slice(s);
-    if (st != FC_OK) return st;
+    fc_status st;
+    if (s->spectral) {
+        st = stage_spectra(s, x, 1, 0);
+        if (st != FC_OK) return st;
+        NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, push_node_mode(s), s->ctrl, 1};
+        LAUNCH(FC_K_NODE, launch_node(na, s->stream));
+        PairArgs pa = pair_args(s, true, 1);
+        pa.finalize = (finalize && (s->mask & FC_SPECTRAL_METRICS)) ? 1 : 0;
+        LAUNCH(FC_K_STREAM, launch_stream_update(pa, s->stream));
+        if (pa.finalize && pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
+        st = stage_resum_slice(s);
+        if (st != FC_OK) return st;
+    }
     st = stage_time_metrics(s, x, 1, 0, 0);
     if (st != FC_OK) return st;
     CommitArgs ca{s->ctrl, 1};
@@ -394,10 +419,13 @@ fc_status push_bulk(fc_session* s, const float* x, int count, bool write_acc) {
     LAUNCH(FC_K_OTHER, launch_validate(x, nx * count, s->ctrl, s->stream));
     const int keep = s->W > 0 ? std::min(count, s->W) : count;
     const int write_from = count - keep;
-    fc_status st = stage_spectra(s, x, count, write_from);
-    if (st != FC_OK) return st;
-    st = stage_window(s, count, write_acc);
-    if (st != FC_OK) return st;
+    fc_status st;
+    if (s->spectral) {
+        st = stage_spectra(s, x, count, write_from);
+        if (st != FC_OK) return st;
+        st = stage_window(s, count, write_acc);
+        if (st != FC_OK) return st;
+    }
     st = stage_time_metrics(s, x, count, write_from, 1);
     if (st != FC_OK) return st;
     CommitArgs ca{s->ctrl, count};
@@ -414,6 +442,14 @@ fc_status ensure_io(fc_session* s) {
     for (int b = 0; b < 2; ++b)
         for (cudaEvent_t* e : {&s->ev_in[b], &s->ev_used[b], &s->ev_snap[b], &s->ev_out[b]})
             CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return FC_OK;
+}
+
+// Host -> device copy ordered on the session stream, complete on return (the host buffer
+// may be pageable and temporary).
+fc_status upload(fc_session* s, void* dst, const void* src, size_t bytes) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
     return FC_OK;
 }
 
@@ -520,12 +556,15 @@ size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode 
     const size_t nt = (n + FC_T - 1) / FC_T, ntp = nt * (nt + 1) / 2;
     const size_t P = (size_t)n * (n - 1) / 2;
     const size_t slots = mode == FC_MODE_FULL ? W : (W > 0 ? W + 1 : 1);
-    size_t b = 256 + (size_t)N * B * 8 + slots * B * n * 8 + (size_t)B * n * 12 + ntp * 4 + 9 * P * 4 +
-               (size_t)n * N * 4;
-    if (mode == FC_MODE_STREAM) b += ntp * B * FC_BLOCK_WORDS * 4;
-    const int groups = std::min(B, std::max(1, (int)((152 * 4 + ntp - 1) / ntp)));
-    if (groups > 1) b += (size_t)groups * 7 * P * 4;
-    if (mask & FC_COR) b += slots * n * N * 4 + 2 * P * 4;
+    size_t b = 256 + 9 * P * 4 + (size_t)n * N * 4;  // control block, network planes, trial staging
+    if (mask & FC_SPECTRAL_METRICS) {
+        b += (size_t)N * B * 8 + slots * B * n * 8 + (size_t)B * n * 12 + ntp * 4;
+        if (mode == FC_MODE_STREAM) b += ntp * B * FC_BLOCK_WORDS * 4;
+        const int groups = std::min(B, std::max(1, (int)((152 * 4 + ntp - 1) / ntp)));
+        if (groups > 1) b += (size_t)groups * 7 * P * 4;
+    }
+    if (mask & FC_COR)
+        b += slots * n * N * 4 + 2 * P * 4 + slots * ((n + 127) / 128) * ((N + 31) / 32) * 32768;
     if (mask & FC_XCOR) {
         size_t L = 1;
         while (L < (size_t)(2 * N - 1)) L *= 2;
@@ -617,6 +656,7 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
     s->taper = taper;
     s->mask = metric_mask;
     s->time_mask = metric_mask & (FC_COR | FC_XCOR);
+    s->spectral = (metric_mask & FC_SPECTRAL_METRICS) != 0;
     s->cfg = cfg;
     s->nt = (n_nodes + FC_T - 1) / FC_T;
     s->ntp = s->nt * (s->nt + 1) / 2;
@@ -655,64 +695,73 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
     fc_status st;
 #define TRY(x) do { st = (x); if (st != FC_OK) return cleanup(st); } while (0)
     TRY(alloc_zero(s, 1, &s->ctrl));
-    // taper-folded DFT factors, FP64 on the host with exact angle reduction
-    {
-        std::vector<float2> tw((size_t)n_samples * B);
-        for (int t = 0; t < n_samples; ++t) {
-            double w = 1.0;
-            if (taper == FC_TAPER_HANN) w = 0.5 - 0.5 * std::cos(2.0 * kPi * t / n_samples);
-            if (taper == FC_TAPER_HANN_SYM) w = n_samples > 1 ? 0.5 - 0.5 * std::cos(2.0 * kPi * t / (n_samples - 1)) : 1.0;
-            for (int b = 0; b < B; ++b) {
-                const long long m = ((long long)(first + b) * t) % band.nfft;
-                const double ang = 2.0 * kPi * (double)m / band.nfft;
-                tw[(size_t)t * B + b] = make_float2((float)(w * std::cos(ang)), (float)(-w * std::sin(ang)));
+    // spectral state only when the session has spectral metrics (a COR / XCOR session holds none)
+    if (s->spectral) {
+        // taper-folded DFT factors, FP64 on the host with exact angle reduction
+        {
+            std::vector<float2> tw((size_t)n_samples * B);
+            for (int t = 0; t < n_samples; ++t) {
+                double w = 1.0;
+                if (taper == FC_TAPER_HANN) w = 0.5 - 0.5 * std::cos(2.0 * kPi * t / n_samples);
+                if (taper == FC_TAPER_HANN_SYM) w = n_samples > 1 ? 0.5 - 0.5 * std::cos(2.0 * kPi * t / (n_samples - 1)) : 1.0;
+                for (int b = 0; b < B; ++b) {
+                    const long long m = ((long long)(first + b) * t) % band.nfft;
+                    const double ang = 2.0 * kPi * (double)m / band.nfft;
+                    tw[(size_t)t * B + b] = make_float2((float)(w * std::cos(ang)), (float)(-w * std::sin(ang)));
+                }
             }
+            TRY(alloc_zero(s, tw.size(), &s->twiddle));
+            cudaError_t e = cudaMemcpyAsync(s->twiddle, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, s->stream);
+            if (e != cudaSuccess) return cleanup(fail(FC_ERR_CUDA, "twiddle upload: %s", cudaGetErrorString(e)));
+            cudaStreamSynchronize(s->stream);
         }
-        TRY(alloc_zero(s, tw.size(), &s->twiddle));
-        cudaError_t e = cudaMemcpyAsync(s->twiddle, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, s->stream);
-        if (e != cudaSuccess) return cleanup(fail(FC_ERR_CUDA, "twiddle upload: %s", cudaGetErrorString(e)));
-        cudaStreamSynchronize(s->stream);
-    }
-    TRY(alloc_zero(s, (size_t)s->slots * B * n_nodes, &s->ring));
-    TRY(alloc_zero(s, (size_t)B * n_nodes, &s->psd));
-    TRY(alloc_zero(s, (size_t)B * n_nodes, &s->inv_psd));
-    {
-        std::vector<unsigned short> ta, tb;
-        for (int a = 0; a < s->nt; ++a)
-            for (int b = a; b < s->nt; ++b) {
-                ta.push_back((unsigned short)a);
-                tb.push_back((unsigned short)b);
-            }
-        TRY(alloc_zero(s, ta.size(), &s->tile_a));
-        TRY(alloc_zero(s, tb.size(), &s->tile_b));
-        cudaMemcpy(s->tile_a, ta.data(), ta.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
-        cudaMemcpy(s->tile_b, tb.data(), tb.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
-    }
-    if (cfg.mode == FC_MODE_STREAM) TRY(alloc_zero(s, (size_t)s->ntp * B * FC_BLOCK_WORDS, &s->acc));
-    if (cfg.precision != FC_PREC_FP32) {
-        s->ab_format = cfg.precision == FC_PREC_BF16 ? 1 : (cfg.precision == FC_PREC_FP16 ? 0 : 2);
-        const int per_chunk = s->ab_format == 2 ? 32 : 64;  // inner elements per 128-byte K-chunk
-        s->nchunks = (2 * window + per_chunk - 1) / per_chunk;
-        s->nt128 = (n_nodes + 127) / 128;
-        s->ntp128 = s->nt128 * (s->nt128 + 1) / 2;
-        std::vector<unsigned short> ta, tb;
-        for (int a = 0; a < s->nt128; ++a)
-            for (int b = a; b < s->nt128; ++b) {
-                ta.push_back((unsigned short)a);
-                tb.push_back((unsigned short)b);
-            }
-        TRY(alloc_zero(s, ta.size(), &s->tile_a128));
-        TRY(alloc_zero(s, tb.size(), &s->tile_b128));
-        cudaMemcpy(s->tile_a128, ta.data(), ta.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
-        cudaMemcpy(s->tile_b128, tb.data(), tb.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
-        TRY(alloc_zero(s, (size_t)s->nt128 * B * 4 * s->nchunks * herk_chunk_bytes(), &s->ops));
-        TRY(alloc_zero(s, (size_t)B * 3 * s->P, &s->herk_bins));
-    }
+        TRY(alloc_zero(s, (size_t)s->slots * B * n_nodes, &s->ring));
+        TRY(alloc_zero(s, (size_t)B * n_nodes, &s->psd));
+        TRY(alloc_zero(s, (size_t)B * n_nodes, &s->inv_psd));
+        {
+            std::vector<unsigned short> ta, tb;
+            for (int a = 0; a < s->nt; ++a)
+                for (int b = a; b < s->nt; ++b) {
+                    ta.push_back((unsigned short)a);
+                    tb.push_back((unsigned short)b);
+                }
+            TRY(alloc_zero(s, ta.size(), &s->tile_a));
+            TRY(alloc_zero(s, tb.size(), &s->tile_b));
+            // on the session stream, after the zero fill of the same buffers (a copy on the legacy
+            // stream is not ordered after work on a non-blocking stream)
+            TRY(upload(s, s->tile_a, ta.data(), ta.size() * sizeof(unsigned short)));
+            TRY(upload(s, s->tile_b, tb.data(), tb.size() * sizeof(unsigned short)));
+        }
+        if (cfg.mode == FC_MODE_STREAM) TRY(alloc_zero(s, (size_t)s->ntp * B * FC_BLOCK_WORDS, &s->acc));
+        if (cfg.precision != FC_PREC_FP32) {
+            s->ab_format = cfg.precision == FC_PREC_BF16 ? 1 : (cfg.precision == FC_PREC_FP16 ? 0 : 2);
+            const int per_chunk = s->ab_format == 2 ? 32 : 64;  // inner elements per 128-byte K-chunk
+            s->nchunks = (2 * window + per_chunk - 1) / per_chunk;
+            s->nt128 = (n_nodes + 127) / 128;
+            s->ntp128 = s->nt128 * (s->nt128 + 1) / 2;
+            std::vector<unsigned short> ta, tb;
+            for (int a = 0; a < s->nt128; ++a)
+                for (int b = a; b < s->nt128; ++b) {
+                    ta.push_back((unsigned short)a);
+                    tb.push_back((unsigned short)b);
+                }
+            TRY(alloc_zero(s, ta.size(), &s->tile_a128));
+            TRY(alloc_zero(s, tb.size(), &s->tile_b128));
+            TRY(upload(s, s->tile_a128, ta.data(), ta.size() * sizeof(unsigned short)));
+            TRY(upload(s, s->tile_b128, tb.data(), tb.size() * sizeof(unsigned short)));
+            TRY(alloc_zero(s, (size_t)s->nt128 * B * 4 * s->nchunks * herk_chunk_bytes(), &s->ops));
+            TRY(alloc_zero(s, (size_t)B * 3 * s->P, &s->herk_bins));
+        }
+        if (max_groups > 1) TRY(alloc_zero(s, (size_t)max_groups * 7 * s->P, &s->partial));
+    }  // spectral state
     TRY(alloc_zero(s, (size_t)FC_NMETRIC * s->P, &s->net));
-    if (max_groups > 1) TRY(alloc_zero(s, (size_t)max_groups * 7 * s->P, &s->partial));
     if (s->time_mask & FC_COR) {
         TRY(alloc_zero(s, (size_t)s->slots * n_nodes * n_samples, &s->zring));
         TRY(alloc_zero(s, (size_t)2 * s->P, &s->cor_acc));
+        s->cor_nt = (n_nodes + 127) / 128;
+        s->cor_ntp = s->cor_nt * (s->cor_nt + 1) / 2;
+        s->cor_nchunks = (n_samples + 31) / 32;
+        TRY(alloc_zero(s, (size_t)s->slots * s->cor_nt * s->cor_nchunks * cor_tc_pair_bytes(), &s->cor_ops));
     }
     if (s->time_mask & FC_XCOR) {
         int L = 1;
@@ -727,7 +776,7 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
             xt[k] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
         }
         TRY(alloc_zero(s, (size_t)M, &s->xcor_tw));
-        cudaMemcpy(s->xcor_tw, xt.data(), M * sizeof(float2), cudaMemcpyHostToDevice);
+        TRY(upload(s, s->xcor_tw, xt.data(), M * sizeof(float2)));
         TRY(alloc_zero(s, (size_t)s->slots * n_nodes * (M + 1), &s->xcor_spec));
         TRY(alloc_zero(s, (size_t)s->slots * n_nodes, &s->xcor_energy));
         TRY(alloc_zero(s, (size_t)s->slots * s->P, &s->xcor_vals));
@@ -1025,6 +1074,8 @@ fc_status fc_set_metric_mask(fc_session* s, uint32_t metric_mask) {
         return fail(FC_ERR_INVALID_ARG, "bad metric mask 0x%x", metric_mask);
     if ((metric_mask & (FC_COR | FC_XCOR)) & ~s->time_mask)
         return fail(FC_ERR_INVALID_ARG, "COR/XCOR can only be kept, not added after creation");
+    if ((metric_mask & FC_SPECTRAL_METRICS) && !s->spectral)
+        return fail(FC_ERR_INVALID_ARG, "the session was created without spectral metrics: none can be added");
     CK(cudaSetDevice(s->device));
     const uint32_t added = metric_mask & ~s->mask & FC_SPECTRAL_METRICS;
     s->mask = metric_mask;
@@ -1069,14 +1120,19 @@ fc_status fc_set_projection(fc_session* s, const float* op, int n_channels, int 
         cudaFree(s->proj);
         s->proj = nullptr;
     }
+    // ordered after the pushes already enqueued (they may still read the previous operator)
+    CK(cudaStreamSynchronize(s->stream));
     if (!s->proj) CK(cudaMalloc(&s->proj, bytes));
     s->proj_C = n_channels;
-    CK(cudaMemcpy(s->proj, op, bytes, op_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(s->proj, op, bytes, op_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       s->stream));
+    CK(cudaStreamSynchronize(s->stream));
     return FC_OK;
 }
 
 fc_status fc_set_band(fc_session* s, double f_lo, double f_hi) {
     if (!s) return fail(FC_ERR_INVALID_ARG, "NULL session");
+    if (!s->spectral) return fail(FC_ERR_INVALID_ARG, "the session was created without spectral metrics");
     fc_band b = s->band;
     b.f_lo = f_lo;
     b.f_hi = f_hi;
@@ -1186,10 +1242,11 @@ fc_status fc_session_restore(fc_session* s, const void* host_buf, size_t len) {
     }
     CK(cudaSetDevice(s->device));
     CK(cudaStreamSynchronize(s->stream));
-    for (const auto& sb : s->state_bufs) {
-        CK(cudaMemcpy(sb.first, in + off, sb.second, cudaMemcpyHostToDevice));
+    for (const auto& sb : s->state_bufs) {  // on the session stream: later pushes are ordered after
+        CK(cudaMemcpyAsync(sb.first, in + off, sb.second, cudaMemcpyHostToDevice, s->stream));
         off += sb.second;
     }
+    CK(cudaStreamSynchronize(s->stream));  // the caller may release host_buf on return
     s->mask = hd.mask;
     s->sel0 = hd.sel0;
     s->sel1 = hd.sel1;
@@ -1247,6 +1304,7 @@ void* fc_session_stream(const fc_session* s) { return s ? (void*)s->stream : nul
 
 fc_status fc_debug_get_spectra(fc_session* s, int age, float* out, size_t out_len) {
     if (!s || !out) return fail(FC_ERR_INVALID_ARG, "NULL argument");
+    if (!s->spectral) return fail(FC_ERR_INVALID_ARG, "the session was created without spectral metrics");
     const size_t need = (size_t)2 * s->B * s->n;
     if (out_len < need) return fail(FC_ERR_INVALID_ARG, "out_len too small");
     CK(cudaSetDevice(s->device));
@@ -1273,6 +1331,8 @@ fc_status fc_debug_get_accumulators(fc_session* s, fc_acc_field field, double* o
     if (!s || !out) return fail(FC_ERR_INVALID_ARG, "NULL argument");
     CK(cudaSetDevice(s->device));
     CK(cudaStreamSynchronize(s->stream));
+    if (field != FC_ACC_COR && field != FC_ACC_XCOR && !s->spectral)
+        return fail(FC_ERR_INVALID_ARG, "the session was created without spectral metrics");
     size_t need;
     if (field == FC_ACC_PSD) need = (size_t)s->B * s->n;
     else if (field == FC_ACC_COR || field == FC_ACC_XCOR) need = (size_t)s->P;

@@ -148,9 +148,11 @@ fc_status fc_fir_create(int n_channels, double fs, fc_fir_kind kind, double f_lo
     if (e == cudaSuccess) e = cudaMalloc(&f->d_h, T * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&f->d_state[0], sb);
     if (e == cudaSuccess) e = cudaMalloc(&f->d_state[1], sb);
-    if (e == cudaSuccess) e = cudaMemcpy(f->d_h, hf.data(), T * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(f->d_state[0], 0, sb);
-    if (e == cudaSuccess) e = cudaMemset(f->d_state[1], 0, sb);
+    // on the filter's stream (non-blocking: not ordered with the legacy stream), then waited for
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f->d_h, hf.data(), T * sizeof(float), cudaMemcpyHostToDevice, f->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_state[0], 0, sb, f->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_state[1], 0, sb, f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
     if (e == cudaSuccess) {  // the attribute is per kernel: set it for the longest filter allowed
         const int smem_max = (int)((2 * MAX_TAPS + OUT_PER_CTA - 1) * sizeof(float));
         e = cudaFuncSetAttribute(k_fir, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);

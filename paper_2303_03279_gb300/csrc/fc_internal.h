@@ -64,6 +64,7 @@ struct fc_session {
     fc_taper taper;
     uint32_t mask;      // metrics finalized each push
     uint32_t time_mask; // COR/XCOR state allocated at creation
+    bool spectral;      // spectral state (spectra ring, pair sums) allocated at creation
     fc_config cfg;
     bool own_stream;
     cudaStream_t stream;
@@ -124,6 +125,8 @@ struct fc_session {
     unsigned short* tile_a128;
     unsigned short* tile_b128;
     unsigned char* ops;     // packed operands [nt128][B][4][nchunks][16 KB]
+    unsigned char* cor_ops; // COR split-TF32 operand ring [slots][cor_nt][cor_nchunks][2][16 KB]
+    int cor_nt, cor_ntp, cor_nchunks;
     float* herk_bins;       // [B][3][P] per-bin COH, IMAGCOHY, PLV
     size_t device_bytes;
 
@@ -289,7 +292,26 @@ struct CorArgs {
     const FcCtrl* ctrl;
 };
 cudaError_t launch_cor_normalize(const CorArgs& a, cudaStream_t st);
-cudaError_t launch_cor_update(const CorArgs& a, cudaStream_t st);
+
+// COR on the tensor cores (k_cor_tc.cu): split-TF32 operand ring and per-trial products.
+struct CorTcArgs {
+    const float* zring;       // [slots][n][N] normalized trials (pack input)
+    unsigned char* ops;       // [slots][nt][nchunks][hi, lo][16 KB] TF32 operand blocks
+    int n, N, nt, ntp, nchunks, slots, W;
+    long long P;
+    int count, write_from;    // this call's trials; the window ends at pushed + count
+    int mode;                 // 0 = stream: add the newest trial, subtract the leaving one; 1 = window
+    int groups;               // mode 1: the window's trials split over this many groups per tile pair
+    float* cor_acc;           // [2][P] double-float sums
+    float* net;               // COR plane
+    float* part;              // groups > 1: [groups][2][P]
+    int finalize;
+    int grid_ctas;
+    const FcCtrl* ctrl;
+};
+cudaError_t launch_cor_tc_pack(const CorTcArgs& a, cudaStream_t st);
+cudaError_t launch_cor_tc(const CorTcArgs& a, cudaStream_t st);
+size_t cor_tc_pair_bytes();
 cudaError_t launch_cor_combine(const CorArgs& a, cudaStream_t st);
 
 struct XcorArgs {

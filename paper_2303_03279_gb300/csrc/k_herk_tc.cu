@@ -23,10 +23,12 @@
 
 #include "fc_internal.h"
 #include "mbar.cuh"
+#include "tc.cuh"
 
 namespace {
 
 using namespace fcmbar;
+using namespace fctc;
 
 constexpr int TILE = 128;             // nodes per tile (M = N = 128)
 constexpr int CHUNK_BYTES = 16384;     // 128 rows x 128 bytes of K
@@ -37,57 +39,6 @@ constexpr int EPI_WARPS = 8;           // epilogue warps: lane quarter w % 4, ro
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 512 + EPI_WARPS * 512;  // + barriers, TMEM address, 1/sqrt(PSD) rows per epilogue warp
 constexpr uint32_t TMEM_COLS = 512;    // 2 phase buffers x 2 accumulators x 128 FP32 columns
 constexpr int THREADS = 32 * EPI_WARPS + 32;  // warps 0-7: epilogue; warp 8: loads + MMAs
-
-// Shared-memory matrix descriptor: K-major, no swizzle; LBO = 128 B (next core matrix
-// along K), SBO = 1024 B (next 8-row group), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// Instruction descriptor: D = F32, A/B format (F16 = 0, BF16 = 1, TF32 = 2), both K-major,
-// N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_format, uint32_t M, uint32_t N) {
-    return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
-
-template <int KIND>  // 0 = kind::f16 (BF16/FP16 operands), 1 = kind::tf32
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
-    if (KIND == 0)
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(da), "l"(db), "r"(idesc), "r"(acc));
-    else
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(da), "l"(db), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 16 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
-}
 
 __device__ __forceinline__ long long packed_index(int i, int j, int n) {
     return (long long)i * n - (long long)i * (i + 1) / 2 + (j - i - 1);

@@ -18,6 +18,7 @@
 
 #include "df32.cuh"
 #include "fc_internal.h"
+#include "row_stats.cuh"
 
 namespace {
 
@@ -75,23 +76,14 @@ __global__ void k_xcor_spectra(XcorArgs a) {
     if (warp >= ntr * a.n) return;
     const int tr = a.write_from + warp / a.n, node = warp % a.n;
     const float* x = a.x + ((size_t)tr * a.n + node) * a.N;
-    double s = 0.0;
-    for (int t = lane; t < a.N; t += 32) s += (double)x[t];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const double mean = s / a.N;
-    double q = 0.0;
-    for (int t = lane; t < a.N; t += 32) {
-        const double d = (double)x[t] - mean;
-        q += d * d;
-    }
-    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-    const float fmean = (float)mean;
+    // centered samples and their energy as double words on the FP32 pipes (row_stats.cuh)
+    const RowStats st = warp_row_stats(x, a.N, lane);
     int bits = 0;
     while ((1 << bits) < M) ++bits;
     for (int m = lane; m < M; m += 32) {
         const int t0 = 2 * m, t1 = 2 * m + 1;
-        const float v0 = t0 < a.N ? __fsub_rn(x[t0], fmean) : 0.f;
-        const float v1 = t1 < a.N ? __fsub_rn(x[t1], fmean) : 0.f;
+        const float v0 = t0 < a.N ? st.dev(x[t0]) : 0.f;
+        const float v1 = t1 < a.N ? st.dev(x[t1]) : 0.f;
         buf[bitrev(m, bits)] = make_float2(v0, v1);
     }
     __syncwarp();
@@ -108,7 +100,7 @@ __global__ void k_xcor_spectra(XcorArgs a) {
         const float2 w = (k < M) ? a.tw[k] : make_float2(-1.f, 0.f);
         out[k] = cadd(e, cmul(w, o));
     }
-    if (lane == 0) a.energy[(size_t)slot * a.n + node] = (float)q;
+    if (lane == 0) a.energy[(size_t)slot * a.n + node] = st.ss;
 }
 
 // ------------------------------------------------------------------ pair correlations

@@ -351,6 +351,10 @@ CASES = {
                              desc="1024 nodes, W = 100, 40 bins, full-window FP32 recompute: bulk fill + 3 pushes"),
     "window_1024_bf16": dict(n=1024, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=100, prec="bf16", pushes=3,
                              desc="1024 nodes, W = 100, 40 bins, BF16 tensor-core full window: bulk fill + 3 pushes"),
+    "cor_1000_window": dict(n=1000, N=1000, fs=600.0, band=(8.0, 12.0, 1200), W=50, prec="fp32", pushes=3,
+                            metrics="COR",
+                            desc="COR only, 1000 nodes, W = 50 trials x 1000 samples, full-window recompute on "
+                                 "the tensor cores (split TF32): bulk fill + 3 pushes"),
 }
 
 
@@ -370,8 +374,8 @@ def run_case(args):
         x = white_trials(5, W + c["pushes"], n, N)
     x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
     prec = {"fp32": fc.FC_PREC_FP32, "bf16": fc.FC_PREC_BF16}[c["prec"]]
-    with fc.Session(n, N, c["fs"], c["band"], "hann", fc.FC_SPECTRAL_METRICS, W, mode=fc.FC_MODE_FULL,
-                    precision=prec) as s:
+    mask = fc.FC_COR if c.get("metrics") == "COR" else fc.FC_SPECTRAL_METRICS
+    with fc.Session(n, N, c["fs"], c["band"], "hann", mask, W, mode=fc.FC_MODE_FULL, precision=prec) as s:
         fc.fc_push_trials(s.handle, x[:W].contiguous(), W)
         fc.fc_sync(s.handle)
         fc.fc_set_profiling(s.handle, True)

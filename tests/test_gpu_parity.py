@@ -254,11 +254,16 @@ def test_zero_and_identical_channels():
     x = white_trials(7, 5, n, N)
     x[:, 3] = 0.0
     x[:, 7] = x[:, 11]
+    x[:, 20] = 3.25  # constant, nonzero: centered to exactly 0, so COR and XCOR are 0
     with _session(n, N, 100.0, (1.0, 40.0, 128), 5) as s:
         s.push(x)
         nets = _nets(s, SPECTRAL + ("COR", "XCOR"))
         for m in ("COH", "IMAGCOHY", "PLV", "PLI", "WPLI", "DSWPLI", "COR", "XCOR"):
             assert np.all(nets[m][packed_index(3, np.arange(4, n), n)] == 0.0), m
+        others = np.array([k for k in range(n) if k != 20])
+        lo, hi = np.minimum(others, 20), np.maximum(others, 20)
+        for m in ("COR", "XCOR"):
+            assert np.all(nets[m][packed_index(lo, hi, n)] == 0.0), m
         p = packed_index(7, 11, n)
         assert abs(nets["COH"][p] - 1) < 1e-5 and abs(nets["PLV"][p] - 1) < 1e-5
         assert nets["PLI"][p] == 0 and nets["IMAGCOHY"][p] == 0 and nets["WPLI"][p] == 0

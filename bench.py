@@ -351,6 +351,10 @@ CASES = {
                              desc="1024 nodes, W = 100, 40 bins, full-window FP32 recompute: bulk fill + 3 pushes"),
     "window_1024_bf16": dict(n=1024, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=100, prec="bf16", pushes=3,
                              desc="1024 nodes, W = 100, 40 bins, BF16 tensor-core full window: bulk fill + 3 pushes"),
+    "xcor_306_window": dict(n=306, N=500, fs=600.0, band=(8.0, 12.0, 600), W=20, prec="fp32", pushes=2,
+                            metrics="XCOR",
+                            desc="XCOR only, 306 nodes, W = 20 trials x 500 samples (1024-point transforms), "
+                                 "full-window recompute: bulk fill + 2 pushes"),
     "cor_1000_window": dict(n=1000, N=1000, fs=600.0, band=(8.0, 12.0, 1200), W=50, prec="fp32", pushes=3,
                             metrics="COR",
                             desc="COR only, 1000 nodes, W = 50 trials x 1000 samples, full-window recompute on "
@@ -374,7 +378,7 @@ def run_case(args):
         x = white_trials(5, W + c["pushes"], n, N)
     x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
     prec = {"fp32": fc.FC_PREC_FP32, "bf16": fc.FC_PREC_BF16}[c["prec"]]
-    mask = fc.FC_COR if c.get("metrics") == "COR" else fc.FC_SPECTRAL_METRICS
+    mask = {"COR": fc.FC_COR, "XCOR": fc.FC_XCOR}.get(c.get("metrics"), fc.FC_SPECTRAL_METRICS)
     with fc.Session(n, N, c["fs"], c["band"], "hann", mask, W, mode=fc.FC_MODE_FULL, precision=prec) as s:
         fc.fc_push_trials(s.handle, x[:W].contiguous(), W)
         fc.fc_sync(s.handle)

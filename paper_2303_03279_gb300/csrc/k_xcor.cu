@@ -30,9 +30,11 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
 // Pair (i, j), i < j, of packed index p (row r starts at r*n - r(r+1)/2).
+// Row i of packed pair p: an FP32 estimate from the quadratic (FP64 runs at a small fraction
+// of the FP32 rate here), corrected exactly in integers.
 __device__ __forceinline__ void unpack_pair(long long p, int n, int& i, int& j) {
-    const double b = 2.0 * n - 1.0;
-    int r = (int)floor((b - sqrt(b * b - 8.0 * (double)p)) * 0.5);
+    const float b = 2.0f * (float)n - 1.0f;
+    int r = (int)floorf((b - sqrtf(fmaxf(b * b - 8.0f * (float)p, 0.f))) * 0.5f);
     if (r < 0) r = 0;
     if (r > n - 2) r = n - 2;
     while (r > 0 && (long long)r * n - (long long)r * (r + 1) / 2 > p) --r;
@@ -193,9 +195,18 @@ __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_
                                                        int n_trials) {
     constexpr int M = 32 * E;
     __shared__ float2 stw[M];  // tw[k] = e^{-2 pi i k / L}, k < M
+    // the butterflies' twiddles by stage: span h reads sth[h + t] = tw[t M / h], t < h, so a
+    // stage's lanes read consecutive entries (or one entry each, broadcast): no bank conflicts
+    __shared__ float2 sth[M];
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
-    for (int k = threadIdx.x; k < M; k += blockDim.x) stw[k] = a.tw[k];
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        stw[k] = a.tw[k];
+        if (k > 0) {
+            const int h = 1 << (31 - __clz(k));
+            sth[k] = a.tw[(k - h) * (M / h)];
+        }
+    }
     __syncthreads();
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
@@ -232,7 +243,7 @@ __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_
             if ((r % (2 * hr)) >= hr) continue;
             const int e = lane + 32 * r;
             const float2 u = x[r], v = x[r + hr];
-            const float2 w = cconj(stw[(e % h) * (M / h)]);
+            const float2 w = cconj(sth[h + e % h]);
             x[r] = cadd(u, v);
             x[r + hr] = cmul(csub(u, v), w);
         }
@@ -240,7 +251,7 @@ __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_
 #pragma unroll
     for (int h = (M / 2 < 16 ? M / 2 : 16); h >= 1; h >>= 1) {  // partner in lane ^ h
         const bool upper = (lane & h) != 0;
-        const float2 w = cconj(stw[(lane % h) * (M / h)]);
+        const float2 w = cconj(sth[h + lane % h]);
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const float2 mine = x[r];

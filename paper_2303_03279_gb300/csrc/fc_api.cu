@@ -270,10 +270,19 @@ fc_status stage_time_metrics(fc_session* s, const float* x, int count, int write
         ta.grid_ctas = s->num_sms;
         ta.ctrl = s->ctrl;
         if (mode == 1) {
-            // few tile pairs: split the window's trials over several CTAs per tile pair
+            // split the window's trials over G groups per tile pair, G minimizing the busiest
+            // CTA's work: ceil(units / SMs) units of ceil(K / G) trials each (ties: fewer groups)
             const long long k_est = s->W > 0 ? std::min<long long>(s->W, s->enqueued + count) : s->enqueued + count;
-            const int G = (int)std::max<long long>(1, std::min<long long>({(s->num_sms + s->cor_ntp - 1) / s->cor_ntp,
-                                                                          k_est, 64}));
+            int G = 1;
+            long long best = -1;
+            for (int g = 1; g <= std::min<long long>(k_est, 64); ++g) {
+                const long long rounds = ((long long)s->cor_ntp * g + s->num_sms - 1) / s->num_sms;
+                const long long cost = rounds * ((k_est + g - 1) / g);
+                if (best < 0 || cost < best) {
+                    best = cost;
+                    G = g;
+                }
+            }
             if (G > 1) {
                 const size_t need = (size_t)G * 2 * s->P;
                 if (s->cor_part_len < need) {

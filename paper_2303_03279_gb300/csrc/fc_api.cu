@@ -443,6 +443,28 @@ fc_status push_bulk(fc_session* s, const float* x, int count, bool write_acc) {
     return FC_OK;
 }
 
+// Bin groups of the full-window kernels (one CTA per tile pair and group of bins, two CTAs
+// per SM): the count minimizing an estimate of the time, the busiest slot's work
+// (ceil(ntp g / (2 SMs)) rounds of ceil(B / g) bins, about 0.67 us per bin and trial of the
+// window) plus, for g > 1, writing and reducing g x 7 band planes of P pairs (~5 TB/s).
+void window_groups(long long ntp, int B, long long P, int K, int sms, int& groups, int& group_bins) {
+    double best = -1.0;
+    groups = 1;
+    group_bins = B;
+    const double us_per_bin = 0.67 * (K > 0 ? K : 100);
+    for (int g = 1; g <= B; ++g) {
+        const int gb = (B + g - 1) / g;
+        if ((B + gb - 1) / gb != g) continue;  // g groups of gb bins cover B exactly
+        const long long rounds = (ntp * g + 2LL * sms - 1) / (2LL * sms);
+        const double t = (double)rounds * gb * us_per_bin + (g > 1 ? g * 7.0 * (double)P * 8.0 / 5.0e6 : 0.0);
+        if (best < 0.0 || t < best) {
+            best = t;
+            groups = g;
+            group_bins = gb;
+        }
+    }
+}
+
 // Streams and events of the pipelined host I/O, created on first use.
 fc_status ensure_io(fc_session* s) {
     if (s->in_stream) return FC_OK;
@@ -569,7 +591,9 @@ size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode 
     if (mask & FC_SPECTRAL_METRICS) {
         b += (size_t)N * B * 8 + slots * B * n * 8 + (size_t)B * n * 12 + ntp * 4;
         if (mode == FC_MODE_STREAM) b += ntp * B * FC_BLOCK_WORDS * 4;
-        const int groups = std::min(B, std::max(1, (int)((152 * 4 + ntp - 1) / ntp)));
+        int wg, wgb;
+        window_groups((long long)ntp, B, (long long)P, W, 152, wg, wgb);
+        const int groups = std::max(wg, std::min(B, std::max(1, (int)((152 * 4 + ntp - 1) / ntp))));
         if (groups > 1) b += (size_t)groups * 7 * P * 4;
     }
     if (mask & FC_COR)
@@ -694,11 +718,10 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
 
     // work split: enough CTAs to fill 152 SMs twice over
     const int target = 152 * 4;
-    s->groups = std::min(B, std::max(1, (target + s->ntp - 1) / s->ntp));
-    s->group_bins = (B + s->groups - 1) / s->groups;
-    s->groups = (B + s->group_bins - 1) / s->group_bins;
-    s->stream_groups = s->groups;
-    s->stream_group_bins = s->group_bins;
+    s->stream_groups = std::min(B, std::max(1, (target + s->ntp - 1) / s->ntp));
+    s->stream_group_bins = (B + s->stream_groups - 1) / s->stream_groups;
+    s->stream_groups = (B + s->stream_group_bins - 1) / s->stream_group_bins;
+    window_groups(s->ntp, B, s->P, window, s->num_sms, s->groups, s->group_bins);
     const int max_groups = std::max(s->groups, s->stream_groups);
 
     fc_status st;

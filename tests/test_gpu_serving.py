@@ -156,3 +156,47 @@ def test_nonfinite_trial_is_rejected_in_the_mix():
                 assert_close(got[k][m], want[k][m], what=f"{m} after a rejected trial")
             else:
                 assert np.array_equal(got[k][m], want[k][m], equal_nan=True), (k, m)
+
+
+def test_time_domain_session_beside_a_spectral_session():
+    """A COR + XCOR session (it holds no spectral state) served beside a spectral session:
+    its networks equal those of a standalone session fed the same trials, and a spectral
+    metric is refused for it."""
+    n1, N1, fs1, band1, W1, T1 = CONFIGS[0]
+    n2, N2, W2, T2 = 48, 160, 6, 12
+    band2 = (1.0, 50.0, 256)
+    x1 = white_trials(61, T1, n1, N1)
+    x2 = white_trials(62, T2, n2, N2)
+    x2[:, 5] = x2[:, 9] * 0.5 + x2[:, 5] * 0.5  # one correlated pair
+    P2 = n2 * (n2 - 1) // 2
+    sv = fc.fc_server_create()
+    try:
+        a = fc.fc_server_open(sv, n1, N1, fs1, band1, "hann", fc.FC_SPECTRAL_METRICS, W1)
+        b = fc.fc_server_open(sv, n2, N2, 500.0, band2, "hann", fc.FC_COR | fc.FC_XCOR, W2)
+        for t in range(max(T1, T2)):
+            if t < T1:
+                fc.fc_server_submit(sv, a, x1[t], fc.fc_server_now_ms())
+            if t < T2:
+                fc.fc_server_submit(sv, b, x2[t], fc.fc_server_now_ms())
+        fc.fc_server_drain(sv, 120000)
+        res = fc.fc_server_poll(sv, 4096)
+        assert len(res) == T1 + T2 and all(r[2] == fc.FC_OK for r in res)
+        served = {}
+        for m in ("COR", "XCOR"):
+            buf = np.empty(P2, np.float32)
+            fc.fc_server_get_network(sv, b, fc.METRIC_BITS[m], buf)
+            served[m] = buf
+        with pytest.raises(fc.FcError):
+            fc.fc_server_get_network(sv, b, fc.FC_COH, np.empty(P2, np.float32))
+        coh = np.empty(n1 * (n1 - 1) // 2, np.float32)
+        fc.fc_server_get_network(sv, a, fc.FC_COH, coh)
+        assert np.all(np.isfinite(coh)) and coh.max() > 0
+    finally:
+        fc.fc_server_destroy(sv)
+    with fc.Session(n2, N2, 500.0, band2, "hann", fc.FC_COR | fc.FC_XCOR, W2) as s:
+        for t in range(T2):
+            s.push(x2[t])
+        for m in ("COR", "XCOR"):
+            assert_close(served[m], s.network(m, packed=True)[0], what=m)
+        with pytest.raises(fc.FcError):  # spectral metrics cannot be added to this session
+            fc.fc_set_metric_mask(s.handle, fc.FC_COR | fc.FC_COH)

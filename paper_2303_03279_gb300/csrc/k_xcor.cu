@@ -184,12 +184,15 @@ __global__ void k_xcor_pairs(XcorArgs a, long long n_items, long long first_tria
 }
 
 // Register form for transforms of M = 32 E points (E = 2 .. 64, trials up to 2,048
-// samples): lane l holds elements l + 32 r, r < E. The inverse transform runs as radix-2
-// decimation in frequency on natural-order input: spans of 32 or more pair registers of
-// the same lane, shorter spans pair lanes through __shfl_xor_sync; twiddles come from a
-// per-block copy of the table in shared memory. The output lands in bit-reversed order,
-// which the scan over lags reads through the bit reversal of each position. No shared
-// memory holds data and no barrier runs between the stages.
+// samples). The inverse transform runs as radix-2 decimation in frequency on natural-order
+// input. Lane l first holds elements l + 32 r, r < E: spans of 32 or more pair registers of
+// the same lane; spans from 16 down to E (only when E <= 16) pair lanes through
+// __shfl_xor_sync. One transpose through this warp's shared-memory buffer (a pad slot per E
+// elements keeps both directions free of bank conflicts) then gives lane l the E
+// consecutive elements l E + q, so the remaining spans (below E and below 32) pair
+// registers of the same lane again, with twiddles that are the same for every lane. The
+// output lands in bit-reversed order, which the scan over lags reads through the bit
+// reversal of each position.
 template <int E>
 __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_items, long long first_trial,
                                                        int n_trials) {
@@ -198,6 +201,7 @@ __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_
     // the butterflies' twiddles by stage: span h reads sth[h + t] = tw[t M / h], t < h, so a
     // stage's lanes read consecutive entries (or one entry each, broadcast): no bank conflicts
     __shared__ float2 sth[M];
+    extern __shared__ float2 xbuf[];  // [warps][M + M / E]: transpose buffers
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_
         }
     }
 #pragma unroll
-    for (int h = (M / 2 < 16 ? M / 2 : 16); h >= 1; h >>= 1) {  // partner in lane ^ h
+    for (int h = 16; h >= E; h >>= 1) {  // partner in lane ^ h (E <= 16 only)
         const bool upper = (lane & h) != 0;
         const float2 w = cconj(sth[h + lane % h]);
 #pragma unroll
@@ -258,6 +262,30 @@ __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_
             const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, mine.x, h),
                                              __shfl_xor_sync(0xffffffffu, mine.y, h));
             x[r] = upper ? cmul(csub(other, mine), w) : cadd(mine, other);
+        }
+    }
+    // transpose: lane l takes elements l E + q, q < E
+    {
+        float2* tb = xbuf + (size_t)wib * (M + M / E);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int e = lane + 32 * r;
+            tb[e + e / E] = x[r];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < E; ++q) x[q] = tb[lane * (E + 1) + q];
+    }
+    constexpr int HL = E / 2 < 16 ? E / 2 : 16;  // first span inside the lane after the transpose
+#pragma unroll
+    for (int h = HL; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            if ((q % (2 * h)) >= h) continue;
+            const float2 u = x[q], v = x[q + h];
+            const float2 w = cconj(sth[h + q % h]);  // (l E + q) mod h = q mod h
+            x[q] = cadd(u, v);
+            x[q + h] = cmul(csub(u, v), w);
         }
     }
     // position e holds y[bitrev(e)]; r[2m] = Re y[m] / M, r[2m+1] = Im y[m] / M
@@ -269,7 +297,7 @@ __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_
     const int L = 2 * M;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-        const int m = bitrev(lane + 32 * r, bits);
+        const int m = bitrev(lane * E + r, bits);
 #pragma unroll
         for (int part = 0; part < 2; ++part) {
             const int idx = 2 * m + part;
@@ -330,6 +358,15 @@ __global__ void k_xcor_update(XcorArgs a) {
 
 }  // namespace
 
+template <int E>
+cudaError_t launch_pairs_reg(const XcorArgs& a, long long items, long long first, int n_trials, cudaStream_t st) {
+    const int dyn = 8 * (32 * E + 32) * (int)sizeof(float2);  // 8 warps x (M + M / E) transpose slots
+    cudaError_t e = cudaFuncSetAttribute(k_xcor_pairs_reg<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return e;
+    k_xcor_pairs_reg<E><<<(unsigned)((items + 7) / 8), 256, dyn, st>>>(a, items, first, n_trials);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_xcor_spectra(const XcorArgs& a, cudaStream_t st) {
     const long long warps = (long long)(a.count - a.write_from) * a.n;
     if (warps <= 0) return cudaSuccess;
@@ -364,14 +401,13 @@ cudaError_t launch_xcor_pairs(const XcorArgs& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     // register form for M = 64 .. 2048 (8 warps per block), shared-memory form otherwise
-    const unsigned rb = (unsigned)((items + 7) / 8);
     switch (M) {
-        case 64: k_xcor_pairs_reg<2><<<rb, 256, 0, st>>>(a, items, first, n_trials); return cudaGetLastError();
-        case 128: k_xcor_pairs_reg<4><<<rb, 256, 0, st>>>(a, items, first, n_trials); return cudaGetLastError();
-        case 256: k_xcor_pairs_reg<8><<<rb, 256, 0, st>>>(a, items, first, n_trials); return cudaGetLastError();
-        case 512: k_xcor_pairs_reg<16><<<rb, 256, 0, st>>>(a, items, first, n_trials); return cudaGetLastError();
-        case 1024: k_xcor_pairs_reg<32><<<rb, 256, 0, st>>>(a, items, first, n_trials); return cudaGetLastError();
-        case 2048: k_xcor_pairs_reg<64><<<rb, 256, 0, st>>>(a, items, first, n_trials); return cudaGetLastError();
+        case 64: return launch_pairs_reg<2>(a, items, first, n_trials, st);
+        case 128: return launch_pairs_reg<4>(a, items, first, n_trials, st);
+        case 256: return launch_pairs_reg<8>(a, items, first, n_trials, st);
+        case 512: return launch_pairs_reg<16>(a, items, first, n_trials, st);
+        case 1024: return launch_pairs_reg<32>(a, items, first, n_trials, st);
+        case 2048: return launch_pairs_reg<64>(a, items, first, n_trials, st);
         default: break;
     }
     k_xcor_pairs<<<(unsigned)((items + wpb - 1) / wpb), wpb * 32, sm, st>>>(a, items, first, n_trials);

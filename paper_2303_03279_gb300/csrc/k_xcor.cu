@@ -183,25 +183,31 @@ __global__ void k_xcor_pairs(XcorArgs a, long long n_items, long long first_tria
     }
 }
 
-// Register form for transforms of M = 32 E points (E = 2 .. 64, trials up to 2,048
-// samples). The inverse transform runs as radix-2 decimation in frequency on natural-order
-// input. Lane l first holds elements l + 32 r, r < E: spans of 32 or more pair registers of
-// the same lane; spans from 16 down to E (only when E <= 16) pair lanes through
-// __shfl_xor_sync. One transpose through this warp's shared-memory buffer (a pad slot per E
-// elements keeps both directions free of bank conflicts) then gives lane l the E
+// Register form for transforms of M = 32 E 2^S complex points (E = 2 .. 64, S = 0 or 1:
+// trials up to 4,096 samples). The inverse transform runs as radix-2 decimation in
+// frequency on natural-order input. With S = 1 the first stage splits it into two
+// independent halves of 32 E points (top: u + v, the even outputs; bottom: (u - v) w, the
+// odd outputs), transformed one after the other in the same registers. Within a transform
+// of 32 E points, lane l first holds elements l + 32 r, r < E: spans of 32 or more pair
+// registers of the same lane; spans from 16 down to E (only when E <= 16) pair lanes
+// through __shfl_xor_sync. One transpose through this warp's shared-memory buffer (a pad
+// slot per E elements keeps both directions free of bank conflicts) then gives lane l the E
 // consecutive elements l E + q, so the remaining spans (below E and below 32) pair
 // registers of the same lane again, with twiddles that are the same for every lane. The
 // output lands in bit-reversed order, which the scan over lags reads through the bit
 // reversal of each position.
-template <int E>
+template <int E, int S>
 __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_items, long long first_trial,
                                                        int n_trials) {
-    constexpr int M = 32 * E;
-    __shared__ float2 stw[M];  // tw[k] = e^{-2 pi i k / L}, k < M
-    // the butterflies' twiddles by stage: span h reads sth[h + t] = tw[t M / h], t < h, so a
-    // stage's lanes read consecutive entries (or one entry each, broadcast): no bank conflicts
-    __shared__ float2 sth[M];
-    extern __shared__ float2 xbuf[];  // [warps][M + M / E]: transpose buffers
+    constexpr int MS = 32 * E;  // points of one register transform
+    constexpr int M = MS << S;  // points of the whole complex transform
+    // dynamic shared memory: stw[M] = tw[k] = e^{-2 pi i k / L}; sth[M] = the butterflies'
+    // twiddles by stage, span h at sth[h + t] = tw[t M / h], t < h (a stage's lanes read
+    // consecutive entries or one entry each, broadcast: no bank conflicts); then one
+    // transpose buffer of MS + MS / E slots per warp
+    extern __shared__ float2 dsm[];
+    float2* stw = dsm;
+    float2* sth = dsm + M;
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
@@ -224,49 +230,62 @@ __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_
     const float2* Zi = a.spec + ((size_t)slot * a.n + i) * (M + 1);
     const float2* Zj = a.spec + ((size_t)slot * a.n + j) * (M + 1);
     // Y[k] = E[k] + i O[k], E = (P[k] + conj P[M-k]) / 2, O = (P[k] - conj P[M-k]) e^{+2 pi i k/L} / 2
-    float2 x[E];
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-        const int k = lane + 32 * r;
+    auto prod = [&](int k) -> float2 {
         const float2 pk = cmul(Zi[k], cconj(Zj[k]));
         const float2 pm = cconj(cmul(Zi[M - k], cconj(Zj[M - k])));
         const float2 e = make_float2(0.5f * __fadd_rn(pk.x, pm.x), 0.5f * __fadd_rn(pk.y, pm.y));
         const float2 dd = csub(pk, pm);
         const float2 w = cconj(stw[k]);  // e^{+2 pi i k / L}
         const float2 o = cmul(make_float2(0.5f * dd.x, 0.5f * dd.y), w);
-        x[r] = make_float2(__fsub_rn(e.x, o.y), __fadd_rn(e.y, o.x));
-    }
-    // inverse transform (e^{+2 pi i ...}), decimation in frequency
-#pragma unroll
-    for (int h = M / 2; h >= 32; h >>= 1) {  // partner in this lane's registers
-        constexpr int dummy = 0;
-        (void)dummy;
-        const int hr = h / 32;
+        return make_float2(__fsub_rn(e.x, o.y), __fadd_rn(e.y, o.x));
+    };
+    constexpr int bits = 5 + (E >= 2) + (E >= 4) + (E >= 8) + (E >= 16) + (E >= 32) + (E >= 64);  // log2 MS
+    float best = -INFINITY;
+    int best_tau = 0;
+    const float invM = 1.0f / (float)M;
+    const int L = 2 * M;
+    float2* tb = dsm + 2 * M + (size_t)wib * (MS + MS / E);
+#pragma unroll 1
+    for (int half = 0; half < (1 << S); ++half) {
+        float2 x[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {
-            if ((r % (2 * hr)) >= hr) continue;
             const int e = lane + 32 * r;
-            const float2 u = x[r], v = x[r + hr];
-            const float2 w = cconj(sth[h + e % h]);
-            x[r] = cadd(u, v);
-            x[r + hr] = cmul(csub(u, v), w);
+            if (S == 0) {
+                x[r] = prod(e);
+            } else {  // first stage, span MS: top half u + v, bottom half (u - v) e^{+2 pi i e / M}
+                const float2 u = prod(e), v = prod(e + MS);
+                x[r] = half == 0 ? cadd(u, v) : cmul(csub(u, v), cconj(sth[MS + e]));
+            }
         }
-    }
+        // inverse transform (e^{+2 pi i ...}), decimation in frequency
 #pragma unroll
-    for (int h = 16; h >= E; h >>= 1) {  // partner in lane ^ h (E <= 16 only)
-        const bool upper = (lane & h) != 0;
-        const float2 w = cconj(sth[h + lane % h]);
+        for (int h = MS / 2; h >= 32; h >>= 1) {  // partner in this lane's registers
+            const int hr = h / 32;
 #pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const float2 mine = x[r];
-            const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, mine.x, h),
-                                             __shfl_xor_sync(0xffffffffu, mine.y, h));
-            x[r] = upper ? cmul(csub(other, mine), w) : cadd(mine, other);
+            for (int r = 0; r < E; ++r) {
+                if ((r % (2 * hr)) >= hr) continue;
+                const int e = lane + 32 * r;
+                const float2 u = x[r], v = x[r + hr];
+                const float2 w = cconj(sth[h + e % h]);
+                x[r] = cadd(u, v);
+                x[r + hr] = cmul(csub(u, v), w);
+            }
         }
-    }
-    // transpose: lane l takes elements l E + q, q < E
-    {
-        float2* tb = xbuf + (size_t)wib * (M + M / E);
+#pragma unroll
+        for (int h = 16; h >= E; h >>= 1) {  // partner in lane ^ h (E <= 16 only)
+            const bool upper = (lane & h) != 0;
+            const float2 w = cconj(sth[h + lane % h]);
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const float2 mine = x[r];
+                const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, mine.x, h),
+                                                 __shfl_xor_sync(0xffffffffu, mine.y, h));
+                x[r] = upper ? cmul(csub(other, mine), w) : cadd(mine, other);
+            }
+        }
+        // transpose: lane l takes elements l E + q, q < E
+        __syncwarp();  // the previous half's reads of the buffer are done
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const int e = lane + 32 * r;
@@ -275,38 +294,33 @@ __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < E; ++q) x[q] = tb[lane * (E + 1) + q];
-    }
-    constexpr int HL = E / 2 < 16 ? E / 2 : 16;  // first span inside the lane after the transpose
+        constexpr int HL = E / 2 < 16 ? E / 2 : 16;  // first span inside the lane after the transpose
 #pragma unroll
-    for (int h = HL; h >= 1; h >>= 1) {
+        for (int h = HL; h >= 1; h >>= 1) {
 #pragma unroll
-        for (int q = 0; q < E; ++q) {
-            if ((q % (2 * h)) >= h) continue;
-            const float2 u = x[q], v = x[q + h];
-            const float2 w = cconj(sth[h + q % h]);  // (l E + q) mod h = q mod h
-            x[q] = cadd(u, v);
-            x[q + h] = cmul(csub(u, v), w);
+            for (int q = 0; q < E; ++q) {
+                if ((q % (2 * h)) >= h) continue;
+                const float2 u = x[q], v = x[q + h];
+                const float2 w = cconj(sth[h + q % h]);  // (l E + q) mod h = q mod h
+                x[q] = cadd(u, v);
+                x[q + h] = cmul(csub(u, v), w);
+            }
         }
-    }
-    // position e holds y[bitrev(e)]; r[2m] = Re y[m] / M, r[2m+1] = Im y[m] / M
-    int bits = 0;
-    while ((1 << bits) < M) ++bits;
-    float best = -INFINITY;
-    int best_tau = 0;
-    const float invM = 1.0f / (float)M;
-    const int L = 2 * M;
+        // position e holds this half's output bitrev(e), i.e. y[m] with m = 2^S bitrev(e) + half;
+        // r[2m] = Re y[m] / M, r[2m+1] = Im y[m] / M
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-        const int m = bitrev(lane * E + r, bits);
+        for (int r = 0; r < E; ++r) {
+            const int m = (bitrev(lane * E + r, bits) << S) + half;
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {
-            const int idx = 2 * m + part;
-            const int tau = idx <= a.N - 1 ? idx : (idx >= L - (a.N - 1) ? idx - L : INT_MIN);
-            if (tau == INT_MIN) continue;
-            const float v = __fmul_rn(part ? x[r].y : x[r].x, invM);
-            if (better(v, tau, best, best_tau)) {
-                best = v;
-                best_tau = tau;
+            for (int part = 0; part < 2; ++part) {
+                const int idx = 2 * m + part;
+                const int tau = idx <= a.N - 1 ? idx : (idx >= L - (a.N - 1) ? idx - L : INT_MIN);
+                if (tau == INT_MIN) continue;
+                const float v = __fmul_rn(part ? x[r].y : x[r].x, invM);
+                if (better(v, tau, best, best_tau)) {
+                    best = v;
+                    best_tau = tau;
+                }
             }
         }
     }
@@ -358,12 +372,14 @@ __global__ void k_xcor_update(XcorArgs a) {
 
 }  // namespace
 
-template <int E>
+template <int E, int S>
 cudaError_t launch_pairs_reg(const XcorArgs& a, long long items, long long first, int n_trials, cudaStream_t st) {
-    const int dyn = 8 * (32 * E + 32) * (int)sizeof(float2);  // 8 warps x (M + M / E) transpose slots
-    cudaError_t e = cudaFuncSetAttribute(k_xcor_pairs_reg<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    constexpr int MS = 32 * E;
+    // twiddle tables (2 M) and 8 warps x (MS + MS / E) transpose slots
+    const int dyn = (2 * (MS << S) + 8 * (MS + MS / E)) * (int)sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_xcor_pairs_reg<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
-    k_xcor_pairs_reg<E><<<(unsigned)((items + 7) / 8), 256, dyn, st>>>(a, items, first, n_trials);
+    k_xcor_pairs_reg<E, S><<<(unsigned)((items + 7) / 8), 256, dyn, st>>>(a, items, first, n_trials);
     return cudaGetLastError();
 }
 
@@ -400,14 +416,15 @@ cudaError_t launch_xcor_pairs(const XcorArgs& a, cudaStream_t st) {
         cudaError_t e = cudaFuncSetAttribute(k_xcor_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    // register form for M = 64 .. 2048 (8 warps per block), shared-memory form otherwise
+    // register form for M = 64 .. 4096 (8 warps per block), shared-memory form otherwise
     switch (M) {
-        case 64: return launch_pairs_reg<2>(a, items, first, n_trials, st);
-        case 128: return launch_pairs_reg<4>(a, items, first, n_trials, st);
-        case 256: return launch_pairs_reg<8>(a, items, first, n_trials, st);
-        case 512: return launch_pairs_reg<16>(a, items, first, n_trials, st);
-        case 1024: return launch_pairs_reg<32>(a, items, first, n_trials, st);
-        case 2048: return launch_pairs_reg<64>(a, items, first, n_trials, st);
+        case 64: return launch_pairs_reg<2, 0>(a, items, first, n_trials, st);
+        case 128: return launch_pairs_reg<4, 0>(a, items, first, n_trials, st);
+        case 256: return launch_pairs_reg<8, 0>(a, items, first, n_trials, st);
+        case 512: return launch_pairs_reg<16, 0>(a, items, first, n_trials, st);
+        case 1024: return launch_pairs_reg<32, 0>(a, items, first, n_trials, st);
+        case 2048: return launch_pairs_reg<64, 0>(a, items, first, n_trials, st);
+        case 4096: return launch_pairs_reg<64, 1>(a, items, first, n_trials, st);
         default: break;
     }
     k_xcor_pairs<<<(unsigned)((items + wpb - 1) / wpb), wpb * 32, sm, st>>>(a, items, first, n_trials);

@@ -1,5 +1,6 @@
-"""XCOR across transform lengths: every register-resident size (transforms of 64 .. 2048
-points) and the shared-memory kernel beyond, against the oracle (values within 1e-5; the
+"""XCOR across transform lengths: the shared-memory kernel (trials of at most 32 samples) and
+every register-resident size (transforms of 64 .. 4096 points, the last one split into two
+halves, tested at both ends), against the oracle (values within 1e-5; the
 reported lag attains the maximum within 1e-5)."""
 
 import math
@@ -25,7 +26,7 @@ def _need_gpu():
 
 
 # N -> transform length L = next power of two >= 2N - 1, complex size M = L / 2
-@pytest.mark.parametrize("N", [20, 40, 70, 130, 300, 600, 1500, 3000])
+@pytest.mark.parametrize("N", [20, 40, 70, 130, 300, 600, 1500, 2048, 2049, 3000, 4096])
 def test_xcor_matches_oracle_at_every_transform_length(N):
     n, K = 24, 3
     x = white_trials(100 + N, K, n, N)
@@ -47,3 +48,8 @@ def test_xcor_matches_oracle_at_every_transform_length(N):
         tau = int(lags[p])
         r = np.dot(xi[tau:], xj[:N - tau]) if tau >= 0 else np.dot(xi[:N + tau], xj[-tau:])
         assert r / math.sqrt(np.dot(xi, xi) * np.dot(xj, xj)) >= v - 1e-5, (N, i, j)
+
+
+def test_xcor_rejects_trials_longer_than_4096_samples():
+    with pytest.raises(fc.FcError):
+        fc.Session(8, 4097, 1000.0, (1.0, 50.0, 8192), "hann", fc.FC_XCOR, 2)

@@ -101,6 +101,49 @@ def _check_against_gpu_spectra(sess, K, names=SPECTRAL, I=None, J=None):
     return X, nets
 
 
+
+def _sign_disagreement(Xg, Xr, n):
+    """Fraction of (trial, pair, bin) terms whose sign of Im(X_i X_j*) differs between the
+    GPU's FP32 spectra and the FP64 oracle spectra of the same raw trials. Both signs are
+    exact for their spectra (FP32 x FP32 products are exact in FP64, one rounding keeps the
+    sign of the difference)."""
+    I, J = np.triu_indices(n, 1)
+    flips = 0
+    for k in range(Xg.shape[0]):
+        g = Xg[k].astype(np.complex128)
+        sg = np.sign((g[I] * np.conj(g[J])).imag)
+        sr = np.sign((Xr[k][I] * np.conj(Xr[k][J])).imag)
+        flips += int(np.count_nonzero(sg != sr))
+    return flips / (Xg.shape[0] * len(I) * Xg.shape[2])
+
+
+@pytest.mark.parametrize("workload", ["eeg", "meg"])
+def test_sign_disagreement_rate_against_fp64_spectra(workload, record_property):
+    """PLI, USPLI, WPLI and DSWPLI count signs of Im(X_i X_j*). On the GPU's own FP32 spectra
+    the counts are exact; against spectra computed in FP64 from the raw trials a sign can
+    differ only where Im is within FP32 rounding of zero. The rate of such terms is measured
+    and reported here (EEG: 60 channels with coupled sinusoids; MEG: 306 channels of pink
+    noise, 1000 samples, 100 bins). Measured on GB300: 0 of 885,000 terms (EEG) and 6.4e-8
+    (3 of 46.7 M terms, MEG)."""
+    if workload == "eeg":
+        x, _ = eeg_sinusoid_trials(7)
+        fs, nfft, band = 1000.0, 512, (1.0, 50.0)
+    else:
+        x, _ = meg_pink_trials(8, n_trials=10)
+        fs, nfft, band = 1000.0, 1000, (0.0, 100.0)
+    K, n, N = x.shape
+    with _session(n, N, fs, (band[0], band[1], nfft), K, mode=fc.FC_MODE_FULL) as s:
+        s.push(x)
+        Xg = window_spectra(s, K)
+    bins = O.band_bins(fs, nfft, *band)
+    Xr = np.stack([O.spectra(x[k], bins, nfft, "hann") for k in range(K)])  # [K][n][B]
+    assert Xr.shape == Xg.shape
+    rate = _sign_disagreement(Xg, Xr, n)
+    record_property("sign_disagreement_rate", rate)
+    print(f"\nsign disagreement vs FP64 spectra ({workload}, {K} trials x {n * (n - 1) // 2} pairs x "
+          f"{Xg.shape[2]} bins): {rate:.3e}")
+    assert rate < 1e-5, rate
+
 def test_full_window_eeg_all_metrics():
     x, pairs = eeg_sinusoid_trials(7)  # 60 ch x 20 trials x 500 samples
     K, n, N = x.shape

@@ -53,3 +53,26 @@ def test_xcor_matches_oracle_at_every_transform_length(N):
 def test_xcor_rejects_trials_longer_than_4096_samples():
     with pytest.raises(fc.FcError):
         fc.Session(8, 4097, 1000.0, (1.0, 50.0, 8192), "hann", fc.FC_XCOR, 2)
+
+
+@pytest.mark.parametrize("N", [2049, 4096])
+def test_xcor_streaming_pushes_at_the_split_transform_length(N):
+    """Single pushes past the window (the leaving trial's values subtracted) through the
+    4096-point transform that is split into two register halves."""
+    n, W, T = 16, 3, 6
+    x = white_trials(300 + N, T, n, N)
+    x[:, 2, :] = np.roll(x[:, 5, :], -7)
+    with fc.Session(n, N, 1000.0, (1.0, 50.0, 1 << (N - 1).bit_length()), "hann", fc.FC_XCOR, W) as s:
+        for t in range(T):
+            s.push(x[t])
+            got = s.network("XCOR", packed=True)[0]
+            val, _ = O.xcor_network(x[max(0, t + 1 - W): t + 1])
+            assert_close(got, val[np.triu_indices(n, 1)], what=f"XCOR N={N} after push {t}")
+        lags = s.xcor_lags()
+    p = int(packed_index_of(2, 5, n))
+    want = O.xcor_trial_pair(x[-1, 2].astype(np.float64), x[-1, 5].astype(np.float64))[1]
+    assert abs(want) == 7 and lags[p] == want, (lags[p], want)
+
+
+def packed_index_of(i, j, n):
+    return i * n - i * (i + 1) // 2 + (j - i - 1)

@@ -415,8 +415,8 @@ def run_sweep(args):
         for K, N in shapes:
             x = torch.from_numpy(white_trials(n + K + N, K, n, N)).cuda()
             for mname, mask in metrics.items():
-                if mname == "XCOR" and (n * (n - 1) // 2 * K * N > 2e10 or N > 4096):
-                    continue  # bounded run time; XCOR transforms are staged in shared memory (N <= 4096)
+                if mname == "XCOR" and (n * (n - 1) // 2 * K * N > 2e10 or N > 8192):
+                    continue  # bounded run time; XCOR sessions take N <= 8192 samples
                 nfft = 600 * ((N + 599) // 600)  # 600 (1 Hz bins) or the next multiple that holds the window
                 with fc.Session(n, N, 600.0, (8.0, 12.0, nfft), "hann", mask, K, mode=fc.FC_MODE_FULL,
                                 stream=stream.cuda_stream) as sess:

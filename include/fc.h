@@ -134,10 +134,12 @@ fc_status fc_config_default(fc_config* cfg);
  *   metric_mask: nonzero subset of FC_ALL_METRICS; the state of a family is allocated
  *     only when the mask holds one of its metrics (spectral: spectra ring and pair sums;
  *     COR: normalized-trial ring and its split-TF32 operand ring; XCOR: spectra ring and
- *     per-trial values), and only those metrics are computed per push;
+ *     per-trial values), and only those metrics are computed per push; XCOR needs
+ *     n_samples <= 8192 (its transforms run in registers up to 8192 complex points);
  *   window: W >= 0 trials (0 = cumulative; FC_MODE_FULL needs W >= 1);
  *   cfg: NULL for defaults. *out receives the handle; on failure *out is NULL and nothing
- *   stays allocated. Errors: FC_ERR_INVALID_ARG, FC_ERR_OUT_OF_MEMORY, FC_ERR_CUDA. */
+ *   stays allocated. Errors: FC_ERR_INVALID_ARG, FC_ERR_UNSUPPORTED (XCOR above 8192
+ *   samples), FC_ERR_OUT_OF_MEMORY, FC_ERR_CUDA. */
 fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band, fc_taper taper,
                             uint32_t metric_mask, int window, const fc_config* cfg,
                             fc_session** out);

@@ -800,7 +800,7 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
         while (L < 2 * n_samples - 1) L *= 2;
         if (L < 64) L = 64;
         s->xcor_L = L;
-        if (L > 8192) return cleanup(fail(FC_ERR_UNSUPPORTED, "XCOR supports n_samples <= 4096"));
+        if (L > 16384) return cleanup(fail(FC_ERR_UNSUPPORTED, "XCOR supports n_samples <= 8192"));
         const int M = L / 2;
         std::vector<float2> xt(M);
         for (int k = 0; k < M; ++k) {

@@ -183,40 +183,43 @@ __global__ void k_xcor_pairs(XcorArgs a, long long n_items, long long first_tria
     }
 }
 
-// Register form for transforms of M = 32 E 2^S complex points (E = 2 .. 64, S = 0 or 1:
-// trials up to 4,096 samples). The inverse transform runs as radix-2 decimation in
-// frequency on natural-order input. With S = 1 the first stage splits it into two
-// independent halves of 32 E points (top: u + v, the even outputs; bottom: (u - v) w, the
-// odd outputs), transformed one after the other in the same registers. Within a transform
-// of 32 E points, lane l first holds elements l + 32 r, r < E: spans of 32 or more pair
-// registers of the same lane; spans from 16 down to E (only when E <= 16) pair lanes
-// through __shfl_xor_sync. One transpose through this warp's shared-memory buffer (a pad
-// slot per E elements keeps both directions free of bank conflicts) then gives lane l the E
-// consecutive elements l E + q, so the remaining spans (below E and below 32) pair
-// registers of the same lane again, with twiddles that are the same for every lane. The
-// output lands in bit-reversed order, which the scan over lags reads through the bit
-// reversal of each position.
+// Register form for transforms of M = 32 E 2^S complex points (E = 2 .. 64, S = 0 .. 2:
+// trials up to 8,192 samples). The inverse transform runs as radix-2 decimation in
+// frequency on natural-order input. With S >= 1 the first S stages split it into 2^S
+// independent blocks of 32 E points (S = 1: top u + v, the even outputs; bottom (u - v) w,
+// the odd outputs; S = 2 repeats the split on both halves, block b holding the outputs
+// 4 k + bitrev2(b)); the blocks are transformed one after the other in the same registers,
+// each forming its inputs from the product spectrum again. Within a block, lane l first
+// holds elements l + 32 r, r < E: spans of 32 or more pair registers of the same lane;
+// spans from 16 down to E (only when E <= 16) pair lanes through __shfl_xor_sync. One
+// transpose through this warp's shared-memory buffer (a pad slot per E elements keeps both
+// directions free of bank conflicts) then gives lane l the E consecutive elements l E + q,
+// so the remaining spans (below E and below 32) pair registers of the same lane again, with
+// twiddles that are the same for every lane. The output lands in bit-reversed order, which
+// the scan over lags reads through the bit reversal of each position.
 template <int E, int S>
 __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_items, long long first_trial,
                                                        int n_trials) {
     constexpr int MS = 32 * E;  // points of one register transform
     constexpr int M = MS << S;  // points of the whole complex transform
-    // dynamic shared memory: stw[M] = tw[k] = e^{-2 pi i k / L}; sth[M] = the butterflies'
-    // twiddles by stage, span h at sth[h + t] = tw[t M / h], t < h (a stage's lanes read
-    // consecutive entries or one entry each, broadcast: no bank conflicts); then one
-    // transpose buffer of MS + MS / E slots per warp
+    // dynamic shared memory: stw[M] = tw[k] = e^{-2 pi i k / L} (S < 2 only); sth[M] = the
+    // butterflies' twiddles by stage, span h at sth[h + t] = tw[t M / h], t < h (a stage's
+    // lanes read consecutive entries or one entry each, broadcast: no bank conflicts); then
+    // one transpose buffer of MS + MS / E slots per warp. With S = 2 the table stw would not
+    // fit beside the rest: tw[2t] = sth[M / 2 + t] and tw[2t + 1] = tw[2t] tw[1].
     extern __shared__ float2 dsm[];
     float2* stw = dsm;
-    float2* sth = dsm + M;
+    float2* sth = dsm + (S < 2 ? M : 0);
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        stw[k] = a.tw[k];
+        if (S < 2) stw[k] = a.tw[k];
         if (k > 0) {
             const int h = 1 << (31 - __clz(k));
             sth[k] = a.tw[(k - h) * (M / h)];
         }
     }
+    const float2 tw1 = a.tw[1];
     __syncthreads();
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
@@ -235,7 +238,11 @@ __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_
         const float2 pm = cconj(cmul(Zi[M - k], cconj(Zj[M - k])));
         const float2 e = make_float2(0.5f * __fadd_rn(pk.x, pm.x), 0.5f * __fadd_rn(pk.y, pm.y));
         const float2 dd = csub(pk, pm);
-        const float2 w = cconj(stw[k]);  // e^{+2 pi i k / L}
+        float2 w;  // e^{+2 pi i k / L}
+        if (S < 2)
+            w = cconj(stw[k]);
+        else
+            w = cconj((k & 1) ? cmul(sth[M / 2 + (k >> 1)], tw1) : sth[M / 2 + (k >> 1)]);
         const float2 o = cmul(make_float2(0.5f * dd.x, 0.5f * dd.y), w);
         return make_float2(__fsub_rn(e.x, o.y), __fadd_rn(e.y, o.x));
     };
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_
     int best_tau = 0;
     const float invM = 1.0f / (float)M;
     const int L = 2 * M;
-    float2* tb = dsm + 2 * M + (size_t)wib * (MS + MS / E);
+    float2* tb = sth + M + (size_t)wib * (MS + MS / E);
 #pragma unroll 1
     for (int half = 0; half < (1 << S); ++half) {
         float2 x[E];
@@ -253,9 +260,20 @@ __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_
             const int e = lane + 32 * r;
             if (S == 0) {
                 x[r] = prod(e);
-            } else {  // first stage, span MS: top half u + v, bottom half (u - v) e^{+2 pi i e / M}
+            } else if (S == 1) {  // first stage, span MS: top half u + v, bottom half (u - v) e^{+2 pi i e / M}
                 const float2 u = prod(e), v = prod(e + MS);
                 x[r] = half == 0 ? cadd(u, v) : cmul(csub(u, v), cconj(sth[MS + e]));
+            } else {  // stages of span 2 MS (top: half < 2) and MS (second split: half odd)
+                const float2 p0 = prod(e), p1 = prod(e + MS), p2 = prod(e + 2 * MS), p3 = prod(e + 3 * MS);
+                float2 t0, t1;
+                if (half < 2) {
+                    t0 = cadd(p0, p2);
+                    t1 = cadd(p1, p3);
+                } else {
+                    t0 = cmul(csub(p0, p2), cconj(sth[2 * MS + e]));
+                    t1 = cmul(csub(p1, p3), cconj(sth[3 * MS + e]));
+                }
+                x[r] = (half & 1) == 0 ? cadd(t0, t1) : cmul(csub(t0, t1), cconj(sth[MS + e]));
             }
         }
         // inverse transform (e^{+2 pi i ...}), decimation in frequency
@@ -306,11 +324,12 @@ __global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_
                 x[q + h] = cmul(csub(u, v), w);
             }
         }
-        // position e holds this half's output bitrev(e), i.e. y[m] with m = 2^S bitrev(e) + half;
-        // r[2m] = Re y[m] / M, r[2m+1] = Im y[m] / M
+        // position e holds this block's output bitrev(e), i.e. y[m] with m = 2^S bitrev(e) +
+        // bitrev_S(block); r[2m] = Re y[m] / M, r[2m+1] = Im y[m] / M
+        const int boff = S == 2 ? ((half & 1) << 1) | (half >> 1) : half;
 #pragma unroll
         for (int r = 0; r < E; ++r) {
-            const int m = (bitrev(lane * E + r, bits) << S) + half;
+            const int m = (bitrev(lane * E + r, bits) << S) + boff;
 #pragma unroll
             for (int part = 0; part < 2; ++part) {
                 const int idx = 2 * m + part;
@@ -375,8 +394,8 @@ __global__ void k_xcor_update(XcorArgs a) {
 template <int E, int S>
 cudaError_t launch_pairs_reg(const XcorArgs& a, long long items, long long first, int n_trials, cudaStream_t st) {
     constexpr int MS = 32 * E;
-    // twiddle tables (2 M) and 8 warps x (MS + MS / E) transpose slots
-    const int dyn = (2 * (MS << S) + 8 * (MS + MS / E)) * (int)sizeof(float2);
+    // twiddle tables (2 M, or M for S = 2) and 8 warps x (MS + MS / E) transpose slots
+    const int dyn = ((S < 2 ? 2 : 1) * (MS << S) + 8 * (MS + MS / E)) * (int)sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_xcor_pairs_reg<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
     k_xcor_pairs_reg<E, S><<<(unsigned)((items + 7) / 8), 256, dyn, st>>>(a, items, first, n_trials);
@@ -386,7 +405,7 @@ cudaError_t launch_pairs_reg(const XcorArgs& a, long long items, long long first
 cudaError_t launch_xcor_spectra(const XcorArgs& a, cudaStream_t st) {
     const long long warps = (long long)(a.count - a.write_from) * a.n;
     if (warps <= 0) return cudaSuccess;
-    const int wpb = 4;
+    const int wpb = a.L / 2 > 4096 ? 2 : 4;  // M float2 per warp: 128 KB per block at M = 8192
     const size_t sm = (size_t)wpb * (a.L / 2) * sizeof(float2);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_xcor_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -409,14 +428,8 @@ cudaError_t launch_xcor_pairs(const XcorArgs& a, cudaStream_t st) {
         first = a.count - a.W;
     }
     const long long items = a.P * n_trials;
-    const int wpb = 4;
-    const size_t sm = (size_t)wpb * (a.L / 2) * sizeof(float2);
     const int M = a.L / 2;
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_xcor_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-    }
-    // register form for M = 64 .. 4096 (8 warps per block), shared-memory form otherwise
+    // register form for M = 64 .. 8192 (8 warps per block), shared-memory form otherwise
     switch (M) {
         case 64: return launch_pairs_reg<2, 0>(a, items, first, n_trials, st);
         case 128: return launch_pairs_reg<4, 0>(a, items, first, n_trials, st);
@@ -425,7 +438,14 @@ cudaError_t launch_xcor_pairs(const XcorArgs& a, cudaStream_t st) {
         case 1024: return launch_pairs_reg<32, 0>(a, items, first, n_trials, st);
         case 2048: return launch_pairs_reg<64, 0>(a, items, first, n_trials, st);
         case 4096: return launch_pairs_reg<64, 1>(a, items, first, n_trials, st);
+        case 8192: return launch_pairs_reg<64, 2>(a, items, first, n_trials, st);
         default: break;
+    }
+    const int wpb = 4;
+    const size_t sm = (size_t)wpb * M * sizeof(float2);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_xcor_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
     }
     k_xcor_pairs<<<(unsigned)((items + wpb - 1) / wpb), wpb * 32, sm, st>>>(a, items, first, n_trials);
     return cudaGetLastError();

@@ -1,6 +1,6 @@
 """XCOR across transform lengths: the shared-memory kernel (trials of at most 32 samples) and
-every register-resident size (transforms of 64 .. 4096 points, the last one split into two
-halves, tested at both ends), against the oracle (values within 1e-5; the
+every register-resident size (transforms of 64 .. 8192 points; 4096 points split into two
+blocks, 8192 into four, each tested at both ends), against the oracle (values within 1e-5; the
 reported lag attains the maximum within 1e-5)."""
 
 import math
@@ -26,7 +26,7 @@ def _need_gpu():
 
 
 # N -> transform length L = next power of two >= 2N - 1, complex size M = L / 2
-@pytest.mark.parametrize("N", [20, 40, 70, 130, 300, 600, 1500, 2048, 2049, 3000, 4096])
+@pytest.mark.parametrize("N", [20, 40, 70, 130, 300, 600, 1500, 2048, 2049, 3000, 4096, 4097, 6000, 8192])
 def test_xcor_matches_oracle_at_every_transform_length(N):
     n, K = 24, 3
     x = white_trials(100 + N, K, n, N)
@@ -50,15 +50,15 @@ def test_xcor_matches_oracle_at_every_transform_length(N):
         assert r / math.sqrt(np.dot(xi, xi) * np.dot(xj, xj)) >= v - 1e-5, (N, i, j)
 
 
-def test_xcor_rejects_trials_longer_than_4096_samples():
+def test_xcor_rejects_trials_longer_than_8192_samples():
     with pytest.raises(fc.FcError):
-        fc.Session(8, 4097, 1000.0, (1.0, 50.0, 8192), "hann", fc.FC_XCOR, 2)
+        fc.Session(8, 8193, 1000.0, (1.0, 50.0, 16384), "hann", fc.FC_XCOR, 2)
 
 
-@pytest.mark.parametrize("N", [2049, 4096])
+@pytest.mark.parametrize("N", [2049, 4096, 4097, 8192])
 def test_xcor_streaming_pushes_at_the_split_transform_length(N):
     """Single pushes past the window (the leaving trial's values subtracted) through the
-    4096-point transform that is split into two register halves."""
+    transforms split into two (4096 points) and four (8192 points) register blocks."""
     n, W, T = 16, 3, 6
     x = white_trials(300 + N, T, n, N)
     x[:, 2, :] = np.roll(x[:, 5, :], -7)

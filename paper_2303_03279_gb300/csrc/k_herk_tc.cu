@@ -201,6 +201,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
                 }
                 __syncwarp();
             }
+            // 1/sqrt(PSD) of this thread's column node, fetched while the MMAs run
+            const float inv_j = (b == 0 && j < a.n) ? a.inv_psd[(size_t)f * a.n + j] : 0.f;
             // warp-uniform outcome: the TMEM loads below are warp-collective
             const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accf[b], accf_ph[b]) ? 1 : 0) != 0;
             accf_ph[b] ^= 1;
@@ -210,26 +212,41 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
             }
             fence_after();
             const uint32_t col = (uint32_t)(b * 2 * TILE);
-            const float inv_j = (b == 0 && j < a.n) ? a.inv_psd[(size_t)f * a.n + j] : 0.f;
             float* out = a.bins_out + (size_t)f * 3 * a.P;
-            for (int i0 = rhalf * (TILE / 2); i0 < (rhalf + 1) * (TILE / 2); i0 += 16) {
-                float vre[16], vim[16];
-                tmem_ld16(lane_base + col + i0, vre);
-                tmem_ld16(lane_base + col + TILE + i0, vim);
-                if (j >= a.n) continue;
+            // this warp's 64 row nodes: all eight loads (re and im of 4 x 16 columns) in flight
+            // at once, one wait
+            const int ibase = rhalf * (TILE / 2);
+            uint32_t rre[4][16], rim[4][16];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int i = ta * TILE + i0 + q;
-                    if (j <= i || i >= a.n) continue;
-                    const long long p = packed_index(i, j, a.n);
-                    if (b == 0) {
-                        const float inv_i = sinv[i0 + q];
-                        const float r = __fmul_rn(__fmul_rn(vre[q], inv_i), inv_j);
-                        const float m = __fmul_rn(__fmul_rn(vim[q], inv_i), inv_j);
-                        out[p] = sqrtf(__fmaf_rn(r, r, __fmul_rn(m, m)));
-                        out[a.P + p] = m;
-                    } else {
-                        out[2 * a.P + p] = __fmul_rn(sqrtf(__fmaf_rn(vre[q], vre[q], __fmul_rn(vim[q], vim[q]))), inv_K);
+            for (int s4 = 0; s4 < 4; ++s4) {
+                tmem_ld16_issue(lane_base + col + ibase + 16 * s4, rre[s4]);
+                tmem_ld16_issue(lane_base + col + TILE + ibase + 16 * s4, rim[s4]);
+            }
+            tmem_wait_ld();
+#pragma unroll
+            for (int s4 = 0; s4 < 4; ++s4) {
+                tmem_keep(rre[s4]);
+                tmem_keep(rim[s4]);
+            }
+            if (j < a.n) {
+                // packed index of (i, j) for i = ta TILE + ibase, then p(i + 1) = p(i) + n - i - 2
+                int i = ta * TILE + ibase;
+                long long p = packed_index(i, j, a.n);
+#pragma unroll
+                for (int s4 = 0; s4 < 4; ++s4) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q, p += a.n - i - 2, ++i) {
+                        if (j <= i || i >= a.n) continue;
+                        const float vre = __uint_as_float(rre[s4][q]), vim = __uint_as_float(rim[s4][q]);
+                        if (b == 0) {
+                            const float inv_i = sinv[ibase + 16 * s4 + q];
+                            const float r = __fmul_rn(__fmul_rn(vre, inv_i), inv_j);
+                            const float m = __fmul_rn(__fmul_rn(vim, inv_i), inv_j);
+                            out[p] = sqrtf(__fmaf_rn(r, r, __fmul_rn(m, m)));
+                            out[a.P + p] = m;
+                        } else {
+                            out[2 * a.P + p] = __fmul_rn(sqrtf(__fmaf_rn(vre, vre, __fmul_rn(vim, vim))), inv_K);
+                        }
                     }
                 }
             }
@@ -247,9 +264,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
 }
 
 // ------------------------------------------------------------------ operand packing
-// One thread per 16-byte row chunk of a core matrix: operand kind, tile, bin, node row m,
-// 16-byte K unit. Elements k of the 2K inner dimension: k < K -> trial k, first half;
-// K <= k < 2K -> trial k - K, second half; beyond 2K -> 0.
+// One thread per 16-byte row chunk of a core matrix position (tile, bin, node row m, 16-byte
+// K unit), writing that chunk of all four operand kinds from one read of the spectra.
+// Elements k of the 2K inner dimension: k < K -> trial k, first half; K <= k < 2K -> trial
+// k - K, second half; beyond 2K -> 0.
 //   XR = [Re X | Im X], XI = [Im X | -Re X], UR = [Re u | Im u], UI = [Im u | -Re u]
 __device__ __forceinline__ float2 phasor_of_x(float2 X) {
     float m2 = __fmaf_rn(X.x, X.x, __fmul_rn(X.y, X.y));
@@ -257,10 +275,24 @@ __device__ __forceinline__ float2 phasor_of_x(float2 X) {
     return make_float2(__fmul_rn(X.x, r), __fmul_rn(X.y, r));
 }
 
-__device__ __forceinline__ float op_value(int kind, float2 X, int part) {
-    if (kind >= 2) X = phasor_of_x(X);
-    if (kind == 0 || kind == 2) return part ? X.y : X.x;
-    return part ? -X.x : X.y;
+__device__ __forceinline__ uint4 pack_chunk(const float (&v)[8], int per16, int ab_format) {
+    if (ab_format == 2) {  // TF32: round to nearest (ties away), stored in 32-bit words
+        uint32_t t[4];
+        for (int q = 0; q < 4; ++q) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t[q]) : "f"(v[q]));
+        return make_uint4(t[0], t[1], t[2], t[3]);
+    }
+    unsigned short h[8];
+    for (int q = 0; q < 8; ++q) {
+        const float x = q < per16 ? v[q] : 0.f;
+        if (ab_format == 1) {
+            __nv_bfloat16 b = __float2bfloat16_rn(x);
+            h[q] = *reinterpret_cast<unsigned short*>(&b);
+        } else {
+            __half b = __float2half_rn(x);
+            h[q] = *reinterpret_cast<unsigned short*>(&b);
+        }
+    }
+    return make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
 }
 
 __global__ void k_pack_operands(PackArgs a) {
@@ -272,54 +304,40 @@ __global__ void k_pack_operands(PackArgs a) {
     const int esize = a.ab_format == 2 ? 4 : 2;
     const int per16 = 16 / esize;                 // elements per 16-byte unit
     const long long units_per_block = (long long)TILE * 8;  // 128 rows x 8 units of 16 bytes
-    const long long total = (long long)a.ntiles * a.B * 4 * a.nchunks * units_per_block;
+    const long long total = (long long)a.ntiles * a.B * a.nchunks * units_per_block;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         long long rest = e;
         const int r = (int)(rest % 8); rest /= 8;       // row within core matrix
         const int kc = (int)(rest % 8); rest /= 8;      // core matrix along K within the chunk
         const int m8 = (int)(rest % 16); rest /= 16;    // 8-row group
         const int ch = (int)(rest % a.nchunks); rest /= a.nchunks;
-        const int kind = (int)(rest % 4); rest /= 4;
         const int f = (int)(rest % a.B); rest /= a.B;
         const int tile = (int)rest;
         const int m = m8 * 8 + r;
         const int node = tile * TILE + m;
         const int k0 = (ch * 8 + kc) * per16;           // first inner index of this 16-byte unit
-        float v[8];
+        float v[4][8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int k = k0 + q;
-            float val = 0.f;
+            v[0][q] = v[1][q] = v[2][q] = v[3][q] = 0.f;  // padding: +0 exactly
             if (q < per16 && node < a.n && k < 2 * K) {
                 const int part = k >= K;
                 const long long trial = start + (part ? k - K : k);
                 const float2 X = a.ring[((size_t)(trial % a.slots) * a.B + f) * a.n + node];
-                val = op_value(kind, X, part);
+                const float2 u = phasor_of_x(X);
+                v[0][q] = part ? X.y : X.x;   // XR
+                v[1][q] = part ? -X.x : X.y;  // XI
+                v[2][q] = part ? u.y : u.x;   // UR
+                v[3][q] = part ? -u.x : u.y;  // UI
             }
-            v[q] = val;
         }
-        unsigned char* dst = a.ops + ((((size_t)tile * a.B + f) * 4 + kind) * a.nchunks + ch) * (size_t)CHUNK_BYTES +
-                             (size_t)(m8 * 8 + kc) * 128 + r * 16;
-        uint4 w;
-        if (a.ab_format == 2) {  // TF32: round to nearest (ties away), stored in 32-bit words
-            uint32_t t[4];
-            for (int q = 0; q < 4; ++q) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t[q]) : "f"(v[q]));
-            w = make_uint4(t[0], t[1], t[2], t[3]);
-        } else {
-            unsigned short h[8];
-            for (int q = 0; q < 8; ++q) {
-                const float x = q < per16 ? v[q] : 0.f;
-                if (a.ab_format == 1) {
-                    __nv_bfloat16 b = __float2bfloat16_rn(x);
-                    h[q] = *reinterpret_cast<unsigned short*>(&b);
-                } else {
-                    __half b = __float2half_rn(x);
-                    h[q] = *reinterpret_cast<unsigned short*>(&b);
-                }
-            }
-            w = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+#pragma unroll
+        for (int kind = 0; kind < 4; ++kind) {
+            unsigned char* dst = a.ops + ((((size_t)tile * a.B + f) * 4 + kind) * a.nchunks + ch) * (size_t)CHUNK_BYTES +
+                                 (size_t)(m8 * 8 + kc) * 128 + r * 16;
+            *reinterpret_cast<uint4*>(dst) = pack_chunk(v[kind], per16, a.ab_format);
         }
-        *reinterpret_cast<uint4*>(dst) = w;
     }
 }
 

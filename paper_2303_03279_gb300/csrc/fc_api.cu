@@ -310,6 +310,29 @@ fc_status stage_time_metrics(fc_session* s, const float* x, int count, int write
     return FC_OK;
 }
 
+// Bin groups of the tensor-core full window: units are (128-node tile pair, group of
+// consecutive selected bins), one CTA walks a unit's bins in order. Chooses the number of
+// groups g <= cap minimizing the busiest CTA's bins (ceil(units / SMs) rounds of a group's
+// bins, ~10 us per tile pair and bin) plus the band-sum planes' traffic (zero fill,
+// reductions' write-back and the final sum: ~12 B per pair, metric and group at ~5 TB/s);
+// every group holds at least one bin.
+void herk_groups(long long ntp, int nsel, int sms, long long P, int cap, int& groups, int& group_bins) {
+    groups = 1;
+    group_bins = nsel;
+    double best = 1e300;
+    for (int g = 1; g <= std::min(nsel, std::max(1, cap)); ++g) {
+        const int gb = (nsel + g - 1) / g;
+        if ((nsel + gb - 1) / gb != g) continue;  // a group would be empty
+        const long long rounds = (ntp * g + sms - 1) / sms;
+        const double t = (double)rounds * gb * 10e-6 + (double)g * 3 * P * 12 / 5e12;
+        if (t < best) {
+            best = t;
+            groups = g;
+            group_bins = gb;
+        }
+    }
+}
+
 // Spectral pair sums over the whole window (bulk push, re-sum, full mode).
 fc_status stage_window(fc_session* s, int count, bool write_acc) {
     NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, 1, s->ctrl, count};
@@ -334,7 +357,7 @@ fc_status stage_window(fc_session* s, int count, bool write_acc) {
         ha.tile_a = s->tile_a128;
         ha.tile_b = s->tile_b128;
         ha.inv_psd = s->inv_psd;
-        ha.bins_out = s->herk_bins;
+        ha.part = s->herk_part;
         ha.net = s->net;
         ha.n = s->n;
         ha.B = s->B;
@@ -350,7 +373,10 @@ fc_status stage_window(fc_session* s, int count, bool write_acc) {
         ha.fsel1 = s->sel1;
         ha.ctrl = s->ctrl;
         if (s->mask & (FC_COH | FC_IMAGCOHY | FC_PLV)) {
+            herk_groups(s->ntp128, s->sel1 - s->sel0, s->num_sms, (long long)s->P, s->herk_gcap, ha.groups,
+                        ha.group_bins);
             LAUNCH(FC_K_HERK_TC, launch_pack_operands(pk, s->stream));
+            CK(cudaMemsetAsync(s->herk_part, 0, (size_t)ha.groups * 3 * s->P * sizeof(float), s->stream));
             LAUNCH(FC_K_HERK_TC, launch_herk_tc(ha, s->stream));
             LAUNCH(FC_K_BAND_REDUCE, launch_herk_band(ha, s->stream));
         }
@@ -782,7 +808,9 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
             TRY(upload(s, s->tile_a128, ta.data(), ta.size() * sizeof(unsigned short)));
             TRY(upload(s, s->tile_b128, tb.data(), tb.size() * sizeof(unsigned short)));
             TRY(alloc_zero(s, (size_t)s->nt128 * B * 4 * s->nchunks * herk_chunk_bytes(), &s->ops));
-            TRY(alloc_zero(s, (size_t)B * 3 * s->P, &s->herk_bins));
+            int gb;
+            herk_groups(s->ntp128, B, s->num_sms, (long long)s->P, B, s->herk_gcap, gb);
+            TRY(alloc_zero(s, (size_t)s->herk_gcap * 3 * s->P, &s->herk_part));
         }
         if (max_groups > 1) TRY(alloc_zero(s, (size_t)max_groups * 7 * s->P, &s->partial));
     }  // spectral state

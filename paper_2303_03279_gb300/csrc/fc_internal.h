@@ -127,7 +127,8 @@ struct fc_session {
     unsigned char* ops;     // packed operands [nt128][B][4][nchunks][16 KB]
     unsigned char* cor_ops; // COR split-TF32 operand ring [slots][cor_nt][cor_nchunks][2][16 KB]
     int cor_nt, cor_ntp, cor_nchunks;
-    float* herk_bins;       // [B][3][P] per-bin COH, IMAGCOHY, PLV
+    float* herk_part;       // [herk_gcap][3][P] band sums of COH, IMAGCOHY, PLV per bin group
+    int herk_gcap;          // bin groups the band-sum planes are allocated for
     size_t device_bytes;
 
     // measurement
@@ -232,9 +233,10 @@ struct HerkArgs {
     const unsigned short* tile_a;  // 128-node tile pairs
     const unsigned short* tile_b;
     const float* inv_psd;
-    float* bins_out;      // [B][3][P] per-bin COH, IMAGCOHY, PLV
+    float* part;          // [groups][3][P] band sums of COH, IMAGCOHY, PLV, zeroed before the launch
     float* net;           // [FC_NMETRIC][P]
     int n, B, ntp, nchunks, W, count, ab_format, grid_ctas;
+    int groups, group_bins;  // the selected bins in groups of group_bins (the last may be shorter)
     long long P;
     uint32_t mask;
     int fsel0, fsel1;     // bins entering the band average

@@ -8,8 +8,11 @@
 //   Re S_csd = A_r(rows i) A_r(rows j)^T,   Im S_csd = A_i(rows i) A_r(rows j)^T,
 // and the same with U for the phasor sums: four real GEMMs of 128 x 128 x 2K per
 // (128-node tile pair, bin), kind::f16 (BF16 or FP16 operands) or kind::tf32, FP32
-// accumulation. COH, IMAGCOHY and PLV of the bin are finalized from TMEM and written per
-// bin; the band average follows in a small reduction kernel. The non-linear sums
+// accumulation. COH, IMAGCOHY and PLV of the bin are finalized from TMEM and added to the
+// band sums of the unit's bin group with fire-and-forget reductions (red.global.add): one CTA
+// walks all bins of a (tile pair, bin group) unit in order and each sum has one owner thread,
+// so the additions land in bin order and the sums are reproducible. A small kernel adds the
+// groups and scales by the number of bins. The non-linear sums
 // (signs, |Im|, Im^2) cannot be contracted and run on the CUDA cores (k_nonlin).
 //
 // Operand layout (built by k_pack_operands from the ring of FP32 spectra): for each
@@ -40,6 +43,11 @@ constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 512 + EPI_WARPS * 512;  // + b
 constexpr uint32_t TMEM_COLS = 512;    // 2 phase buffers x 2 accumulators x 128 FP32 columns
 constexpr int THREADS = 32 * EPI_WARPS + 32;  // warps 0-7: epilogue; warp 8: loads + MMAs
 
+// *addr += v as a fire-and-forget reduction (no value returned, nothing to wait for)
+__device__ __forceinline__ void red_add(float* addr, float v) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(v) : "memory");
+}
+
 __device__ __forceinline__ long long packed_index(int i, int j, int n) {
     return (long long)i * n - (long long)i * (i + 1) / 2 + (j - i - 1);
 }
@@ -48,7 +56,22 @@ __device__ __forceinline__ const unsigned char* op_block(const HerkArgs& a, int 
     return a.ops + ((((size_t)tile * a.B + f) * 4 + kind) * a.nchunks + chunk) * (size_t)CHUNK_BYTES;
 }
 
-// Per (128-node tile pair, bin) unit, two phases, each a pair of transposed products
+// Work of one CTA: units u = blockIdx.x + k gridDim.x of ntp x groups (tile pair u / groups,
+// bin group u % groups), each over its bins in order, each bin in two phases.
+struct HerkSeq {
+    int u, f, fend;
+};
+__device__ __forceinline__ void seq_unit(const HerkArgs& a, HerkSeq& s, int u) {
+    s.u = u;
+    const int g = u % a.groups;
+    s.f = a.fsel0 + g * a.group_bins;
+    s.fend = min(a.fsel1, s.f + a.group_bins);
+}
+__device__ __forceinline__ void seq_next_bin(const HerkArgs& a, HerkSeq& s) {
+    if (++s.f >= s.fend) seq_unit(a, s, s.u + (int)gridDim.x);
+}
+
+// Per (128-node tile pair, bin) step, two phases, each a pair of transposed products
 // D^T[j][i] (TMEM lane = column node j of tile b, TMEM column = row node i of tile a):
 //   phase A (CSD):     Re = XR_b XR_a^T,  Im = XR_b XI_a^T   -> COH, IMAGCOHY
 //   phase B (phasors): Re = UR_b UR_a^T,  Im = UR_b UI_a^T   -> PLV
@@ -63,7 +86,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     FcCtrl* c = const_cast<FcCtrl*>(a.ctrl);
     if (c->bad) return;
-    const int units = a.ntp * a.B;
+    const int units = a.ntp * a.groups;
     if ((int)blockIdx.x >= units) return;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);  // [NSTAGE]
     uint64_t* freeb = full + NSTAGE;                                             // [NSTAGE]
@@ -99,9 +122,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
     const long long wend = c->pushed + a.count;
     const int K = (int)(wend - ((a.W > 0 && wend > a.W) ? wend - a.W : 0));
     const float inv_K = 1.0f / (float)K;
-    // this CTA's units: blockIdx.x + k gridDim.x; its phase sequence: 2 per unit
-    const int my_units = (units - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int nphase = 2 * my_units;
+    // this CTA's phase sequence: 2 per bin of each of its units
+    int nphase = 0;
+    for (int u = (int)blockIdx.x; u < units; u += (int)gridDim.x) {
+        HerkSeq t;
+        seq_unit(a, t, u);
+        nphase += 2 * (t.fend - t.f);
+    }
     bool failed = false;
 
     if (warp == EPI_WARPS) {
@@ -113,6 +140,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
             for (int s = 0; s < NSTAGE; ++s) full_ph[s] = free_ph[s] = 0;
             uint32_t acce_ph[2] = {0, 0};
             long long loads = 0;
+            HerkSeq ls;  // unit and bin of the phase being loaded
+            seq_unit(a, ls, (int)blockIdx.x);
+            long long lph = 0;
             auto issue_load = [&]() {  // chunk `loads` of the sequence into stage loads % NSTAGE
                 if (loads >= nchunk_total) return;
                 const int st = (int)(loads % NSTAGE);
@@ -122,8 +152,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
                 }
                 const long long ph = loads / a.nchunks;
                 const int ch = (int)(loads % a.nchunks);
-                const int u = (int)blockIdx.x + (int)(ph >> 1) * (int)gridDim.x;
-                const int tp = u / a.B, f = u % a.B;
+                for (; lph < ph; ++lph)
+                    if (lph & 1) seq_next_bin(a, ls);  // after phase B: the next bin
+                const int tp = ls.u / a.groups, f = ls.f;
                 const int ta = a.tile_a[tp], tb = a.tile_b[tp];
                 const int k0 = (ph & 1) ? 2 : 0;  // phase A: X operands, phase B: U operands
                 unsigned char* dst = smem + st * STAGE_BYTES;
@@ -187,10 +218,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
         const int quarter = warp & 3, rhalf = warp >> 2;  // TMEM lanes 32 quarter ..; rows 64 rhalf ..
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         float* sinv = sinv_all + warp * TILE;  // this warp's copy: no barrier across warps
+        HerkSeq es;
+        seq_unit(a, es, (int)blockIdx.x);
         for (int ph = 0; ph < nphase; ++ph) {
             const int b = ph & 1;
-            const int u = (int)blockIdx.x + (ph >> 1) * (int)gridDim.x;
-            const int tp = u / a.B, f = u % a.B;
+            if (ph > 0 && b == 0) seq_next_bin(a, es);
+            const int tp = es.u / a.groups, f = es.f;
             const int ta = a.tile_a[tp], tb = a.tile_b[tp];
             const int j = tb * TILE + quarter * 32 + (tid & 31);  // this thread's TMEM lane: column node j
             if (b == 0) {  // 1/sqrt(PSD) of tile a's nodes, staged by this warp for itself
@@ -212,7 +245,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
             }
             fence_after();
             const uint32_t col = (uint32_t)(b * 2 * TILE);
-            float* out = a.bins_out + (size_t)f * 3 * a.P;
+            float* out = a.part + (size_t)(es.u % a.groups) * 3 * a.P;  // this group's band sums
             // this warp's 64 row nodes: all eight loads (re and im of 4 x 16 columns) in flight
             // at once, one wait
             const int ibase = rhalf * (TILE / 2);
@@ -242,10 +275,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
                             const float inv_i = sinv[ibase + 16 * s4 + q];
                             const float r = __fmul_rn(__fmul_rn(vre, inv_i), inv_j);
                             const float m = __fmul_rn(__fmul_rn(vim, inv_i), inv_j);
-                            out[p] = sqrtf(__fmaf_rn(r, r, __fmul_rn(m, m)));
-                            out[a.P + p] = m;
+                            red_add(out + p, sqrtf(__fmaf_rn(r, r, __fmul_rn(m, m))));
+                            red_add(out + a.P + p, m);
                         } else {
-                            out[2 * a.P + p] = __fmul_rn(sqrtf(__fmaf_rn(vre, vre, __fmul_rn(vim, vim))), inv_K);
+                            red_add(out + 2 * a.P + p, __fmul_rn(sqrtf(__fmaf_rn(vre, vre, __fmul_rn(vim, vim))), inv_K));
                         }
                     }
                 }
@@ -341,7 +374,7 @@ __global__ void k_pack_operands(PackArgs a) {
     }
 }
 
-// Band average of the per-bin COH, IMAGCOHY, PLV values.
+// Band average of COH, IMAGCOHY, PLV: the bin groups' sums added in group order, times 1/bins.
 __global__ void k_herk_band(HerkArgs a) {
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
@@ -352,7 +385,7 @@ __global__ void k_herk_band(HerkArgs a) {
         const int mi = m == 0 ? MI_COH : m == 1 ? MI_IMAGCOHY : MI_PLV;
         if (!(a.mask & (1u << mi))) continue;
         float s = 0.f;
-        for (int f = a.fsel0; f < a.fsel1; ++f) s = __fadd_rn(s, a.bins_out[((size_t)f * 3 + m) * a.P + p]);
+        for (int g = 0; g < a.groups; ++g) s = __fadd_rn(s, a.part[((size_t)g * 3 + m) * a.P + p]);
         a.net[(size_t)mi * a.P + p] = __fmul_rn(s, invB);
     }
 }
@@ -365,7 +398,7 @@ cudaError_t launch_pack_operands(const PackArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_herk_tc(const HerkArgs& a, cudaStream_t st) {
-    const int units = a.ntp * a.B;
+    const int units = a.ntp * a.groups;
     const int ctas = units < a.grid_ctas ? units : a.grid_ctas;
     cudaError_t e;
     if (a.ab_format == 2) {

@@ -313,9 +313,9 @@ fc_status stage_time_metrics(fc_session* s, const float* x, int count, int write
 // Bin groups of the tensor-core full window: units are (128-node tile pair, group of
 // consecutive selected bins), one CTA walks a unit's bins in order. Chooses the number of
 // groups g <= cap minimizing the busiest CTA's bins (ceil(units / SMs) rounds of a group's
-// bins, ~10 us per tile pair and bin) plus the band-sum planes' traffic (zero fill,
-// reductions' write-back and the final sum: ~12 B per pair, metric and group at ~5 TB/s);
-// every group holds at least one bin.
+// bins, ~17 us per tile pair and bin as measured on GB300) plus the band-sum planes' traffic
+// (write-back and final sum: ~8 B per pair, metric and group at ~6 TB/s); every group holds
+// at least one bin.
 void herk_groups(long long ntp, int nsel, int sms, long long P, int cap, int& groups, int& group_bins) {
     groups = 1;
     group_bins = nsel;
@@ -324,7 +324,7 @@ void herk_groups(long long ntp, int nsel, int sms, long long P, int cap, int& gr
         const int gb = (nsel + g - 1) / g;
         if ((nsel + gb - 1) / gb != g) continue;  // a group would be empty
         const long long rounds = (ntp * g + sms - 1) / sms;
-        const double t = (double)rounds * gb * 10e-6 + (double)g * 3 * P * 12 / 5e12;
+        const double t = (double)rounds * gb * 17e-6 + (double)g * 3 * P * 8 / 6e12;
         if (t < best) {
             best = t;
             groups = g;
@@ -376,7 +376,6 @@ fc_status stage_window(fc_session* s, int count, bool write_acc) {
             herk_groups(s->ntp128, s->sel1 - s->sel0, s->num_sms, (long long)s->P, s->herk_gcap, ha.groups,
                         ha.group_bins);
             LAUNCH(FC_K_HERK_TC, launch_pack_operands(pk, s->stream));
-            CK(cudaMemsetAsync(s->herk_part, 0, (size_t)ha.groups * 3 * s->P * sizeof(float), s->stream));
             LAUNCH(FC_K_HERK_TC, launch_herk_tc(ha, s->stream));
             LAUNCH(FC_K_BAND_REDUCE, launch_herk_band(ha, s->stream));
         }

@@ -233,7 +233,7 @@ struct HerkArgs {
     const unsigned short* tile_a;  // 128-node tile pairs
     const unsigned short* tile_b;
     const float* inv_psd;
-    float* part;          // [groups][3][P] band sums of COH, IMAGCOHY, PLV, zeroed before the launch
+    float* part;          // [groups][3][P] band sums of COH, IMAGCOHY, PLV per bin group
     float* net;           // [FC_NMETRIC][P]
     int n, B, ntp, nchunks, W, count, ab_format, grid_ctas;
     int groups, group_bins;  // the selected bins in groups of group_bins (the last may be shorter)

@@ -9,9 +9,10 @@
 // and the same with U for the phasor sums: four real GEMMs of 128 x 128 x 2K per
 // (128-node tile pair, bin), kind::f16 (BF16 or FP16 operands) or kind::tf32, FP32
 // accumulation. COH, IMAGCOHY and PLV of the bin are finalized from TMEM and added to the
-// band sums of the unit's bin group with fire-and-forget reductions (red.global.add): one CTA
-// walks all bins of a (tile pair, bin group) unit in order and each sum has one owner thread,
-// so the additions land in bin order and the sums are reproducible. A small kernel adds the
+// band sums of the unit's bin group (the first bin stores, the later ones add with
+// fire-and-forget reductions, red.global.add): one CTA walks all bins of a (tile pair, bin
+// group) unit in order and each sum has one owner thread, so the additions land in bin order
+// and the sums are reproducible. A small kernel adds the
 // groups and scales by the number of bins. The non-linear sums
 // (signs, |Im|, Im^2) cannot be contracted and run on the CUDA cores (k_nonlin).
 //
@@ -28,6 +29,8 @@
 #include "mbar.cuh"
 #include "tc.cuh"
 
+#include <type_traits>
+
 namespace {
 
 using namespace fcmbar;
@@ -42,11 +45,6 @@ constexpr int EPI_WARPS = 8;           // epilogue warps: lane quarter w % 4, ro
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 512 + EPI_WARPS * 512;  // + barriers, TMEM address, 1/sqrt(PSD) rows per epilogue warp
 constexpr uint32_t TMEM_COLS = 512;    // 2 phase buffers x 2 accumulators x 128 FP32 columns
 constexpr int THREADS = 32 * EPI_WARPS + 32;  // warps 0-7: epilogue; warp 8: loads + MMAs
-
-// *addr += v as a fire-and-forget reduction (no value returned, nothing to wait for)
-__device__ __forceinline__ void red_add(float* addr, float v) {
-    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(v) : "memory");
-}
 
 __device__ __forceinline__ long long packed_index(int i, int j, int n) {
     return (long long)i * n - (long long)i * (i + 1) / 2 + (j - i - 1);
@@ -246,6 +244,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
             fence_after();
             const uint32_t col = (uint32_t)(b * 2 * TILE);
             float* out = a.part + (size_t)(es.u % a.groups) * 3 * a.P;  // this group's band sums
+            // the unit's first bin writes its values, the later bins add to them (same thread,
+            // same address: the reductions land after the store and in bin order)
+            const bool first = f == a.fsel0 + (es.u % a.groups) * a.group_bins;
             // this warp's 64 row nodes: all eight loads (re and im of 4 x 16 columns) in flight
             // at once, one wait
             const int ibase = rhalf * (TILE / 2);
@@ -262,26 +263,46 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
                 tmem_keep(rim[s4]);
             }
             if (j < a.n) {
-                // packed index of (i, j) for i = ta TILE + ibase, then p(i + 1) = p(i) + n - i - 2
-                int i = ta * TILE + ibase;
-                long long p = packed_index(i, j, a.n);
+                // packed index of (i, j) for i = ta TILE + ibase, then p(i + 1) = p(i) + n - i - 2;
+                // the unit's first bin stores, the later ones add (atomicAdd without its result:
+                // a fire-and-forget reduction; same thread, same address, so in bin order)
+                auto emit = [&](auto first_c) {
+                    constexpr bool FIRST = decltype(first_c)::value;
+                    int i = ta * TILE + ibase;
+                    long long p = packed_index(i, j, a.n);
 #pragma unroll
-                for (int s4 = 0; s4 < 4; ++s4) {
+                    for (int s4 = 0; s4 < 4; ++s4) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q, p += a.n - i - 2, ++i) {
-                        if (j <= i || i >= a.n) continue;
-                        const float vre = __uint_as_float(rre[s4][q]), vim = __uint_as_float(rim[s4][q]);
-                        if (b == 0) {
-                            const float inv_i = sinv[ibase + 16 * s4 + q];
-                            const float r = __fmul_rn(__fmul_rn(vre, inv_i), inv_j);
-                            const float m = __fmul_rn(__fmul_rn(vim, inv_i), inv_j);
-                            red_add(out + p, sqrtf(__fmaf_rn(r, r, __fmul_rn(m, m))));
-                            red_add(out + a.P + p, m);
-                        } else {
-                            red_add(out + 2 * a.P + p, __fmul_rn(sqrtf(__fmaf_rn(vre, vre, __fmul_rn(vim, vim))), inv_K));
+                        for (int q = 0; q < 16; ++q, p += a.n - i - 2, ++i) {
+                            if (j <= i || i >= a.n) continue;
+                            const float vre = __uint_as_float(rre[s4][q]), vim = __uint_as_float(rim[s4][q]);
+                            float v0, v1 = 0.f;
+                            long long o0;
+                            if (b == 0) {
+                                const float inv_i = sinv[ibase + 16 * s4 + q];
+                                const float r = __fmul_rn(__fmul_rn(vre, inv_i), inv_j);
+                                const float m = __fmul_rn(__fmul_rn(vim, inv_i), inv_j);
+                                v0 = sqrtf(__fmaf_rn(r, r, __fmul_rn(m, m)));
+                                v1 = m;
+                                o0 = p;
+                            } else {
+                                v0 = __fmul_rn(sqrtf(__fmaf_rn(vre, vre, __fmul_rn(vim, vim))), inv_K);
+                                o0 = 2 * a.P + p;
+                            }
+                            if (FIRST) {
+                                out[o0] = v0;
+                                if (b == 0) out[a.P + p] = v1;
+                            } else {
+                                atomicAdd(out + o0, v0);
+                                if (b == 0) atomicAdd(out + a.P + p, v1);
+                            }
                         }
                     }
-                }
+                };
+                if (first)
+                    emit(std::true_type{});
+                else
+                    emit(std::false_type{});
             }
             fence_before();
             __syncwarp();

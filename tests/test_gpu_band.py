@@ -79,3 +79,29 @@ def test_band_change_errors():
                 fc.fc_set_band(s.handle, lo, hi)
             assert e.value.status == fc.FC_ERR_INVALID_ARG
         fc.fc_set_band(s.handle, 8.0, 30.0)
+
+
+def test_bf16_band_change_at_1024_nodes_matches_fp32():
+    """1024 nodes: the tensor-core band sums run over groups of several bins (reductions after
+    each unit's first bin) starting inside the computed bins. After a band change and back,
+    the BF16 session's linear metrics stay within 5e-3 of an FP32 session's on the same
+    trials (itself checked against the oracle elsewhere), the non-linear ones within 1e-5."""
+    n, N, W = 1024, 500, 20
+    x = white_trials(31, W, n, N)
+    x[:, 7] += 0.8 * x[:, 300]
+    nets = {}
+    for prec in (fc.FC_PREC_FP32, fc.FC_PREC_BF16):
+        with fc.Session(n, N, 1000.0, (4.0, 44.0, 1000), "hann", fc.FC_SPECTRAL_METRICS, W,
+                        mode=fc.FC_MODE_FULL, precision=prec) as s:
+            s.push(x)
+            out = []
+            for lo, hi in ((10.0, 35.0), (4.0, 44.0)):
+                fc.fc_set_band(s.handle, lo, hi)
+                out.append({m: s.network(m, packed=True)[0].astype(np.float64) for m in SPECTRAL})
+            nets[prec] = out
+    for k in range(2):
+        a, b = nets[fc.FC_PREC_FP32][k], nets[fc.FC_PREC_BF16][k]
+        for m in SPECTRAL:
+            d = np.nanmax(np.abs(a[m] - b[m]))
+            assert d <= (5e-3 if m in LINEAR else 1e-5 * max(1.0, np.nanmax(np.abs(a[m])))), (k, m, d)
+        assert a["COH"][7 * n - 7 * 8 // 2 + (300 - 7 - 1)] > 0.5  # the coupled pair stands out

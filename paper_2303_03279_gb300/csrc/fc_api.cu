@@ -73,7 +73,7 @@ fc_status alloc_zero(fc_session* s, size_t count, T** out) {
     fc_status st = dev_alloc(s, count * sizeof(T), &p);
     if (st != FC_OK) return st;
     CK(cudaMemsetAsync(p, 0, count * sizeof(T), s->stream));
-    s->state_bufs.emplace_back(p, count * sizeof(T) ? count * sizeof(T) : 16);
+    s->state_bufs.emplace_back(p, count > 0 ? count * sizeof(T) : 16);
     *out = static_cast<T*>(p);
     return FC_OK;
 }

@@ -24,7 +24,7 @@ using namespace fcpair;
 
 constexpr int NK = 16;  // trials per staged chunk (and per FP32 partial sum)
 
-__global__ void __launch_bounds__(256, 2) k_nonlin(PairArgs a) {
+__global__ void __launch_bounds__(256, 3) k_nonlin(PairArgs a) {
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
     const long long end = c->pushed + a.count;

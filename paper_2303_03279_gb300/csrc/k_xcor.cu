@@ -197,8 +197,13 @@ __global__ void k_xcor_pairs(XcorArgs a, long long n_items, long long first_tria
 // so the remaining spans (below E and below 32) pair registers of the same lane again, with
 // twiddles that are the same for every lane. The output lands in bit-reversed order, which
 // the scan over lags reads through the bit reversal of each position.
+// CTAs per SM to keep registers for: at 512-point transforms one more than the register use
+// alone would allow (shared memory holds four; the kernel is issue-bound and gains from warps)
+template <int E> struct XcorMinBlocks { static constexpr int v = 1; };
+template <> struct XcorMinBlocks<16> { static constexpr int v = 4; };
+
 template <int E, int S>
-__global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_items, long long first_trial,
+__global__ void __launch_bounds__(256, XcorMinBlocks<E>::v) k_xcor_pairs_reg(XcorArgs a, long long n_items, long long first_trial,
                                                        int n_trials) {
     constexpr int MS = 32 * E;  // points of one register transform
     constexpr int M = MS << S;  // points of the whole complex transform

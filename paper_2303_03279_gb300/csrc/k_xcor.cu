@@ -197,28 +197,35 @@ __global__ void k_xcor_pairs(XcorArgs a, long long n_items, long long first_tria
 // so the remaining spans (below E and below 32) pair registers of the same lane again, with
 // twiddles that are the same for every lane. The output lands in bit-reversed order, which
 // the scan over lags reads through the bit reversal of each position.
-// CTAs per SM to keep registers for: at 512-point transforms one more than the register use
-// alone would allow (shared memory holds four; the kernel is issue-bound and gains from warps)
+// CTAs per SM to keep registers for: at 512- and 1024-point transforms one more than the
+// register use alone would allow (shared memory holds four and three; the kernel is
+// issue-bound and gains from warps)
 template <int E> struct XcorMinBlocks { static constexpr int v = 1; };
 template <> struct XcorMinBlocks<16> { static constexpr int v = 4; };
+template <> struct XcorMinBlocks<32> { static constexpr int v = 3; };
+// Forms without the product-step twiddle table stw (its odd entries come from the stage
+// table): 8192 points, where it does not fit, and 1024 points, where leaving it out lets a
+// third CTA onto the SM
+template <int E, int S> struct XcorNoStw { static constexpr bool v = S == 2 || (E == 32 && S == 0); };
 
 template <int E, int S>
 __global__ void __launch_bounds__(256, XcorMinBlocks<E>::v) k_xcor_pairs_reg(XcorArgs a, long long n_items, long long first_trial,
                                                        int n_trials) {
     constexpr int MS = 32 * E;  // points of one register transform
     constexpr int M = MS << S;  // points of the whole complex transform
-    // dynamic shared memory: stw[M] = tw[k] = e^{-2 pi i k / L} (S < 2 only); sth[M] = the
+    // dynamic shared memory: stw[M] = tw[k] = e^{-2 pi i k / L} (not in every form); sth[M] = the
     // butterflies' twiddles by stage, span h at sth[h + t] = tw[t M / h], t < h (a stage's
     // lanes read consecutive entries or one entry each, broadcast: no bank conflicts); then
-    // one transpose buffer of MS + MS / E slots per warp. With S = 2 the table stw would not
-    // fit beside the rest: tw[2t] = sth[M / 2 + t] and tw[2t + 1] = tw[2t] tw[1].
+    // one transpose buffer of MS + MS / E slots per warp. Without stw (see XcorNoStw):
+    // tw[2t] = sth[M / 2 + t] and tw[2t + 1] = tw[2t] tw[1].
+    constexpr bool NO_STW = XcorNoStw<E, S>::v;
     extern __shared__ float2 dsm[];
     float2* stw = dsm;
-    float2* sth = dsm + (S < 2 ? M : 0);
+    float2* sth = dsm + (NO_STW ? 0 : M);
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        if (S < 2) stw[k] = a.tw[k];
+        if (!NO_STW) stw[k] = a.tw[k];
         if (k > 0) {
             const int h = 1 << (31 - __clz(k));
             sth[k] = a.tw[(k - h) * (M / h)];
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(256, XcorMinBlocks<E>::v) k_xcor_pairs_reg(Xco
         const float2 e = make_float2(0.5f * __fadd_rn(pk.x, pm.x), 0.5f * __fadd_rn(pk.y, pm.y));
         const float2 dd = csub(pk, pm);
         float2 w;  // e^{+2 pi i k / L}
-        if (S < 2)
+        if (!NO_STW)
             w = cconj(stw[k]);
         else
             w = cconj((k & 1) ? cmul(sth[M / 2 + (k >> 1)], tw1) : sth[M / 2 + (k >> 1)]);
@@ -399,8 +406,8 @@ __global__ void k_xcor_update(XcorArgs a) {
 template <int E, int S>
 cudaError_t launch_pairs_reg(const XcorArgs& a, long long items, long long first, int n_trials, cudaStream_t st) {
     constexpr int MS = 32 * E;
-    // twiddle tables (2 M, or M for S = 2) and 8 warps x (MS + MS / E) transpose slots
-    const int dyn = ((S < 2 ? 2 : 1) * (MS << S) + 8 * (MS + MS / E)) * (int)sizeof(float2);
+    // twiddle tables (2 M, or M without stw) and 8 warps x (MS + MS / E) transpose slots
+    const int dyn = ((XcorNoStw<E, S>::v ? 1 : 2) * (MS << S) + 8 * (MS + MS / E)) * (int)sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_xcor_pairs_reg<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
     k_xcor_pairs_reg<E, S><<<(unsigned)((items + 7) / 8), 256, dyn, st>>>(a, items, first, n_trials);

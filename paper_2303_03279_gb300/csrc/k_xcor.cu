@@ -200,17 +200,21 @@ __global__ void k_xcor_pairs(XcorArgs a, long long n_items, long long first_tria
 // CTAs per SM to keep registers for: at 512- and 1024-point transforms one more than the
 // register use alone would allow (shared memory holds four and three; the kernel is
 // issue-bound and gains from warps)
-template <int E> struct XcorMinBlocks { static constexpr int v = 1; };
-template <> struct XcorMinBlocks<16> { static constexpr int v = 4; };
-template <> struct XcorMinBlocks<32> { static constexpr int v = 3; };
+// 0: no minimum (the plain bound). The explicit minimum of one at 2048 points lets ptxas
+// keep 240 registers instead of 188 (15 % faster); at 4096 points it made ptxas spill
+// 564 bytes (22 % slower), so that form keeps the plain bound.
+template <int E, int S> struct XcorMinBlocks { static constexpr int v = 0; };
+template <> struct XcorMinBlocks<16, 0> { static constexpr int v = 4; };
+template <> struct XcorMinBlocks<32, 0> { static constexpr int v = 3; };
+template <> struct XcorMinBlocks<64, 0> { static constexpr int v = 1; };
 // Forms without the product-step twiddle table stw (its odd entries come from the stage
 // table): 8192 points, where it does not fit, and 1024 points, where leaving it out lets a
 // third CTA onto the SM
 template <int E, int S> struct XcorNoStw { static constexpr bool v = S == 2 || (E == 32 && S == 0); };
 
 template <int E, int S>
-__global__ void __launch_bounds__(256, XcorMinBlocks<E>::v) k_xcor_pairs_reg(XcorArgs a, long long n_items, long long first_trial,
-                                                       int n_trials) {
+__device__ __forceinline__ void xcor_pairs_reg(const XcorArgs& a, long long n_items, long long first_trial,
+                                               int n_trials) {
     constexpr int MS = 32 * E;  // points of one register transform
     constexpr int M = MS << S;  // points of the whole complex transform
     // dynamic shared memory: stw[M] = tw[k] = e^{-2 pi i k / L} (not in every form); sth[M] = the
@@ -377,6 +381,17 @@ __global__ void __launch_bounds__(256, XcorMinBlocks<E>::v) k_xcor_pairs_reg(Xco
     }
 }
 
+template <int E, int S>
+__global__ void __launch_bounds__(256) k_xcor_pairs_reg(XcorArgs a, long long n_items, long long first_trial,
+                                                       int n_trials) {
+    xcor_pairs_reg<E, S>(a, n_items, first_trial, n_trials);
+}
+template <int E, int S>
+__global__ void __launch_bounds__(256, XcorMinBlocks<E, S>::v) k_xcor_pairs_reg_mb(XcorArgs a, long long n_items,
+                                                                                 long long first_trial, int n_trials) {
+    xcor_pairs_reg<E, S>(a, n_items, first_trial, n_trials);
+}
+
 // ------------------------------------------------------------------ network update
 __global__ void k_xcor_update(XcorArgs a) {
     const FcCtrl* c = a.ctrl;
@@ -408,9 +423,16 @@ cudaError_t launch_pairs_reg(const XcorArgs& a, long long items, long long first
     constexpr int MS = 32 * E;
     // twiddle tables (2 M, or M without stw) and 8 warps x (MS + MS / E) transpose slots
     const int dyn = ((XcorNoStw<E, S>::v ? 1 : 2) * (MS << S) + 8 * (MS + MS / E)) * (int)sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_xcor_pairs_reg<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-    if (e != cudaSuccess) return e;
-    k_xcor_pairs_reg<E, S><<<(unsigned)((items + 7) / 8), 256, dyn, st>>>(a, items, first, n_trials);
+    const unsigned grid = (unsigned)((items + 7) / 8);
+    if constexpr (XcorMinBlocks<E, S>::v > 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_xcor_pairs_reg_mb<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return e;
+        k_xcor_pairs_reg_mb<E, S><<<grid, 256, dyn, st>>>(a, items, first, n_trials);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_xcor_pairs_reg<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return e;
+        k_xcor_pairs_reg<E, S><<<grid, 256, dyn, st>>>(a, items, first, n_trials);
+    }
     return cudaGetLastError();
 }
 

@@ -248,6 +248,26 @@ def test_xcor_fft_matches_direct_sums_and_correlate():
     assert np.all(lag == -lag.T)
 
 
+
+@pytest.mark.parametrize("N", [2049, 4097, 8192])
+def test_xcor_fft_matches_correlate_at_long_trials(N):
+    """The FFT form at the longest trials XCOR sessions take (transforms of 4096 to 16384
+    points): value and lag of every ordered pair against numpy's direct correlation."""
+    rng = np.random.default_rng(N)
+    x = rng.standard_normal((3, N))
+    x[1] = np.roll(x[0], 11) + 0.3 * x[1]
+    val, lag = O.xcor_trial_dense(x)
+    for i in range(3):
+        for j in range(3):
+            if i == j:
+                continue
+            di, dj = x[i] - x[i].mean(), x[j] - x[j].mean()
+            c = np.correlate(di, dj, "full")  # index k <-> lag k - (N - 1)
+            k = int(np.argmax(c))
+            assert lag[i, j] == k - (N - 1)
+            assert abs(c[k] / math.sqrt(np.dot(di, di) * np.dot(dj, dj)) - val[i, j]) < 1e-10
+    assert abs(lag[1, 0]) == 11 and val[1, 0] > 0.9
+
 def test_xcor_recovers_shift():
     rng = np.random.default_rng(15)
     s = rng.standard_normal(300)

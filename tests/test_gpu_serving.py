@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 from paper_2303_03279_gb300 import fc  # noqa: E402
 
 SPECTRAL = ("COH", "IMAGCOHY", "PLV", "PLI", "USPLI", "WPLI", "DSWPLI")
-CONFIGS = [  # n, N, fs, band, W, trials
+SESSION_SHAPES = [  # n, N, fs, band, W, trials
     (60, 200, 500.0, (1.0, 50.0, 256), 8, 14),
     (128, 200, 500.0, (4.0, 44.0, 250), 12, 17),
     (70, 128, 256.0, (8.0, 40.0, 128), 5, 11),
@@ -35,7 +35,7 @@ def _need_gpu():
 
 
 def _trials():
-    return [white_trials(40 + k, t, n, N) for k, (n, N, fs, band, W, t) in enumerate(CONFIGS)]
+    return [white_trials(40 + k, t, n, N) for k, (n, N, fs, band, W, t) in enumerate(SESSION_SHAPES)]
 
 
 def _serve(which, interleave=True, plain=False, max_batch=0, launch_blocks=0, xs=None):
@@ -45,25 +45,25 @@ def _serve(which, interleave=True, plain=False, max_batch=0, launch_blocks=0, xs
     try:
         ids = {}
         for k in which:
-            n, N, fs, band, W, _ = CONFIGS[k]
+            n, N, fs, band, W, _ = SESSION_SHAPES[k]
             ids[k] = fc.fc_server_open(sv, n, N, fs, band, "hann", fc.FC_SPECTRAL_METRICS, W)
         # arrival order: round-robin across sessions (mixed) or session after session
         order = []
         if interleave:
-            for t in range(max(CONFIGS[k][5] for k in which)):
-                order += [(k, t) for k in which if t < CONFIGS[k][5]]
+            for t in range(max(SESSION_SHAPES[k][5] for k in which)):
+                order += [(k, t) for k in which if t < SESSION_SHAPES[k][5]]
         else:
-            order = [(k, t) for k in which for t in range(CONFIGS[k][5])]
+            order = [(k, t) for k in which for t in range(SESSION_SHAPES[k][5])]
         for k, t in order:
             fc.fc_server_submit(sv, ids[k], xs[k][t], fc.fc_server_now_ms())
         fc.fc_server_drain(sv, 120000)
         res = fc.fc_server_poll(sv, 4096)
-        assert len(res) == sum(CONFIGS[k][5] for k in which)
+        assert len(res) == sum(SESSION_SHAPES[k][5] for k in which)
         for sid, seq, status, arr, done, batch in res:
             assert done >= arr and batch >= 1
         out = {}
         for k in which:
-            n = CONFIGS[k][0]
+            n = SESSION_SHAPES[k][0]
             P = n * (n - 1) // 2
             nets = {}
             for m in SPECTRAL:
@@ -88,7 +88,7 @@ def test_same_alone_and_in_the_mix(launch_blocks):
     if launch_blocks:
         # every push of the 128-node session after its first (calibrating, whole) one needs
         # at least two launches
-        assert stats["launches"] >= 2 * (CONFIGS[1][5] - 1)
+        assert stats["launches"] >= 2 * (SESSION_SHAPES[1][5] - 1)
     for k in range(3):
         alone, _, _ = _serve([k], interleave=False)
         for m in SPECTRAL:
@@ -99,7 +99,7 @@ def test_served_equals_standalone_session_and_plain_mode():
     served, _, _ = _serve([0, 1, 2], interleave=True)
     plain, _, _ = _serve([0, 1, 2], interleave=True, plain=True)
     xs = _trials()
-    for k, (n, N, fs, band, W, T) in enumerate(CONFIGS):
+    for k, (n, N, fs, band, W, T) in enumerate(SESSION_SHAPES):
         with fc.Session(n, N, fs, band, "hann", fc.FC_SPECTRAL_METRICS, W) as s:
             for t in range(T):
                 s.push(xs[k][t])
@@ -111,22 +111,22 @@ def test_served_equals_standalone_session_and_plain_mode():
 
 def test_admission_by_device_memory_budget():
     need = [fc.fc_server_session_bytes(n, N, fs, band, fc.FC_SPECTRAL_METRICS, W)
-            for (n, N, fs, band, W, _) in CONFIGS]
+            for (n, N, fs, band, W, _) in SESSION_SHAPES]
     sv = fc.fc_server_create(hbm_budget=need[0] + need[1] + 1024)
     try:
-        a = fc.fc_server_open(sv, *CONFIGS[0][:3], CONFIGS[0][3], "hann", fc.FC_SPECTRAL_METRICS, CONFIGS[0][4])
-        b = fc.fc_server_open(sv, *CONFIGS[1][:3], CONFIGS[1][3], "hann", fc.FC_SPECTRAL_METRICS, CONFIGS[1][4])
+        a = fc.fc_server_open(sv, *SESSION_SHAPES[0][:3], SESSION_SHAPES[0][3], "hann", fc.FC_SPECTRAL_METRICS, SESSION_SHAPES[0][4])
+        b = fc.fc_server_open(sv, *SESSION_SHAPES[1][:3], SESSION_SHAPES[1][3], "hann", fc.FC_SPECTRAL_METRICS, SESSION_SHAPES[1][4])
         with pytest.raises(fc.FcError) as e:
-            fc.fc_server_open(sv, *CONFIGS[1][:3], CONFIGS[1][3], "hann", fc.FC_SPECTRAL_METRICS, CONFIGS[1][4])
+            fc.fc_server_open(sv, *SESSION_SHAPES[1][:3], SESSION_SHAPES[1][3], "hann", fc.FC_SPECTRAL_METRICS, SESSION_SHAPES[1][4])
         assert e.value.status == fc.FC_ERR_ADMISSION
         assert fc.fc_server_stats_get(sv)["hbm_used"] == need[0] + need[1]
         fc.fc_server_close(sv, b)  # frees need[1]: the refused session now fits
         assert fc.fc_server_stats_get(sv)["hbm_used"] == need[0]
-        c = fc.fc_server_open(sv, *CONFIGS[1][:3], CONFIGS[1][3], "hann", fc.FC_SPECTRAL_METRICS, CONFIGS[1][4])
+        c = fc.fc_server_open(sv, *SESSION_SHAPES[1][:3], SESSION_SHAPES[1][3], "hann", fc.FC_SPECTRAL_METRICS, SESSION_SHAPES[1][4])
         assert c not in (a, b)
         with pytest.raises(fc.FcError):  # a closed session takes no more trials
-            fc.fc_server_submit(sv, b, white_trials(8, 1, CONFIGS[1][0], CONFIGS[1][1])[0], 0.0)
-        x = white_trials(9, 1, CONFIGS[1][0], CONFIGS[1][1])[0]
+            fc.fc_server_submit(sv, b, white_trials(8, 1, SESSION_SHAPES[1][0], SESSION_SHAPES[1][1])[0], 0.0)
+        x = white_trials(9, 1, SESSION_SHAPES[1][0], SESSION_SHAPES[1][1])[0]
         fc.fc_server_submit(sv, c, x, fc.fc_server_now_ms())
         fc.fc_server_drain(sv, 60000)
         assert len(fc.fc_server_poll(sv, 16)) == 1
@@ -141,12 +141,12 @@ def test_nonfinite_trial_is_rejected_in_the_mix():
     bad = [x.copy() for x in xs]
     bad[1] = np.concatenate([xs[1][:6], xs[1][6:7].copy(), xs[1][6:]])
     bad[1][6, 3, 17] = np.nan  # session 1's 7th submission is poisoned, its trials shift by one
-    CONF = list(CONFIGS)
-    CONFIGS[1] = CONF[1][:5] + (CONF[1][5] + 1,)
+    CONF = list(SESSION_SHAPES)
+    SESSION_SHAPES[1] = CONF[1][:5] + (CONF[1][5] + 1,)
     try:
         got, _, res = _serve([0, 1, 2], interleave=True, launch_blocks=100, xs=bad)
     finally:
-        CONFIGS[1] = CONF[1]
+        SESSION_SHAPES[1] = CONF[1]
     want, _, _ = _serve([0, 1, 2], interleave=True)
     st = {(r[0], r[1]): r[2] for r in res}
     assert sorted(v for v in st.values() if v != fc.FC_OK) == [fc.FC_ERR_NONFINITE]
@@ -162,7 +162,7 @@ def test_time_domain_session_beside_a_spectral_session():
     """A COR + XCOR session (it holds no spectral state) served beside a spectral session:
     its networks equal those of a standalone session fed the same trials, and a spectral
     metric is refused for it."""
-    n1, N1, fs1, band1, W1, T1 = CONFIGS[0]
+    n1, N1, fs1, band1, W1, T1 = SESSION_SHAPES[0]
     n2, N2, W2, T2 = 48, 160, 6, 12
     band2 = (1.0, 50.0, 256)
     x1 = white_trials(61, T1, n1, N1)

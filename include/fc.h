@@ -452,6 +452,12 @@ fc_status fc_fir_destroy(fc_fir* f);
  *   stream:   cudaStream_t to enqueue on (NULL: the legacy default stream). The call is
  *             asynchronous; results are ready when the stream reaches this point.
  *
+ * The spectra may be in any unit: as a session does with its own, the call scales them by
+ * the power of two that brings their largest |re|, |im| into [1, 2) (exact; every metric
+ * is invariant to it) as the kernels read them; the caller's buffer is not written. The
+ * values must be finite: they are not checked, and a NaN or Inf gives NaN in the networks
+ * of the pairs of its node (the call still returns FC_OK).
+ *
  * Every intermediate (window control block, per-node PSD sums, tile tables, band
  * partial sums) lives in one file-scope device array of FC_NOALLOC_SCRATCH_BYTES that
  * every GPU loading the library holds until the process exits. Limits: the PSD sums and
@@ -459,9 +465,10 @@ fc_status fc_fir_destroy(fc_fir* f);
  * work split shrinks to what fits. Sizes beyond the limit return FC_ERR_INVALID_ARG with a
  * message in fc_last_error(). The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. All calls share the array and it keeps the last call's contents
- * (the control block is cleared on every call): calls whose work overlaps on the GPU
- * (different streams, no ordering between them) race and corrupt each other.
+ * any stream capture (a failed lookup is not kept: the next call tries again). All calls
+ * share the array and it keeps the last call's contents (the control block is cleared on
+ * every call): calls whose work overlaps on the GPU (different streams, no ordering
+ * between them) race and corrupt each other.
  * No cudaMalloc, cudaFree or allocating library routine is called. */
 fc_status fc_window_networks_noalloc(const float* spectra, int n_trials, int n_bins, int n_nodes,
                                      uint32_t metric_mask, float* out, size_t out_len, void* stream);

@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "fc_internal.h"
@@ -153,7 +154,7 @@ PairArgs pair_args(fc_session* s, bool stream_kernel, int count) {
     a.acc = s->acc;
     a.tile_a = s->tile_a;
     a.tile_b = s->tile_b;
-    a.net = s->net;
+    a.net_spec = s->net + (size_t)MI_COH * s->P;
     a.partial = s->partial;
     a.slots = s->slots;
     a.n = s->n;
@@ -544,6 +545,26 @@ fc_status check_latched(fc_session* s, FcCtrl* h) {
 
 void fc_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
 
+int fc_device_sms(int device) {
+    static std::mutex mu;
+    static int cache[64] = {0};
+    if (device < 0 && cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (device >= 64) device = 63;
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache[device] <= 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v < 1) {
+            cudaGetLastError();
+            return 152;  // not cached: the next call asks again
+        }
+        cache[device] = v;
+    }
+    return cache[device];
+}
+
 // ------------------------------------------------- streaming push in pieces (serving)
 bool fc_push_needs_single(fc_session* s) {
     return !s->calibrated || s->time_mask != 0 || s->cfg.mode != FC_MODE_STREAM;
@@ -617,8 +638,9 @@ size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode 
         b += (size_t)N * B * 8 + slots * B * n * 8 + (size_t)B * n * 12 + ntp * 4;
         if (mode == FC_MODE_STREAM) b += ntp * B * FC_BLOCK_WORDS * 4;
         int wg, wgb;
-        window_groups((long long)ntp, B, (long long)P, W, 152, wg, wgb);
-        const int groups = std::max(wg, std::min(B, std::max(1, (int)((152 * 4 + ntp - 1) / ntp))));
+        const int sms = fc_device_sms();
+        window_groups((long long)ntp, B, (long long)P, W, sms, wg, wgb);
+        const int groups = std::max(wg, std::min(B, std::max(1, (int)((sms * 4 + ntp - 1) / ntp))));
         if (groups > 1) b += (size_t)groups * 7 * P * 4;
     }
     if (mask & FC_COR)
@@ -721,9 +743,7 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
     s->P = (long long)n_nodes * (n_nodes - 1) / 2;
     s->slots = cfg.mode == FC_MODE_FULL ? window : (window > 0 ? window + 1 : 1);
     cudaGetDevice(&s->device);
-    if (cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
-        s->num_sms < 1)
-        s->num_sms = 152;
+    s->num_sms = fc_device_sms(s->device);
 
     auto cleanup = [&](fc_status st) {
         if (s->stream) cudaStreamSynchronize(s->stream);
@@ -741,8 +761,8 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
         s->own_stream = true;
     }
 
-    // work split: enough CTAs to fill 152 SMs twice over
-    const int target = 152 * 4;
+    // work split: enough CTAs to fill every SM twice over (two CTAs per SM)
+    const int target = s->num_sms * 4;
     s->stream_groups = std::min(B, std::max(1, (target + s->ntp - 1) / s->ntp));
     s->stream_group_bins = (B + s->stream_groups - 1) / s->stream_groups;
     s->stream_groups = (B + s->stream_group_bins - 1) / s->stream_group_bins;

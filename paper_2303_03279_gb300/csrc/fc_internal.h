@@ -48,7 +48,8 @@ struct FcCtrl {
     unsigned int max_bits; // calibration: max |re|,|im| of the first spectra (float bits)
     float scale;           // power-of-two prescale of all spectra (0 = not calibrated)
     int timeout;           // a bounded device-side wait ran out
-    int pad_;
+    float in_scale;        // power-of-two factor the full-window kernels apply to the spectra
+                           // as they read them (0: none; sessions store prescaled spectra)
 };
 
 struct FcPendingTiming {
@@ -187,7 +188,7 @@ struct PairArgs {
     float* acc;
     const unsigned short* tile_a;
     const unsigned short* tile_b;
-    float* net;        // [FC_NMETRIC][P]
+    float* net_spec;   // network planes of the 7 spectral metrics, [7][P] (COH .. DSWPLI)
     float* partial;    // [groups][7][P]
     int slots, n, B, W, ntp;
     long long P;
@@ -358,6 +359,9 @@ cudaError_t launch_network_top(const float* w, long long P, int n, long long k, 
                                int* degree, float* strength, int num_sms, cudaStream_t stream);
 
 void fc_internal_set_error(const char* msg);
+// Multiprocessor count of a device (device < 0: the current one), queried once per device
+// and cached; 152 (GB300) only if the query fails.
+int fc_device_sms(int device = -1);
 
 // Streaming pushes of several sessions split into stages, for the serving engine
 // (fc_server.cu): each trial is already on the device (x[i]). pre: validation, spectrum and

@@ -8,7 +8,9 @@
 // from spectra the caller already holds on the device, into an output the caller owns,
 // and keeps every intermediate (window control block, per-node PSD sums, tile tables,
 // band partial sums) in one file-scope device array of FC_NOALLOC_SCRATCH_BYTES that
-// the library holds on every GPU that loads it, until the process exits.
+// the library holds on every GPU that loads it, until the process exits. Like a session,
+// it brings the spectra into a fixed range by an exact power-of-two factor applied as the
+// kernels read them.
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
@@ -22,21 +24,54 @@ constexpr size_t kScratchBytes = (size_t)FC_NOALLOC_SCRATCH_BYTES;
 // The shared scratch: every call uses it, and it keeps the last call's contents.
 static __device__ __align__(256) unsigned char fc_noalloc_scratch[kScratchBytes];
 
-// Device address of the scratch array per device (the host symbol is only a stand-in).
+// Device address of the scratch array and multiprocessor count, per device (the host-side
+// symbol is only a stand-in). Only a successful lookup is kept: a failed one (a sticky error
+// from earlier work, a call made during stream capture) is tried again by the next call.
 constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices];
-std::once_flag g_scratch_once[kMaxDevices];
-cudaError_t g_scratch_status[kMaxDevices];
+int g_scratch_sms[kMaxDevices];
 
-cudaError_t scratch_address(int dev, void** out) {
+cudaError_t scratch_address(int dev, void** out, int* sms) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::call_once(g_scratch_once[dev], [dev]() {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
         void* p = nullptr;
-        g_scratch_status[dev] = cudaGetSymbolAddress(&p, fc_noalloc_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, fc_noalloc_scratch);
+        if (e != cudaSuccess || !p) return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
         g_scratch_addr[dev] = p;
-    });
+        g_scratch_sms[dev] = fc_device_sms(dev);
+    }
     *out = g_scratch_addr[dev];
-    return g_scratch_status[dev];
+    *sms = g_scratch_sms[dev];
+    return cudaSuccess;
+}
+
+// Power-of-two prescale of the caller's spectra, as a session applies to its own: the largest
+// |re|, |im| of the window is brought into [1, 2) so that the squared terms (Im^2, |X|^2)
+// stay far from FP32 underflow for spectra in physical units. A power of two is exact and
+// every metric is invariant to a common positive factor. The kernels apply it as they read
+// the spectra (FcCtrl::in_scale); the caller's buffer is not written.
+__global__ void k_noalloc_max(const float* __restrict__ v, long long count, FcCtrl* ctrl) {
+    unsigned int m = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float x = fabsf(v[i]);
+        if (x <= 3.4028234663852886e38f) m = max(m, __float_as_uint(x));  // finite values only
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&ctrl->max_bits, m);
+}
+
+__global__ void k_noalloc_scale(FcCtrl* ctrl) {
+    const float m = __uint_as_float(ctrl->max_bits);
+    float s = 1.f;
+    if (m > 0.f) {
+        int e;
+        frexpf(m, &e);          // m = f 2^e, f in [0.5, 1)
+        s = ldexpf(1.f, 1 - e); // m s in [1, 2)
+    }
+    ctrl->in_scale = s;
 }
 
 __global__ void k_noalloc_tiles(unsigned short* ta, unsigned short* tb, int nt) {
@@ -82,21 +117,21 @@ extern "C" fc_status fc_window_networks_noalloc(const float* spectra, int n_tria
     if (off_part > kScratchBytes)
         return noalloc_fail(FC_ERR_INVALID_ARG,
                             "window too large for the fixed scratch (n_bins * n_nodes must stay below ~1.3 M)");
-    // bin groups: as many as fill the GPU and fit in the remaining scratch
-    int groups = std::min(n_bins, std::max(1, (152 * 4 + ntp - 1) / ntp));
-    const size_t per_group = sizeof(float) * 7 * (size_t)P;
-    while (groups > 1 && off_part + per_group * groups > kScratchBytes) --groups;
-    const int group_bins = (n_bins + groups - 1) / groups;
-    groups = (n_bins + group_bins - 1) / group_bins;
-
-    int dev = 0;
+    int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     void* base = nullptr;
-    if (e == cudaSuccess) e = scratch_address(dev, &base);
+    if (e == cudaSuccess) e = scratch_address(dev, &base, &sms);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return noalloc_fail(FC_ERR_CUDA, cudaGetErrorString(e));
     }
+    // bin groups: as many as fill the GPU (two CTAs per SM, twice over) and fit in the
+    // remaining scratch
+    int groups = std::min(n_bins, std::max(1, (sms * 4 + ntp - 1) / ntp));
+    const size_t per_group = sizeof(float) * 7 * (size_t)P;
+    while (groups > 1 && off_part + per_group * groups > kScratchBytes) --groups;
+    const int group_bins = (n_bins + groups - 1) / groups;
+    groups = (n_bins + group_bins - 1) / group_bins;
     unsigned char* s = static_cast<unsigned char*>(base);
     FcCtrl* ctrl = reinterpret_cast<FcCtrl*>(s);
     double* psd = reinterpret_cast<double*>(s + off_psd);
@@ -112,6 +147,16 @@ extern "C" fc_status fc_window_networks_noalloc(const float* spectra, int n_tria
         k_noalloc_tiles<<<(ntp + 255) / 256, 256, 0, st>>>(ta, tb, nt);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess) {
+        const long long count = 2LL * n_trials * n_bins * n_nodes;
+        const long long blocks = std::min<long long>((count + 255) / 256, 8LL * sms);
+        k_noalloc_max<<<(unsigned)std::max(1LL, blocks), 256, 0, st>>>(spectra, count, ctrl);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_noalloc_scale<<<1, 1, 0, st>>>(ctrl);
+        e = cudaGetLastError();
+    }
     const float2* ring = reinterpret_cast<const float2*>(spectra);
     if (e == cudaSuccess) {
         NodeArgs na{ring, psd, inv, n_trials, n_nodes, n_bins, n_trials, 1, ctrl, n_trials};
@@ -123,9 +168,7 @@ extern "C" fc_status fc_window_networks_noalloc(const float* spectra, int n_tria
     pa.acc = nullptr;
     pa.tile_a = ta;
     pa.tile_b = tb;
-    // the kernels address network planes 2..8 (the spectral metrics) of a [9][P] block:
-    // base the block two planes before `out` so that they land in out[0..6][P]
-    pa.net = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(out) - 2 * sizeof(float) * (size_t)P);
+    pa.net_spec = out;  // the seven spectral planes, COH .. DSWPLI
     pa.partial = partial;
     pa.slots = n_trials;
     pa.n = n_nodes;
@@ -142,7 +185,7 @@ extern "C" fc_status fc_window_networks_noalloc(const float* spectra, int n_tria
     pa.update = 1;
     pa.write_acc = 0;
     pa.count = n_trials;
-    pa.grid_ctas = 2 * 152;
+    pa.grid_ctas = 2 * sms;
     pa.ctrl = ctrl;
     if (e == cudaSuccess) e = launch_window_sums(pa, st);
     if (e == cudaSuccess && groups > 1) e = launch_band_reduce(pa, st);

@@ -405,7 +405,7 @@ fc_status fc_server_create(const fc_server_config* cfg, fc_server** out) {
         return sfail(FC_ERR_INVALID_ARG, "max_batch must be 0..32");
     }
     cudaGetDevice(&sv->device);
-    cudaDeviceGetAttribute(&sv->num_sms, cudaDevAttrMultiProcessorCount, sv->device);
+    sv->num_sms = fc_device_sms(sv->device);
     if (cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete sv;
         return sfail(FC_ERR_CUDA, "stream creation failed");

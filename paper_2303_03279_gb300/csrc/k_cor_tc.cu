@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cor_tc(CorTcArgs a) {
 
 cudaError_t launch_cor_tc_pack(const CorTcArgs& a, cudaStream_t st) {
     if (a.count - a.write_from <= 0) return cudaSuccess;
-    k_cor_tc_pack<<<152 * 8, 256, 0, st>>>(a);
+    k_cor_tc_pack<<<fc_device_sms() * 8, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

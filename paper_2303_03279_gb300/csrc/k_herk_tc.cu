@@ -414,7 +414,7 @@ __global__ void k_herk_band(HerkArgs a) {
 }  // namespace
 
 cudaError_t launch_pack_operands(const PackArgs& a, cudaStream_t st) {
-    k_pack_operands<<<152 * 8, 256, 0, st>>>(a);
+    k_pack_operands<<<fc_device_sms() * 8, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -38,9 +38,11 @@ __device__ __forceinline__ void node_elem(const NodeArgs& a, int e) {
     } else {
         const long long end = c->pushed + a.count;
         const long long start = (a.W > 0 && end > a.W) ? end - a.W : 0;
+        const float sc = c->in_scale;  // 0 for sessions (their ring holds prescaled spectra)
         s = 0.0;
         for (long long k = start; k < end; ++k) {
-            const float2 X = a.ring[((size_t)(k % a.slots) * a.B + f) * a.n + i];
+            float2 X = a.ring[((size_t)(k % a.slots) * a.B + f) * a.n + i];
+            if (sc != 0.f) X = make_float2(__fmul_rn(X.x, sc), __fmul_rn(X.y, sc));
             s += (double)X.x * X.x + (double)X.y * X.y;
         }
     }
@@ -111,12 +113,14 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
             const int kn = min(WK, K - k0);
             __syncthreads();
             bool any_tiny = false;
+            const float sc = c->in_scale;  // 0 for sessions (their ring holds prescaled spectra)
             for (int e = tid; e < WK * 2 * FC_T; e += 256) {
                 const int kk = e / (2 * FC_T), side = (e / FC_T) & 1, l = e % FC_T;
                 const int node = (side ? tb : ta) * FC_T + l;
                 float2 X = make_float2(0.f, 0.f);
                 if (kk < kn && node < a.n)
                     X = a.ring[((size_t)((wf.start + k0 + kk) % a.slots) * a.B + f) * a.n + node];
+                if (sc != 0.f) X = make_float2(__fmul_rn(X.x, sc), __fmul_rn(X.y, sc));
                 const float2 u = phasor_of(X);
                 sn[kk][side][0][l] = X.x;
                 sn[kk][side][1][l] = X.y;
@@ -250,7 +254,7 @@ __global__ void k_band_reduce(PairArgs a) {
         if (!(a.mask & (1u << (m + 2)))) continue;
         float s = 0.f;
         for (int g = 0; g < a.groups; ++g) s = __fadd_rn(s, a.partial[((size_t)g * 7 + m) * a.P + p]);
-        a.net[(size_t)(m + 2) * a.P + p] = __fmul_rn(s, invB);
+        a.net_spec[(size_t)m * a.P + p] = __fmul_rn(s, invB);
     }
 }
 

@@ -195,7 +195,8 @@ __global__ void k_commit_batch(CommitBatch b) {
 
 cudaError_t launch_validate(const float* x, long long count, FcCtrl* ctrl, cudaStream_t st) {
     long long blocks = (count + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    const long long cap = 16LL * fc_device_sms();
+    if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     k_validate<<<(unsigned)blocks, 256, 0, st>>>(x, count, ctrl);
     return cudaGetLastError();
@@ -212,7 +213,8 @@ cudaError_t launch_spectrum(const SpectrumArgs& a, cudaStream_t st) {
 cudaError_t launch_calibrate(const SpectrumArgs& a, cudaStream_t st, int phase) {
     long long work = (long long)(a.count - a.write_from) * a.B * a.n;
     long long blocks = phase == 2 ? 1 : (work + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    const long long cap = 8LL * fc_device_sms();
+    if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     k_calibrate<<<(unsigned)blocks, 256, 0, st>>>(a, phase);
     return cudaGetLastError();
@@ -223,7 +225,7 @@ cudaError_t launch_validate_batch(const PreBatch& b, cudaStream_t st) {
     long long most = 0;
     for (int s = 0; s < b.nsess; ++s) most = std::max(most, b.val_prefix[s + 1] - b.val_prefix[s]);
     long long blocks = (most + 255) / 256;
-    blocks = std::min(blocks, std::max(1LL, 152LL * 16 / b.nsess));
+    blocks = std::min(blocks, std::max(1LL, 16LL * fc_device_sms() / b.nsess));
     if (blocks < 1) blocks = 1;
     k_validate_batch<<<dim3((unsigned)blocks, b.nsess), 256, 0, st>>>(b);
     return cudaGetLastError();

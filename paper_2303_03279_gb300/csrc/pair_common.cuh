@@ -114,7 +114,7 @@ __device__ __forceinline__ void write_band(const PairArgs& a, int g, const float
     for (int m = 0; m < 7; ++m) {
         if (!(a.mask & (1u << (m + 2)))) continue;
         if (a.groups == 1) {
-            float* dst = a.net + (size_t)(m + 2) * a.P;
+            float* dst = a.net_spec + (size_t)m * a.P;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if (vmask & (1u << q)) dst[packed_index(gi, gj0 + q, a.n)] = __fmul_rn(band[m][q], invB);

@@ -81,6 +81,51 @@ def test_mixed_full_window_meg_sampled(prec):
         _check(s, K, I, J, prec=prec)
 
 
+def _herk_groups(ntp128, nsel, sms, P, cap):
+    """Bin groups the library picks for the tensor-core band sums (its makespan model:
+    ceil(units / SMs) rounds of a group's bins at ~17 us per tile pair and bin, plus the
+    band-sum planes' traffic), restated here only to assert that a case runs several groups."""
+    best, groups = None, 1
+    for g in range(1, min(nsel, max(1, cap)) + 1):
+        gb = -(-nsel // g)
+        if -(-nsel // gb) != g:
+            continue
+        rounds = -(-(ntp128 * g) // sms)
+        t = rounds * gb * 17e-6 + g * 3 * P * 8 / 6e12
+        if best is None or t < best:
+            best, groups = t, g
+    return groups
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_mixed_band_groups_against_oracle(prec):
+    """1100 nodes x 40 bins: the tensor-core band sums run over several bin groups (the first
+    bin of a (tile pair, bin group) unit stores its values, the later bins add to them by
+    reductions), over nine 128-node tiles of which the last is ragged (76 nodes). Sampled
+    pairs, including pairs across the 128-node tile edges, inside diagonal tiles and in the
+    ragged tile, against the oracle on the GPU's spectra: COH, IMAGCOHY, PLV within 5e-3,
+    PLI, USPLI, WPLI, DSWPLI within 1e-5 with exact sign sums."""
+    n, N, W = 1100, 500, 20
+    nt = -(-n // 128)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert _herk_groups(nt * (nt + 1) // 2, 40, sms, n * (n - 1) // 2, 40) > 1
+    x = white_trials(33, W, n, N)
+    x[:, 7] += 0.8 * x[:, 1090]  # a coupled pair reaching into the ragged tile
+    rng = np.random.default_rng(5)
+    with fc.Session(n, N, 1000.0, (4.0, 44.0, 1000), "hann", fc.FC_SPECTRAL_METRICS, W,
+                    mode=fc.FC_MODE_FULL, precision=PRECISIONS[prec]) as s:
+        assert s.B == 40
+        s.push(x)
+        iu = np.triu_indices(n, 1)
+        pick = rng.choice(len(iu[0]), 3000, replace=False)
+        I = np.concatenate([iu[0][pick], [0, 127, 127, 128, 255, 1023, 1023, 1024, 7, 1098, 0]])
+        J = np.concatenate([iu[1][pick], [1, 128, 1099, 255, 256, 1024, 1099, 1099, 1090, 1099, 1099]])
+        errs = _check(s, W, I, J, prec=prec)
+        coh = s.network("COH", packed=True)[0]
+        assert coh[packed_index(7, 1090, n)] > 0.5  # the coupled pair stands out
+    assert errs["COH"] > 0.0  # the contracted metrics carry the operand rounding
+
+
 def test_mixed_window_fill_and_slide():
     # the window fills (K < W), then slides; the contraction length follows K
     n, N, W = 150, 128, 6

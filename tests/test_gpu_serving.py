@@ -1,5 +1,8 @@
 """Serving: many sessions on one GPU, continuous batching, admission by device-memory budget.
 
+* Each served session's networks match the FP64 oracle (Supplementary Information 1) on the
+  window's spectra: every metric within 1e-5 and the sign sums exactly on the GPU's FP32
+  spectra, and COH, IMAGCOHY, PLV, WPLI within 1e-5 on FP64 spectra of the raw trials.
 * Each session's networks are bit-identical when it is served alone and when its trials
   share launches with other sessions (the batched kernel computes every pair with the same
   arithmetic), and agree with a standalone session fed the same trials (1e-5).
@@ -11,8 +14,9 @@
 import numpy as np
 import pytest
 
+import oracle as O
 from synth import white_trials
-from _fc_helpers import assert_close
+from _fc_helpers import assert_close, oracle_spectral, window_spectra
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -93,6 +97,44 @@ def test_same_alone_and_in_the_mix(launch_blocks):
         alone, _, _ = _serve([k], interleave=False)
         for m in SPECTRAL:
             assert np.array_equal(alone[k][m], mixed[k][m], equal_nan=True), (k, m)
+
+
+@pytest.mark.parametrize("launch_blocks", [0, 100])
+def test_served_networks_match_the_oracle(launch_blocks):
+    """The batched serving kernels (validation, spectrum and per-node sums of several sessions
+    per launch, the multi-session streaming kernel, the batched commit) against the oracle.
+
+    Every session's first push runs alone (it calibrates the prescale); its later pushes join
+    the batched launches. launch_blocks = 100 splits each push of the 128-node session over
+    several launches shared with the other sessions. The oracle runs on the spectra of the
+    window: the GPU's own FP32 spectra (read from a standalone session fed the same trials:
+    the batched spectrum kernel computes the same tiles with the same arithmetic and the same
+    prescale), every metric within 1e-5 and the band sum of |sign sums| exactly; and FP64
+    spectra of the raw trials, COH, IMAGCOHY, PLV and WPLI within 1e-5.
+    """
+    served, stats, res = _serve([0, 1, 2], interleave=True, launch_blocks=launch_blocks)
+    assert all(r[2] == fc.FC_OK for r in res)
+    assert max(r[5] for r in res) > 1  # launches carried several sessions
+    xs = _trials()
+    for k, (n, N, fs, band, W, T) in enumerate(SESSION_SHAPES):
+        K = min(W, T)
+        with fc.Session(n, N, fs, band, "hann", fc.FC_SPECTRAL_METRICS, W) as s:
+            for t in range(T):
+                s.push(xs[k][t])
+            X = window_spectra(s, K)  # [K][n][B] complex64
+            B = s.B
+        ref = oracle_spectral(X.astype(np.complex128))
+        for m in SPECTRAL:
+            assert_close(served[k][m], ref[m], what=f"served {m} vs oracle (GPU spectra), cfg {k}")
+        # PLI = (1/B) sum_b |S_b| / K: the integer sum over bins of |sign sums| is exact
+        got_s = np.rint(served[k]["PLI"].astype(np.float64) * K * B)
+        assert np.array_equal(got_s, np.rint(ref["PLI"] * K * B)), f"sign sums, cfg {k}"
+        bins = O.band_bins(fs, band[2], band[0], band[1])
+        assert len(bins) == B
+        X64 = O.spectra(xs[k][T - K:T], bins, band[2], "hann")  # FP64 spectra of the raw trials
+        ref64 = oracle_spectral(X64)
+        for m in ("COH", "IMAGCOHY", "PLV", "WPLI"):
+            assert_close(served[k][m], ref64[m], what=f"served {m} vs oracle (FP64 spectra), cfg {k}")
 
 
 def test_served_equals_standalone_session_and_plain_mode():

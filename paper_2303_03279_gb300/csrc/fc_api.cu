@@ -334,9 +334,33 @@ void herk_groups(long long ntp, int nsel, int sms, long long P, int cap, int& gr
     }
 }
 
+// Bin groups of the non-linear sums kernel (one CTA per 32-node tile pair and group of
+// selected bins, nonlinear_ctas_per_sm() CTAs per SM): the count g <= cap minimizing the
+// busiest slot's work (ceil(ntp g / slots) rounds of ceil(nsel / g) bins of K trials, about
+// 0.1 us per bin and trial) plus, for g > 1, writing and reducing the g x 4 band planes
+// (~5 TB/s); every group holds at least one bin.
+void nonlin_groups(long long ntp, int nsel, long long P, int K, int sms, int cap, int& groups, int& group_bins) {
+    groups = 1;
+    group_bins = nsel;
+    const long long slots = (long long)sms * nonlinear_ctas_per_sm();
+    double best = -1.0;
+    for (int g = 1; g <= std::min(nsel, std::max(1, cap)); ++g) {
+        const int gb = (nsel + g - 1) / g;
+        if ((nsel + gb - 1) / gb != g) continue;
+        const long long rounds = (ntp * g + slots - 1) / slots;
+        const double t = (double)rounds * gb * (K > 0 ? K : 1) * 0.1e-6 + (g > 1 ? g * 4.0 * (double)P * 8.0 / 5.0e12 : 0.0);
+        if (best < 0.0 || t < best) {
+            best = t;
+            groups = g;
+            group_bins = gb;
+        }
+    }
+}
+
 // Spectral pair sums over the whole window (bulk push, re-sum, full mode).
 fc_status stage_window(fc_session* s, int count, bool write_acc) {
     NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, 1, s->ctrl, count};
+    if (s->ops && !write_acc) na.tiny = s->tiny_flags;  // read by the non-linear sums
     LAUNCH(FC_K_NODE, launch_node(na, s->stream));
     if (s->ops && !write_acc) {
         // mixed precision: linear sums (COH, IMAGCOHY, PLV) on the tensor cores, the
@@ -382,6 +406,10 @@ fc_status stage_window(fc_session* s, int count, bool write_acc) {
         }
         PairArgs pn = pair_args(s, false, count);
         pn.mask = s->mask & (FC_PLI | FC_USPLI | FC_WPLI | FC_DSWPLI);
+        pn.tiny = s->tiny_flags;
+        const long long k_est = std::min<long long>(s->W, s->enqueued + count);
+        nonlin_groups(s->ntp, s->sel1 - s->sel0, s->P, (int)k_est, s->num_sms, s->partial_groups, pn.groups,
+                      pn.group_bins);
         if (pn.mask) {
             LAUNCH(FC_K_WINDOW, launch_nonlinear_sums(pn, s->stream));
             if (pn.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pn, s->stream));
@@ -827,11 +855,13 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
             TRY(upload(s, s->tile_a128, ta.data(), ta.size() * sizeof(unsigned short)));
             TRY(upload(s, s->tile_b128, tb.data(), tb.size() * sizeof(unsigned short)));
             TRY(alloc_zero(s, (size_t)s->nt128 * B * 4 * s->nchunks * herk_chunk_bytes(), &s->ops));
+            TRY(alloc_zero(s, (size_t)B * n_nodes, &s->tiny_flags));
             int gb;
             herk_groups(s->ntp128, B, s->num_sms, (long long)s->P, B, s->herk_gcap, gb);
             TRY(alloc_zero(s, (size_t)s->herk_gcap * 3 * s->P, &s->herk_part));
         }
         if (max_groups > 1) TRY(alloc_zero(s, (size_t)max_groups * 7 * s->P, &s->partial));
+        s->partial_groups = max_groups > 1 ? max_groups : 1;
     }  // spectral state
     TRY(alloc_zero(s, (size_t)FC_NMETRIC * s->P, &s->net));
     if (s->time_mask & FC_COR) {

@@ -112,6 +112,7 @@ struct fc_session {
     unsigned short* tile_b; // [ntp]
     float* net;             // [FC_NMETRIC][P]
     float* partial;         // [groups][7][P] band partial sums (when groups > 1)
+    int partial_groups;     // bin groups the partial planes are allocated for
     float* zring;           // COR: [slots][n][N] normalized trials
     float* cor_acc;         // COR: [2][P] double-float
     float* xcor_vals;       // XCOR: [slots][P] per-trial values
@@ -126,6 +127,7 @@ struct fc_session {
     unsigned short* tile_a128;
     unsigned short* tile_b128;
     unsigned char* ops;     // packed operands [nt128][B][4][nchunks][16 KB]
+    unsigned char* tiny_flags;  // [B][n] a trial of the window has a tiny component (mixed path)
     unsigned char* cor_ops; // COR split-TF32 operand ring [slots][cor_nt][cor_nchunks][2][16 KB]
     int cor_nt, cor_ntp, cor_nchunks;
     float* herk_part;       // [herk_gcap][3][P] band sums of COH, IMAGCOHY, PLV per bin group
@@ -179,6 +181,7 @@ struct NodeArgs {
     int mode;   // 0 = add newest / subtract leaving, 1 = recompute from the window
     FcCtrl* ctrl;
     int count;  // trials pushed by this call (mode 1: the window ends at pushed + count)
+    unsigned char* tiny;  // mode 1, optional: [B][n] 1 where a trial of the window has a tiny component
 };
 cudaError_t launch_node(const NodeArgs& a, cudaStream_t st);
 
@@ -203,6 +206,7 @@ struct PairArgs {
     int count;         // trials pushed by this call (window end = pushed + count)
     int grid_ctas;     // persistent grid size of the streaming kernel
     const FcCtrl* ctrl;
+    const unsigned char* tiny;  // non-linear sums: [B][n] tiny-component flags of the window (k_node)
 };
 cudaError_t launch_stream_update(const PairArgs& a, cudaStream_t st);
 
@@ -248,7 +252,9 @@ cudaError_t launch_herk_tc(const HerkArgs& a, cudaStream_t st);
 cudaError_t launch_herk_band(const HerkArgs& a, cudaStream_t st);
 size_t herk_chunk_bytes();
 // Non-linear sums only (signs, |Im|, Im, Im^2) with the PLI/USPLI/WPLI/DSWPLI finalize.
+// Bin groups partition the selected bins fsel0 .. fsel1 - 1 (group_bins each).
 cudaError_t launch_nonlinear_sums(const PairArgs& a, cudaStream_t st);
+int nonlinear_ctas_per_sm();
 
 struct CommitArgs {
     FcCtrl* ctrl;

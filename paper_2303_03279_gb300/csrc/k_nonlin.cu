@@ -4,13 +4,25 @@
 //   PLI = |sum sign(Im CSD)| / K, USPLI from the same integer,
 //   WPLI = |sum Im| / sum |Im|,  DSWPLI = ((sum Im)^2 - sum Im^2) / ((sum |Im|)^2 - sum Im^2),
 // with Im = Im(X_i X_j*). Here they run on the CUDA cores beside the tensor-core linear
-// sums (k_herk_tc.cu), which produce COH, IMAGCOHY and PLV. Im and its exact sign use the
-// same term code as the exact path (terms.cuh). The sums run in FP32 over chunks of 16
-// trials and each chunk's partial sums (Im, |Im|, Im^2) are promoted to double-word
-// accumulators, so the debiased cancellation (sum Im)^2 - sum Im^2 is evaluated from
-// FP64-class sums; the sign count is an exact int32.
+// sums (k_herk_tc.cu), which produce COH, IMAGCOHY and PLV. Im and its exact sign come from
+// Kahan's 2x2 determinant (terms.cuh), so the sign counts equal those of exact arithmetic
+// on the stored FP32 spectra.
 //
-// CTA: one 32 x 32 tile pair x a group of bins; thread: 4 adjacent pairs of the tile.
+// Sums. The signs are tallied as counts of positive and of negative terms in FP32 (exact
+// integers below 2^24 trials). Im, |Im| and Im^2 are summed in FP32 over chunks of NK
+// trials and each chunk's partial sums are added to double-word window sums, so the
+// debiased differences x^2 - s are evaluated from FP64-class sums with the exact square
+// of their leading word (df_sq_minus). Where at most one term of the window is nonzero
+// both differences are exactly 0 (sum_{k != l} of products), and DSWPLI is 0, as the
+// definition's zero denominator gives; the counts decide this exactly.
+//
+// Work split: a CTA of 128 threads takes one 32 x 32 tile pair and a group of bins; each
+// thread holds a 2 x 4 register tile of pairs (rows 2 rg, 2 rg + 1; columns 4 cg .. 4 cg + 3),
+// so every staged spectrum value feeds 4 or 2 pairs per load. Row spectra are staged as
+// (a, a, b, b) and (-a, -a) so that they load straight into packed FP32x2 operands; column
+// spectra as planes of a and b. Per pair and trial the loop issues the determinant (two
+// packed FMAs, a packed multiply and FMA for two pairs), two compare-to-float tallies, one
+// absolute add and a packed add and FMA for two pairs.
 #include "df32.cuh"
 #include "fc_internal.h"
 #include "pair_common.cuh"
@@ -22,9 +34,38 @@ namespace {
 
 using namespace fcpair;
 
-constexpr int NK = 16;  // trials per staged chunk (and per FP32 partial sum)
+constexpr int NK = 36;         // most trials per staged chunk (and per FP32 partial sum)
+constexpr int NL_THREADS = 128;
 
-__global__ void __launch_bounds__(256, 3) k_nonlin(PairArgs a) {
+// 1.0f if x > 0 (resp. x < 0) else 0.0f: one exact compare each.
+__device__ __forceinline__ float gt0(float x) {
+    float r;
+    asm("set.gt.f32.f32 %0, %1, 0f00000000;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float lt0(float x) {
+    float r;
+    asm("set.lt.f32.f32 %0, %1, 0f00000000;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+struct NlSmem {
+    float2 raw[NK][2 * FC_T];   // the next chunk's spectra as copied (row tile, column tile)
+    float4 rowv[NK][FC_T];  // row node i: (a, a, b, b)
+    float2 rown[NK][FC_T];  // row node i: (-a, -a)
+    float4 cola[NK][FC_T / 4];  // column nodes: a, four per vector
+    float4 colb[NK][FC_T / 4];  //                b
+    float band[4][FC_T][FC_T];  // band sums of PLI, USPLI, WPLI, DSWPLI per pair
+};
+
+__global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
     const long long end = c->pushed + a.count;
@@ -32,137 +73,224 @@ __global__ void __launch_bounds__(256, 3) k_nonlin(PairArgs a) {
     const int K = (int)(end - start);
     if (K <= 0) return;
     const KConst kc = make_kconst(K);
+    extern __shared__ __align__(16) unsigned char nl_smem_raw[];
+    NlSmem& sm = *reinterpret_cast<NlSmem*>(nl_smem_raw);
 
+    // bin group g: selected bins fsel0 + g group_bins .. (bins outside the selected band take
+    // no part in the average and are not computed)
     const int tp = blockIdx.x, g = blockIdx.y;
-    const int f0 = g * a.group_bins, f1 = min(a.B, f0 + a.group_bins);
+    const int fa = a.fsel0 + g * a.group_bins, fb = min(a.fsel1, fa + a.group_bins);
     const int ta = a.tile_a[tp], tb = a.tile_b[tp];
-    const int tid = threadIdx.x, li = tid >> 3, lj0 = (tid & 7) * 4;
-    const unsigned vmask = pair_mask(ta, tb, li, lj0, a.n);
-    const int gi = ta * FC_T + li, gj0 = tb * FC_T + lj0;
-
-    // planar: [trial][node] real parts, imaginary parts, tiny flags (two adjacent column
-    // nodes load as one packed operand)
-    __shared__ __align__(16) float sa[NK][2 * FC_T];
-    __shared__ __align__(16) float sb[NK][2 * FC_T];
-    __shared__ unsigned char stiny[NK][2 * FC_T];
-
-    float band[7][4];
+    const int tid = threadIdx.x, rg = tid >> 3, cg = tid & 7;
+    const int li0 = 2 * rg, lj0 = 4 * cg;
+    unsigned vmask = 0;  // bit 4 r + q: pair (li0 + r, lj0 + q)
 #pragma unroll
-    for (int m = 0; m < 7; ++m)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) band[m][q] = 0.f;
-
-    for (int f = f0; f < f1; ++f) {
-        df32 s_im[4], s_sq[4], s_abs[4];
-        int s_sg[4];
+    for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            s_im[q] = s_sq[q] = s_abs[q] = df_make(0.f, 0.f);
-            s_sg[q] = 0;
+            const int gi = ta * FC_T + li0 + r, gj = tb * FC_T + lj0 + q;
+            if (gi < a.n && gj < a.n && (ta != tb || lj0 + q > li0 + r)) vmask |= 1u << (4 * r + q);
         }
-        for (int k0 = 0; k0 < K; k0 += NK) {
-            const int kn = min(NK, K - k0);
-            __syncthreads();
-            bool any_tiny = false;
-            for (int e = tid; e < kn * 2 * FC_T; e += 256) {
-                const int kk = e / (2 * FC_T), l = e % (2 * FC_T);
-                const int node = l < FC_T ? ta * FC_T + l : tb * FC_T + l - FC_T;
-                const long long trial = start + k0 + kk;
-                float2 X = make_float2(0.f, 0.f);
-                if (node < a.n) X = a.ring[((size_t)(trial % a.slots) * a.B + f) * a.n + node];
-                sa[kk][l] = X.x;
-                sb[kk][l] = X.y;
-                const bool tn = node_tiny(X);
-                stiny[kk][l] = tn ? 1 : 0;
-                any_tiny |= tn;
-            }
-            // chunks without a tiny node (the rule) run a loop with no FP64 branch at all
-            const bool chunk_tiny = __syncthreads_or(any_tiny ? 1 : 0) != 0;
-            if (!vmask) continue;
-            // FP32 partial sums of this chunk, two column pairs per packed lane pair
-            float2 p_im[2], p_sq[2], p_abs[2], p_sqe[2], p_pos[2], p_neg[2];
+    for (int e = tid; e < 4 * FC_TT; e += NL_THREADS) (&sm.band[0][0][0])[e] = 0.f;
+
+    // Chunks of NK trials of the bins fa .. fb - 1 in order. Thread tid always copies and
+    // converts node l = tid % 64 of the two tiles, trials kk = tid / 64 + 2 q of a chunk: the
+    // copy of chunk c + 1 (cp.async, asynchronous) runs while chunk c is computed.
+    const int l_node = tid & 63, kk0 = tid >> 6;
+    const int node = l_node < FC_T ? ta * FC_T + l_node : tb * FC_T + l_node - FC_T;
+    const bool node_ok = node < a.n;
+    const int nchunk = (K + NK - 1) / NK;
+    const int csize = (K + nchunk - 1) / nchunk;  // balanced chunks of at most NK trials
+    const int slot_start = (int)(start % a.slots);
+    constexpr int PER = NK * 2 * FC_T / NL_THREADS;  // elements per thread and chunk
+    auto issue_copy = [&](int f, int k0) {
+        const int kn = min(csize, K - k0);
+        int slot = slot_start + k0 + kk0;
+        while (slot >= a.slots) slot -= a.slots;
+        const float2* src = a.ring + (size_t)f * a.n + node;
+        const size_t slot_stride = (size_t)a.B * a.n;
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
-                p_im[h] = p_sq[h] = p_abs[h] = p_sqe[h] = p_pos[h] = p_neg[h] = make_float2(0.f, 0.f);
+        for (int q = 0; q < PER; ++q) {
+            const int kk = kk0 + 2 * q;
+            if (kk < kn && node_ok) cp_async8(&sm.raw[kk][l_node], src + (size_t)slot * slot_stride);
+            slot += 2;
+            if (slot >= a.slots) slot -= a.slots;
+        }
+        cp_async_commit();
+    };
+    if (fa < fb) issue_copy(fa, 0);
+
+    for (int f = fa; f < fb; ++f) {
+        // window sums, packed pair q = 2 r + h covers pairs (li0 + r, lj0 + 2h + {0, 1});
+        // pos / neg: counts of positive / negative terms (exact integers in FP32)
+        float2 pos[4], neg[4], imh[4], iml[4], abh[4], abl[4], sqh[4], sql[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            pos[q] = neg[q] = imh[q] = iml[q] = abh[q] = abl[q] = sqh[q] = sql[q] = make_float2(0.f, 0.f);
+        // nodes with a tiny component somewhere in the window (flags of the per-node sums
+        // kernel) take the FP64 branch; bins without one (the rule) run a loop without it
+        // (no flags given: every node takes it)
+        auto tiny_at = [&](int node) { return a.tiny ? a.tiny[(size_t)f * a.n + min(node, a.n - 1)] != 0 : true; };
+        unsigned tmask = 0;  // bits 0, 1: rows li0, li0 + 1; bits 2 .. 5: columns lj0 .. lj0 + 3
+#pragma unroll
+        for (int r = 0; r < 2; ++r) tmask |= tiny_at(ta * FC_T + li0 + r) ? 1u << r : 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tmask |= tiny_at(tb * FC_T + lj0 + q) ? 4u << q : 0u;
+        const bool bin_tiny = __syncthreads_or(tmask ? 1 : 0) != 0;
+        for (int ci = 0; ci < nchunk; ++ci) {
+            const int k0 = ci * csize;
+            const int kn = min(csize, K - k0);
+            cp_async_wait_all();
+            __syncthreads();  // the chunk has landed; every thread is done with the previous one
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int kk = kk0 + 2 * q;
+                float2 X = make_float2(0.f, 0.f);
+                if (kk < kn && node_ok) X = sm.raw[kk][l_node];
+                if (l_node < FC_T) {
+                    sm.rowv[kk][l_node] = make_float4(X.x, X.x, X.y, X.y);
+                    sm.rown[kk][l_node] = make_float2(-X.x, -X.x);
+                } else {
+                    reinterpret_cast<float*>(sm.cola[kk])[l_node - FC_T] = X.x;
+                    reinterpret_cast<float*>(sm.colb[kk])[l_node - FC_T] = X.y;
+                }
+            }
+            __syncthreads();  // converted; the raw buffer is free again
+            // start copying the next chunk (this bin's or the next's)
+            if (ci + 1 < nchunk)
+                issue_copy(f, k0 + csize);
+            else if (f + 1 < fb)
+                issue_copy(f + 1, 0);
+            if (!vmask) continue;
+            float2 pim[4], pab[4], psq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pim[q] = pab[q] = psq[q] = make_float2(0.f, 0.f);
             auto chunk = [&](auto tiny_c) {
                 constexpr bool TINY = decltype(tiny_c)::value;
+#pragma unroll 2
                 for (int kk = 0; kk < kn; ++kk) {
-                    const float ai = sa[kk][li], bi = sb[kk][li];
-                    const float2 bi2 = f2(bi), ai2 = f2(ai), nai2 = f2(-ai);
-                    const bool ti = TINY && stiny[kk][li] != 0;
+                    const float4 ca = sm.cola[kk][cg], cb = sm.colb[kk][cg];
+                    const float2 aj[2] = {make_float2(ca.x, ca.y), make_float2(ca.z, ca.w)};
+                    const float2 bj[2] = {make_float2(cb.x, cb.y), make_float2(cb.z, cb.w)};
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int j = FC_T + lj0 + 2 * h;
-                        const float2 aj = *reinterpret_cast<const float2*>(&sa[kk][j]);
-                        const float2 bj = *reinterpret_cast<const float2*>(&sb[kk][j]);
-                        // Im(X_i X_j*) and its exact sign, as in pair_terms2 (terms.cuh)
-                        float2 im = kahan_im2(bi2, ai2, nai2, aj, bj);
-                        if (TINY) {
-                            int sg0 = sign_of(im.x), sg1 = sign_of(im.y);
-                            if (ti || stiny[kk][j]) im_sign_fp64(ai, bi, aj.x, bj.x, im.x, sg0);
-                            if (ti || stiny[kk][j + 1]) im_sign_fp64(ai, bi, aj.y, bj.y, im.y, sg1);
-                            s_sg[2 * h] += sg0;
-                            s_sg[2 * h + 1] += sg1;
-                        } else {
-                            // sign tallies as exact small FP32 counts (at most NK per chunk)
-                            p_pos[h] = add2(p_pos[h], make_float2(im.x > 0.f ? 1.f : 0.f, im.y > 0.f ? 1.f : 0.f));
-                            p_neg[h] = add2(p_neg[h], make_float2(im.x < 0.f ? 1.f : 0.f, im.y < 0.f ? 1.f : 0.f));
+                    for (int r = 0; r < 2; ++r) {
+                        const float4 rv = sm.rowv[kk][li0 + r];
+                        const float2 rn = sm.rown[kk][li0 + r];
+                        const float2 ai = make_float2(rv.x, rv.y), bi = make_float2(rv.z, rv.w);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int q = 2 * r + h;
+                            float2 im = kahan_im2(bi, ai, rn, aj[h], bj[h]);
+                            if (TINY) {
+                                int s0 = sign_of(im.x), s1 = sign_of(im.y);
+                                if (tmask & ((1u << r) | (4u << (2 * h)))) im_sign_fp64(rv.x, rv.z, aj[h].x, bj[h].x, im.x, s0);
+                                if (tmask & ((1u << r) | (8u << (2 * h)))) im_sign_fp64(rv.x, rv.z, aj[h].y, bj[h].y, im.y, s1);
+                                pos[q] = add2(pos[q], make_float2(s0 > 0 ? 1.f : 0.f, s1 > 0 ? 1.f : 0.f));
+                                neg[q] = add2(neg[q], make_float2(s0 < 0 ? 1.f : 0.f, s1 < 0 ? 1.f : 0.f));
+                            } else {
+                                pos[q] = add2(pos[q], make_float2(gt0(im.x), gt0(im.y)));
+                                neg[q] = add2(neg[q], make_float2(lt0(im.x), lt0(im.y)));
+                            }
+                            pab[q] = make_float2(__fadd_rn(pab[q].x, fabsf(im.x)), __fadd_rn(pab[q].y, fabsf(im.y)));
+                            pim[q] = add2(pim[q], im);
+                            psq[q] = fma2(im, im, psq[q]);
                         }
-                        p_abs[h] = make_float2(__fadd_rn(p_abs[h].x, fabsf(im.x)), __fadd_rn(p_abs[h].y, fabsf(im.y)));
-                        p_im[h] = add2(p_im[h], im);
-                        // im^2 as an exact two-product (t + r), scalar: the products feed additions;
-                        // a lone nonzero term then gives (sum |Im|)^2 - sum Im^2 = 0 exactly
-                        float2 t, r;
-                        two_prod(im.x, im.x, t.x, r.x);
-                        two_prod(im.y, im.y, t.y, r.y);
-                        p_sq[h] = make_float2(__fadd_rn(p_sq[h].x, t.x), __fadd_rn(p_sq[h].y, t.y));
-                        p_sqe[h] = add2(p_sqe[h], r);
                     }
                 }
             };
-            if (chunk_tiny)
+            if (bin_tiny)
                 chunk(std::true_type{});
             else
                 chunk(std::false_type{});
+            // the chunk's partial sums into the double-word window sums (lazy: renormalized
+            // once per bin)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float pim = (q & 1) ? p_im[q >> 1].y : p_im[q >> 1].x;
-                const float psq = (q & 1) ? p_sq[q >> 1].y : p_sq[q >> 1].x;
-                const float pse = (q & 1) ? p_sqe[q >> 1].y : p_sqe[q >> 1].x;
-                const float pab = (q & 1) ? p_abs[q >> 1].y : p_abs[q >> 1].x;
-                const float pps = (q & 1) ? p_pos[q >> 1].y : p_pos[q >> 1].x;
-                const float png = (q & 1) ? p_neg[q >> 1].y : p_neg[q >> 1].x;
-                s_sg[q] += (int)pps - (int)png;
-                s_im[q] = df_add_f(s_im[q], pim);
-                s_sq[q] = df_add_f(df_add_f(s_sq[q], psq), pse);
-                s_abs[q] = df_add_f(s_abs[q], pab);
+                acc2_f_lazy(imh[q], iml[q], pim[q]);
+                acc2_f_lazy(abh[q], abl[q], pab[q]);
+                acc2_f_lazy(sqh[q], sql[q], psq[q]);
             }
         }
-        if (vmask && f >= a.fsel0 && f < a.fsel1) {
+        if (vmask) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (!(vmask & (1u << q))) continue;
-                // PLI, USPLI, WPLI, DSWPLI (metric slots 3..6)
-                band[3][q] = __fadd_rn(band[3][q], __fmul_rn((float)abs(s_sg[q]), kc.inv_K));
-                const float usn = K <= 46340 ? (float)(s_sg[q] * s_sg[q] - K)
-                                             : (float)((long long)s_sg[q] * s_sg[q] - K);
-                band[4][q] = __fadd_rn(band[4][q], __fmul_rn(usn, kc.inv_KK1));
-                const float sim = df_to_f(s_im[q]);
-                const float sab = df_to_f(s_abs[q]);
-                band[5][q] = __fadd_rn(band[5][q], sab > 0.f ? __fdividef(fabsf(sim), sab) : 0.f);
-                const float num = df_sq_minus(s_im[q], s_sq[q]);
-                const float den = df_sq_minus(s_abs[q], s_sq[q]);
-                band[6][q] = __fadd_rn(band[6][q], den != 0.f ? __fdividef(num, den) : 0.f);
+                renorm2(imh[q], iml[q]);
+                renorm2(abh[q], abl[q]);
+                renorm2(sqh[q], sql[q]);
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                float4 acc[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) acc[m] = *reinterpret_cast<float4*>(&sm.band[m][li0 + r][lj0]);
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int q = 2 * r + (c4 >> 1);
+                    const bool y = c4 & 1;
+                    const float fp = y ? pos[q].y : pos[q].x, fn = y ? neg[q].y : neg[q].x;
+                    const int np = (int)fp, nn = (int)fn;
+                    const int sg = np - nn;
+                    const df32 sim = y ? df_make(imh[q].y, iml[q].y) : df_make(imh[q].x, iml[q].x);
+                    const df32 sab = y ? df_make(abh[q].y, abl[q].y) : df_make(abh[q].x, abl[q].x);
+                    const df32 ssq = y ? df_make(sqh[q].y, sql[q].y) : df_make(sqh[q].x, sql[q].x);
+                    // |S| and S^2 - K as floats, exactly, as in the session finalize
+                    float pli_n, usn;
+                    if (K <= 2048) {
+                        pli_n = small_int_to_float(abs(sg));
+                        usn = small_int_to_float(sg * sg - K);
+                    } else {
+                        pli_n = (float)abs(sg);
+                        usn = K <= 46340 ? (float)(sg * sg - K) : (float)((long long)sg * sg - K);
+                    }
+                    const float pli = __fmul_rn(pli_n, kc.inv_K);
+                    const float uspli = __fmul_rn(usn, kc.inv_KK1);
+                    const float fsab = df_to_f(sab);
+                    const float wpli = fsab > 0.f ? __fdividef(fabsf(df_to_f(sim)), fsab) : 0.f;
+                    float dswpli = 0.f;
+                    if (np + nn > 1) {  // two or more nonzero terms
+                        const float num = df_sq_minus(sim, ssq);
+                        const float den = df_sq_minus(sab, ssq);
+                        dswpli = den != 0.f ? __fdividef(num, den) : 0.f;
+                    }
+                    set4(acc[0], c4, __fadd_rn(get4(acc[0], c4), pli));
+                    set4(acc[1], c4, __fadd_rn(get4(acc[1], c4), uspli));
+                    set4(acc[2], c4, __fadd_rn(get4(acc[2], c4), wpli));
+                    set4(acc[3], c4, __fadd_rn(get4(acc[3], c4), dswpli));
+                }
+#pragma unroll
+                for (int m = 0; m < 4; ++m) *reinterpret_cast<float4*>(&sm.band[m][li0 + r][lj0]) = acc[m];
             }
         }
     }
-    if (vmask) write_band(a, g, band, gi, gj0, vmask, f1 - f0);
+    if (!vmask) return;
+    const float invB = 1.0f / (float)(a.fsel1 - a.fsel0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int mi = m + 3;  // PLI .. DSWPLI among the seven spectral planes
+        if (!(a.mask & (1u << (mi + 2)))) continue;
+        float* dst = a.groups == 1 ? a.net_spec + (size_t)mi * a.P : a.partial + ((size_t)g * 7 + mi) * a.P;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int gi = ta * FC_T + li0 + r;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!(vmask & (1u << (4 * r + q)))) continue;
+                const float v = sm.band[m][li0 + r][lj0 + q];
+                dst[packed_index(gi, tb * FC_T + lj0 + q, a.n)] = a.groups == 1 ? __fmul_rn(v, invB) : v;
+            }
+        }
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_nonlinear_sums(const PairArgs& a, cudaStream_t st) {
+    const int smem = (int)sizeof(NlSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_nonlin, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
     dim3 grid(a.ntp, a.groups);
-    k_nonlin<<<grid, 256, 0, st>>>(a);
+    k_nonlin<<<grid, NL_THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }
+
+int nonlinear_ctas_per_sm() { return 3; }

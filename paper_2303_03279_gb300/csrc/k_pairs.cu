@@ -40,11 +40,14 @@ __device__ __forceinline__ void node_elem(const NodeArgs& a, int e) {
         const long long start = (a.W > 0 && end > a.W) ? end - a.W : 0;
         const float sc = c->in_scale;  // 0 for sessions (their ring holds prescaled spectra)
         s = 0.0;
+        bool tiny = false;
         for (long long k = start; k < end; ++k) {
             float2 X = a.ring[((size_t)(k % a.slots) * a.B + f) * a.n + i];
             if (sc != 0.f) X = make_float2(__fmul_rn(X.x, sc), __fmul_rn(X.y, sc));
             s += (double)X.x * X.x + (double)X.y * X.y;
+            tiny |= node_tiny(X);
         }
+        if (a.tiny) a.tiny[e] = tiny ? 1 : 0;
     }
     a.psd[e] = s;
     a.inv_psd[e] = (s > 0.0) ? (float)(1.0 / sqrt(s)) : 0.f;

@@ -65,19 +65,57 @@ __global__ void k_node_batch(PreBatch b) {
 }
 
 // ---------------------------------------------------------------- full-window sums
-constexpr int WK = 16;     // trials staged per chunk
-constexpr int NODE_W = 5;  // staged words per node: a, b, Re u, Im u, tiny flag
+constexpr int WK = 24;           // most trials per staged chunk (balanced chunks)
+constexpr int WIN_THREADS = 256;
+
+struct WinSmem {
+    float2 raw[WK][2 * FC_T];    // the next chunk's spectra as copied (row tile, column tile)
+    // row node i, pre-broadcast for the packed operands: (a, a, b, b), (-a, -a, ua, ua),
+    // (ub, ub, -ua, -ua) with u = X / |X|
+    float4 row[WK][FC_T][3];
+    float4 ca[WK][FC_T / 4], cb[WK][FC_T / 4], cua[WK][FC_T / 4], cub[WK][FC_T / 4];  // column planes
+    unsigned char tiny[WK][2 * FC_T];
+    float sinv[2][2][FC_T];      // 1/sqrt(PSD) of the row and column tiles, by bin parity
+};
+struct WinBand {
+    float band[7][FC_T][FC_T];   // band sums per pair (finalizing launches only)
+};
+
+__device__ __forceinline__ void win_cp_async8(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ float win_gt0(float x) {
+    float r;
+    asm("set.gt.f32.f32 %0, %1, 0f00000000;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float win_lt0(float x) {
+    float r;
+    asm("set.lt.f32.f32 %0, %1, 0f00000000;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // Thread: row node li of tile ta against columns lj0 .. lj0 + 3 of tile tb, as two packed
-// column pairs (FP32x2 lanes), double-float running sums per lane: lazy TwoSum updates
-// (acc2_f_lazy / acc2_d_lazy) renormalized after every chunk of WK trials, which keeps the
-// error of a sum of K terms within about (WK + 1) K u^2 of their summed magnitudes.
-__global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, float* bins_out) {
+// column pairs (FP32x2 lanes). The terms are those of the streaming kernel (pair_terms2 on
+// the same staged values), so a re-summed accumulator and the later streaming subtraction
+// of a trial agree bit for bit. Double-float running sums per lane: lazy TwoSum updates
+// (acc2_f_lazy / acc2_d_lazy) renormalized after every chunk of at most WK trials, which
+// keeps the error of a sum of K terms within about (WK + 1) K u^2 of their summed
+// magnitudes. Sign counts: exact FP32 tallies of positive and negative terms. The next
+// chunk's spectra are copied by cp.async while the current chunk is summed.
+__global__ void __launch_bounds__(WIN_THREADS, 2) k_window(PairArgs a, int bins_metric, float* bins_out) {
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
     const WinFacts wf = window_facts(c, a.W, a.count);
     const int K = wf.K;
+    if (K <= 0) return;
     const KConst kc = make_kconst(K);
+    extern __shared__ __align__(16) unsigned char win_smem_raw[];
+    WinSmem& sm = *reinterpret_cast<WinSmem*>(win_smem_raw);
+    WinBand& sb = *reinterpret_cast<WinBand*>(win_smem_raw + sizeof(WinSmem));
+    const bool band_out = a.finalize && !bins_out;
 
     const int tp = a.tp0 + blockIdx.x;
     const int g = blockIdx.y;
@@ -85,71 +123,116 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
     const int f1 = min(a.B, f0 + a.group_bins);
     const int ta = a.tile_a[tp], tb = a.tile_b[tp];
     const int tid = threadIdx.x;
-    const int li = tid >> 3, lj0 = (tid & 7) * 4;
+    const int li = tid >> 3, lj0 = (tid & 7) * 4, cg = tid & 7;
     const unsigned vmask = pair_mask(ta, tb, li, lj0, a.n);
     const int gi = ta * FC_T + li, gj0 = tb * FC_T + lj0;
+    if (band_out)
+        for (int e = tid; e < 7 * FC_TT; e += WIN_THREADS) (&sb.band[0][0][0])[e] = 0.f;
+    const float sc = c->in_scale;  // 0 for sessions (their ring holds prescaled spectra)
 
-    // [trial][side: 0 row tile, 1 column tile][word][node], planar so that two adjacent
-    // column nodes load as one packed operand
-    __shared__ __align__(16) float sn[WK][2][NODE_W][FC_T];
-    __shared__ float sinv[2][FC_T];
-
-    float band[7][4];
+    // chunk copies: thread tid copies and converts node l_node of the two tiles, trials
+    // kk0 + 4 q of a chunk
+    const int l_node = tid & 63, kk0 = tid >> 6;
+    const int node = l_node < FC_T ? ta * FC_T + l_node : tb * FC_T + l_node - FC_T;
+    const bool node_ok = node < a.n;
+    const int nchunk = (K + WK - 1) / WK;
+    const int csize = (K + nchunk - 1) / nchunk;
+    const int slot_start = (int)(wf.start % a.slots);
+    constexpr int PER = WK * 2 * FC_T / WIN_THREADS;
+    auto issue_copy = [&](int f, int k0) {
+        const int kn = min(csize, K - k0);
+        int slot = slot_start + k0 + kk0;
+        while (slot >= a.slots) slot -= a.slots;
+        const float2* src = a.ring + (size_t)f * a.n + node;
+        const size_t slot_stride = (size_t)a.B * a.n;
 #pragma unroll
-    for (int m = 0; m < 7; ++m)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) band[m][q] = 0.f;
+        for (int q = 0; q < PER; ++q) {
+            const int kk = kk0 + 4 * q;
+            if (kk < kn && node_ok) win_cp_async8(&sm.raw[kk][l_node], src + (size_t)slot * slot_stride);
+            slot += 4;
+            while (slot >= a.slots) slot -= a.slots;
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (f0 < f1) issue_copy(f0, 0);
 
     for (int f = f0; f < f1; ++f) {
-        float2 vh[2][FC_NFIELD], vl[2][FC_NFIELD];
-        int s[4] = {0, 0, 0, 0};
+        float2 vh[2][FC_NFIELD], vl[2][FC_NFIELD], pos[2], neg[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < 2; ++h) {
+            pos[h] = neg[h] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < FC_NFIELD; ++k) vh[h][k] = vl[h][k] = make_float2(0.f, 0.f);
+        }
+        // (parity: a slow thread may still read the previous bin's values in its finalize;
+        // the chunk barriers below order this bin's reads after these writes)
+        const int par = f & 1;
         if (tid < 64) {
             const int w = tid >> 5, l = tid & 31;
-            const int node = (w ? tb : ta) * FC_T + l;
-            sinv[w][l] = node < a.n ? a.inv_psd[(size_t)f * a.n + node] : 0.f;
+            const int nd = (w ? tb : ta) * FC_T + l;
+            sm.sinv[par][w][l] = nd < a.n ? a.inv_psd[(size_t)f * a.n + nd] : 0.f;
         }
-        for (int k0 = 0; k0 < K; k0 += WK) {
-            const int kn = min(WK, K - k0);
-            __syncthreads();
+        for (int ci = 0; ci < nchunk; ++ci) {
+            const int k0 = ci * csize;
+            const int kn = min(csize, K - k0);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();  // the chunk has landed; every thread is done with the previous one
             bool any_tiny = false;
-            const float sc = c->in_scale;  // 0 for sessions (their ring holds prescaled spectra)
-            for (int e = tid; e < WK * 2 * FC_T; e += 256) {
-                const int kk = e / (2 * FC_T), side = (e / FC_T) & 1, l = e % FC_T;
-                const int node = (side ? tb : ta) * FC_T + l;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int kk = kk0 + 4 * q;
                 float2 X = make_float2(0.f, 0.f);
-                if (kk < kn && node < a.n)
-                    X = a.ring[((size_t)((wf.start + k0 + kk) % a.slots) * a.B + f) * a.n + node];
+                if (kk < kn && node_ok) X = sm.raw[kk][l_node];
                 if (sc != 0.f) X = make_float2(__fmul_rn(X.x, sc), __fmul_rn(X.y, sc));
                 const float2 u = phasor_of(X);
-                sn[kk][side][0][l] = X.x;
-                sn[kk][side][1][l] = X.y;
-                sn[kk][side][2][l] = u.x;
-                sn[kk][side][3][l] = u.y;
+                if (l_node < FC_T) {
+                    sm.row[kk][l_node][0] = make_float4(X.x, X.x, X.y, X.y);
+                    sm.row[kk][l_node][1] = make_float4(-X.x, -X.x, u.x, u.x);
+                    sm.row[kk][l_node][2] = make_float4(u.y, u.y, -u.x, -u.x);
+                } else {
+                    const int l = l_node - FC_T;
+                    reinterpret_cast<float*>(sm.ca[kk])[l] = X.x;
+                    reinterpret_cast<float*>(sm.cb[kk])[l] = X.y;
+                    reinterpret_cast<float*>(sm.cua[kk])[l] = u.x;
+                    reinterpret_cast<float*>(sm.cub[kk])[l] = u.y;
+                }
                 const bool tn = node_tiny(X);
-                sn[kk][side][4][l] = tn ? 1.f : 0.f;
+                sm.tiny[kk][l_node] = tn ? 1 : 0;
                 any_tiny |= tn;
             }
             // chunks without a tiny node (the rule) run a loop with no FP64 branch at all
             const bool chunk_tiny = __syncthreads_or(any_tiny ? 1 : 0) != 0;
+            // the raw buffer is free again: copy the next chunk (this bin's or the next's)
+            if (ci + 1 < nchunk)
+                issue_copy(f, k0 + csize);
+            else if (f + 1 < f1)
+                issue_copy(f + 1, 0);
+            if (!vmask) continue;
             auto chunk = [&](auto tiny_c) {
                 constexpr bool TINY = decltype(tiny_c)::value;
+#pragma unroll 2
                 for (int kk = 0; kk < kn; ++kk) {
-                    const float (*r)[FC_T] = sn[kk][0];
-                    const float (*cl)[FC_T] = sn[kk][1];
-                    const RowConst rc = row_const(r[0][li], r[1][li], r[2][li], r[3][li], r[4][li] != 0.f);
+                    const float4 r0 = sm.row[kk][li][0], r1 = sm.row[kk][li][1], r2 = sm.row[kk][li][2];
+                    RowConst rc;
+                    rc.a = make_float2(r0.x, r0.y);
+                    rc.b = make_float2(r0.z, r0.w);
+                    rc.na = make_float2(r1.x, r1.y);
+                    rc.ua = make_float2(r1.z, r1.w);
+                    rc.ub = make_float2(r2.x, r2.y);
+                    rc.nua = make_float2(r2.z, r2.w);
+                    rc.as = r0.x;
+                    rc.bs = r0.z;
+                    rc.tiny = TINY && sm.tiny[kk][li] != 0;
+                    const float4 xa = sm.ca[kk][cg], xb = sm.cb[kk][cg], xua = sm.cua[kk][cg], xub = sm.cub[kk][cg];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const int j = lj0 + 2 * h;
-                        const float2 tj = *reinterpret_cast<const float2*>(&cl[4][j]);
-                        const PairTerms2 t = pair_terms2<TINY>(rc, *reinterpret_cast<const float2*>(&cl[0][j]),
-                                                         *reinterpret_cast<const float2*>(&cl[1][j]),
-                                                         *reinterpret_cast<const float2*>(&cl[2][j]),
-                                                         *reinterpret_cast<const float2*>(&cl[3][j]), tj.x != 0.f,
-                                                         tj.y != 0.f);
+                        const float2 aj = h ? make_float2(xa.z, xa.w) : make_float2(xa.x, xa.y);
+                        const float2 bj = h ? make_float2(xb.z, xb.w) : make_float2(xb.x, xb.y);
+                        const float2 uaj = h ? make_float2(xua.z, xua.w) : make_float2(xua.x, xua.y);
+                        const float2 ubj = h ? make_float2(xub.z, xub.w) : make_float2(xub.x, xub.y);
+                        const int j = FC_T + lj0 + 2 * h;
+                        const PairTerms2 t = pair_terms2<TINY>(rc, aj, bj, uaj, ubj, TINY && sm.tiny[kk][j] != 0,
+                                                               TINY && sm.tiny[kk][j + 1] != 0);
                         acc2_f_lazy(vh[h][0], vl[h][0], t.re);
                         acc2_f_lazy(vh[h][1], vl[h][1], t.im);
                         acc2_f_lazy(vh[h][2], vl[h][2], t.ure);
@@ -160,32 +243,37 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
                         two_prod(t.im.x, t.im.x, p2.x, e2.x);
                         two_prod(t.im.y, t.im.y, p2.y, e2.y);
                         acc2_d_lazy(vh[h][5], vl[h][5], p2, e2);
-                        s[2 * h] += t.s0;
-                        s[2 * h + 1] += t.s1;
+                        if (TINY) {
+                            pos[h] = add2(pos[h], make_float2(t.s0 > 0 ? 1.f : 0.f, t.s1 > 0 ? 1.f : 0.f));
+                            neg[h] = add2(neg[h], make_float2(t.s0 < 0 ? 1.f : 0.f, t.s1 < 0 ? 1.f : 0.f));
+                        } else {
+                            pos[h] = add2(pos[h], make_float2(win_gt0(t.im.x), win_gt0(t.im.y)));
+                            neg[h] = add2(neg[h], make_float2(win_lt0(t.im.x), win_lt0(t.im.y)));
+                        }
                     }
                 }
-                // back to normalized double words once per chunk of WK terms
+                // back to normalized double words once per chunk
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
 #pragma unroll
                     for (int k = 0; k < FC_NFIELD; ++k) renorm2(vh[h][k], vl[h][k]);
             };
-            if (vmask) {
-                if (chunk_tiny)
-                    chunk(std::true_type{});
-                else
-                    chunk(std::false_type{});
-            }
+            if (chunk_tiny)
+                chunk(std::true_type{});
+            else
+                chunk(std::false_type{});
         }
-        __syncthreads();  // sinv visible
         if (vmask) {
             df32 v[4][FC_NFIELD];
+            int sgn[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < 4; ++q) {
 #pragma unroll
                 for (int k = 0; k < FC_NFIELD; ++k)
                     v[q][k] = (q & 1) ? df_make(vh[q >> 1][k].y, vl[q >> 1][k].y)
                                       : df_make(vh[q >> 1][k].x, vl[q >> 1][k].x);
+                sgn[q] = (q & 1) ? (int)pos[q >> 1].y - (int)neg[q >> 1].y : (int)pos[q >> 1].x - (int)neg[q >> 1].x;
+            }
             if (a.write_acc) {
                 float* blk = a.acc + ((size_t)tp * a.B + f) * FC_BLOCK_WORDS;
                 const int w0 = li * FC_T + lj0;
@@ -196,28 +284,40 @@ __global__ void __launch_bounds__(256, 2) k_window(PairArgs a, int bins_metric, 
                     __stcs(reinterpret_cast<float4*>(blk + (2 * k) * FC_TT + w0), hq);
                     __stcs(reinterpret_cast<float4*>(blk + (2 * k + 1) * FC_TT + w0), lq);
                 }
-                __stcs(reinterpret_cast<int4*>(blk + 12 * FC_TT + w0), make_int4(s[0], s[1], s[2], s[3]));
+                __stcs(reinterpret_cast<int4*>(blk + 12 * FC_TT + w0), make_int4(sgn[0], sgn[1], sgn[2], sgn[3]));
             }
             if (a.finalize || bins_out) {
-                const float inv_i = sinv[0][li];
+                const float inv_i = sm.sinv[par][0][li];
+                const bool in_band = band_out && f >= a.fsel0 && f < a.fsel1;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    if (!(vmask & (1u << q))) continue;
                     float m[7];
-                    finalize_bin(v[q], s[q], inv_i, sinv[1][lj0 + q], kc, m);
-                    if (bins_out) {
-                        bins_out[(size_t)f * a.P + packed_index(gi, gj0 + q, a.n)] = m[bins_metric - 2];
-                    } else if (f >= a.fsel0 && f < a.fsel1) {
+                    finalize_bin(v[q], sgn[q], inv_i, sm.sinv[par][1][lj0 + q], kc, m);
+                    if (bins_out && (vmask & (1u << q))) {
+                        float val = m[0];
 #pragma unroll
-                        for (int mm = 0; mm < 7; ++mm) band[mm][q] = __fadd_rn(band[mm][q], m[mm]);
+                        for (int mm = 1; mm < 7; ++mm) val = (mm == bins_metric - 2) ? m[mm] : val;
+                        bins_out[(size_t)f * a.P + packed_index(gi, gj0 + q, a.n)] = val;
+                    }
+                    if (in_band) {
+#pragma unroll
+                        for (int mm = 0; mm < 7; ++mm) sb.band[mm][li][lj0 + q] = __fadd_rn(sb.band[mm][li][lj0 + q], m[mm]);
                     }
                 }
             }
         }
-        __syncthreads();  // sinv of the next bin is staged over this one
     }
-    if (a.finalize && !bins_out && vmask) write_band(a, g, band, gi, gj0, vmask, f1 - f0);
+    if (band_out && vmask) {
+        float band[7][4];
+#pragma unroll
+        for (int mm = 0; mm < 7; ++mm)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) band[mm][q] = sb.band[mm][li][lj0 + q];
+        write_band(a, g, band, gi, gj0, vmask, f1 - f0);
+    }
 }
+
+size_t window_smem_bytes(bool band) { return sizeof(WinSmem) + (band ? sizeof(WinBand) : 0); }
 
 // --------------------------------------------------- per-bin metrics from accumulators
 __global__ void __launch_bounds__(256) k_bins_from_acc(PairArgs a, int metric, float* out) {
@@ -310,11 +410,19 @@ cudaError_t launch_node_batch(const PreBatch& b, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+static cudaError_t launch_window_kernel(const PairArgs& a, dim3 grid, int metric_index, float* out, cudaStream_t st) {
+    const size_t smem = window_smem_bytes(a.finalize && !out);
+    cudaError_t e = cudaFuncSetAttribute(k_window, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)window_smem_bytes(true));
+    if (e != cudaSuccess) return e;
+    k_window<<<grid, WIN_THREADS, smem, st>>>(a, metric_index, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_window_sums(const PairArgs& a, cudaStream_t st) {
     if (a.tp0 < 0 || a.tp_count < 0 || a.tp0 + (a.tp_count ? a.tp_count : a.ntp) > a.ntp) return cudaErrorInvalidValue;
     dim3 grid(a.tp_count ? a.tp_count : a.ntp, a.groups);
-    k_window<<<grid, 256, 0, st>>>(a, 0, nullptr);
-    return cudaGetLastError();
+    return launch_window_kernel(a, grid, 0, nullptr, st);
 }
 
 cudaError_t launch_bins_window(const PairArgs& a, int metric_index, float* out, cudaStream_t st) {
@@ -324,8 +432,7 @@ cudaError_t launch_bins_window(const PairArgs& a, int metric_index, float* out, 
     b.write_acc = 0;
     b.tp0 = 0;
     b.tp_count = 0;
-    k_window<<<grid, 256, 0, st>>>(b, metric_index, out);
-    return cudaGetLastError();
+    return launch_window_kernel(b, grid, metric_index, out, st);
 }
 
 cudaError_t launch_bins_from_acc(const PairArgs& a, int metric_index, float* out, cudaStream_t st) {

@@ -362,6 +362,97 @@ CASES = {
 }
 
 
+CONFIG_LEGS = {
+    # the other workloads of the benchmark, measured beside the headline in the default run
+    "eeg_full_window": dict(n=60, N=500, fs=1000.0, band=(1.0, 50.0, 512), W=20, gen="eeg", mode="full", reps=10,
+                            desc="sensor-space EEG, plain method: 60 channels, 20 trials x 500 samples @1 kHz "
+                                 "(N(0,1) + 10 Hz sinusoids coupled at lags 0, pi/4, pi/2 on 10 seeded pairs), "
+                                 "Hann, nfft 512, 1-50 Hz (25 bins), all 9 metrics once over the full trial set"),
+    "meg_full_window": dict(n=306, N=1000, fs=1000.0, band=(1.0, 100.0, 1024), W=100, gen="meg", mode="full", reps=4,
+                            desc="MEG sensor space, full-window GPU path: 306 channels, 100 trials x 1000 samples "
+                                 "@1 kHz (1/f Gaussian noise + 40 coupled pairs at 8-30 Hz), Hann, nfft 1024, "
+                                 "1-100 Hz (101 bins), all 9 metrics; one new trial per push, whole window "
+                                 "recomputed"),
+    "source_stream": dict(n=2000, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=50, gen="ar2", mode="stream",
+                          pushes=500,
+                          desc="source space, streaming: 2000 AR(2) alpha sources with a 200-edge coupling "
+                               "graph, W = 50 trials x 500 samples @1 kHz, one new trial per push (98 % overlap), "
+                               "500 pushes, Hann, nfft 1000, 4-44 Hz (40 bins), 7 spectral metrics"),
+}
+
+
+def config_legs(fc, torch, stream):
+    """Device time per push of the other workloads (CUDA events on the session stream).
+
+    Full-window legs: one bulk fill, then ``reps`` single-trial pushes, each recomputing the
+    whole window (the EEG leg instead repeats its one evaluation of all 20 trials). Streaming
+    leg: one bulk fill of the window, then ``pushes`` single-trial pushes; beside it the same
+    pushes through the mixed-precision full window (BF16, TF32 tensor-core linear sums).
+    """
+    from synth import ar2_source_model, ar2_source_trials, eeg_sinusoid_trials, meg_pink_trials
+
+    def timed(sess, xs, count=1):
+        ev = []
+        for x in xs:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if count == 1:
+                fc.fc_push_trial(sess.handle, x)
+            else:
+                fc.fc_push_trials(sess.handle, x, count)
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    out = {}
+    for name, c in CONFIG_LEGS.items():
+        n, N, W = c["n"], c["N"], c["W"]
+        if c["gen"] == "eeg":
+            x = eeg_sinusoid_trials(21, W, n, N, fs=c["fs"])[0]
+        elif c["gen"] == "meg":
+            x = meg_pink_trials(22, W + c["reps"], n, N, fs=c["fs"])[0]
+        else:
+            x = ar2_source_trials(ar2_source_model(23, n, fs=c["fs"]), 0, W + 16, N)
+        dev = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+        leg = {"description": c["desc"]}
+        precs = [("fp32", fc.FC_PREC_FP32)] + ([("bf16", fc.FC_PREC_BF16), ("tf32", fc.FC_PREC_TF32)]
+                                               if c["gen"] != "eeg" else [("bf16", fc.FC_PREC_BF16)])
+        for pname, prec in precs:
+            mode = fc.FC_MODE_STREAM if (c["mode"] == "stream" and prec == fc.FC_PREC_FP32) else fc.FC_MODE_FULL
+            mask = fc.FC_ALL_METRICS if (c["mode"] == "full" and prec == fc.FC_PREC_FP32) else fc.FC_SPECTRAL_METRICS
+            with fc.Session(n, N, c["fs"], c["band"], "hann", mask, W, mode=mode, precision=prec,
+                            stream=stream.cuda_stream) as s:
+                P, B = s.P, s.B
+                fc.fc_set_profiling(s.handle, True)
+                if c["gen"] == "eeg":
+                    ts = timed(s, [dev] * (c["reps"] + 1), count=W)[1:]  # one evaluation of the 20 trials each
+                else:
+                    fc.fc_push_trials(s.handle, dev[:W].contiguous(), W)
+                    fc.fc_sync(s.handle)
+                    fc.fc_kernel_times(s.handle, reset=True)
+                    k = c.get("pushes", c.get("reps")) if mode == fc.FC_MODE_STREAM else c.get("reps", 4)
+                    pool = dev.shape[0] - W
+                    ts = timed(s, [dev[W + (i % pool)] for i in range(k)])
+                kt = fc.fc_kernel_times(s.handle, reset=True)
+            ms = sum(ts) / len(ts)
+            ts_sorted = sorted(ts)
+            leg[pname] = {
+                "path": ("streaming add/subtract update" if mode == fc.FC_MODE_STREAM else
+                         ("full-window recompute, CUDA cores" if prec == fc.FC_PREC_FP32 else
+                          f"full-window recompute, tcgen05 {pname.upper()} linear sums + CUDA-core non-linear sums")),
+                "metrics": "all 9" if mask == fc.FC_ALL_METRICS else "7 spectral",
+                "pushes_timed": len(ts), "ms_per_push": ms,
+                "p50_ms": ts_sorted[len(ts) // 2], "p99_ms": ts_sorted[min(len(ts) - 1, int(round(0.99 * (len(ts) - 1))))],
+                "pair_bins_per_push": P * B, "value": P * B / (ms / 1000.0), "unit": UNIT,
+                "contributions_per_s": (P * B * W / (ms / 1000.0)) if mode == fc.FC_MODE_FULL else None,
+                "kernels_ms_per_push": {k2: round(v[1] / len(ts), 4) for k2, v in kt.items() if v[0]},
+            }
+        out[name] = leg
+        del dev
+    return out
+
+
 def run_case(args):
     """One small named case (the profiler captures' workloads); prints its timing per push."""
     import torch
@@ -602,19 +693,23 @@ def run_ours(args, w, wname):
                          "+ CUDA-core non-linear sums (PLI, USPLI, WPLI, DSWPLI)",
                  "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in mkt.items() if v[0]}}
         if tc_launches:
-            # tensor-core work: 4 real GEMMs of 128 x 128 x Kp per (128-node tile pair, bin), Kp = 2W padded to 64
+            # algorithmic tensor work: 16 flop per pair-bin-trial (the CSD and phasor complex
+            # multiply-adds); the launched GEMMs (4 real 128 x 128 x Kp per 128-node tile pair and
+            # bin, Kp = 2W padded to 64, full diagonal tiles) are larger
             nt128 = (n + 127) // 128
             kp = ((2 * W + 63) // 64) * 64
-            flops = 4 * 2 * 128 * 128 * kp * (nt128 * (nt128 + 1) // 2) * B
+            flops_alg = 16 * P * B * W
+            flops_padded = 4 * 2 * 128 * 128 * kp * (nt128 * (nt128 + 1) // 2) * B
             herk_ms = tc_ms / tc_launches * 2
-            achieved = flops / (herk_ms / 1000.0) / 1e12
+            achieved = flops_alg / (herk_ms / 1000.0) / 1e12
             bf16_peak = measured_bf16_tflops()
-            mixed["tensor"] = {"flops_per_push": flops, "herk_ms_per_push": herk_ms,
+            mixed["tensor"] = {"flops_per_push": flops_alg, "launched_flops_per_push": flops_padded,
+                               "herk_ms_per_push": herk_ms,
                                "achieved_tflops": achieved, "peak_tflops": bf16_peak,
                                "frac": achieved / bf16_peak if bf16_peak else None,
                                "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)" if bf16_peak else None,
-                               "note": "time covers the operand pack and the MMA kernel (tensor flops of the "
-                                       "4 real GEMMs per 128-node tile pair and bin, K padded to 64)"}
+                               "note": "algorithmic flops (16 per pair-bin-trial) over the operand pack + MMA "
+                                       "kernel time per push"}
         ms.close()
 
     # serving: many concurrent sessions, continuous batching vs plain FP32 one trial at a time
@@ -622,12 +717,32 @@ def run_ours(args, w, wname):
     if world == 1 and not args.no_serving:
         del dev
         torch.cuda.empty_cache()
+        rep_b = serving_leg(fc, False, args.serving_seconds, 11)
+        rep_p = serving_leg(fc, True, args.serving_seconds, 11)
+        burst = serving_leg(fc, False, args.serving_seconds, 11, saturate=True)
         serving = {"trace": SERVING["desc"], "seconds": args.serving_seconds,
-                   "batched_replay": serving_leg(fc, False, args.serving_seconds, 11),
-                   "batched_saturated": serving_leg(fc, False, args.serving_seconds, 11, saturate=True),
-                   "plain_fp32_replay": serving_leg(fc, True, args.serving_seconds, 11),
+                   "summary": {
+                       "what": "Poisson replay of the trace; latency = trial arrival to network ready (host clock); "
+                               "value = pair-bin updates of all completed pushes / span",
+                       "batched": {"p50_ms": rep_b["latency_ms"]["p50"], "p99_ms": rep_b["latency_ms"]["p99"],
+                                   "value": rep_b["value"], "unit": UNIT},
+                       "plain_fp32": {"p50_ms": rep_p["latency_ms"]["p50"], "p99_ms": rep_p["latency_ms"]["p99"],
+                                      "value": rep_p["value"], "unit": UNIT},
+                       "p99_ratio_plain_over_batched": rep_p["latency_ms"]["p99"] / max(1e-9, rep_b["latency_ms"]["p99"]),
+                       "burst_peak_value": burst["value"],
+                   },
+                   "batched_replay": rep_b,
+                   "plain_fp32_replay": rep_p,
+                   "burst_all_submitted_at_once": burst,
                    "batched_path": "streaming add/subtract update, up to 32 sessions per launch of the persistent kernel",
-                   "plain_path": "one trial at a time, full-window FP32 recompute (FC_MODE_FULL), no batching"}
+                   "plain_path": "one trial at a time, full-window FP32 recompute (FC_MODE_FULL), no batching",
+                   "burst_note": "every trial of the trace submitted at t = 0: peak aggregate throughput; its "
+                                 "latencies are queueing behind the whole burst, not the serving latency"}
+
+    configs = None
+    if world == 1 and not args.no_configs:
+        torch.cuda.empty_cache()
+        configs = config_legs(fc, torch, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -658,7 +773,8 @@ def run_ours(args, w, wname):
                    "l2": "inputs larger than L2 (27.8 GB resident state), no flush",
                    "parallelism": f"{world} independent session(s), one per GPU"},
         "latency_ms": {"p50": p50, "p99": p99, "what": "device time from push enqueue to network ready"},
-        "plain_fp32": plain, "mixed_bf16_full_window": mixed, "serving": serving, "roofline": roofline, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
+        "plain_fp32": plain, "mixed_bf16_full_window": mixed, "serving": serving, "configs": configs,
+        "roofline": roofline, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
         "clocks": clocks.summary(), "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)
@@ -682,6 +798,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the EEG, MEG and source-space legs")
     ap.add_argument("--no-cpu-all-core", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="print the paper-style performance sweep instead")
     ap.add_argument("--case", choices=sorted(CASES), help="run one small named case (profiler captures)")

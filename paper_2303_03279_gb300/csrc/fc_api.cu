@@ -357,6 +357,34 @@ void nonlin_groups(long long ntp, int nsel, long long P, int K, int sms, int cap
     }
 }
 
+// Column tiles per resident-operand work item: longer segments reuse the row tile's operands
+// more, but every CTA's band sums (a segment's tile pairs x 3 planes) must stay in L2 while
+// its bins are added: 152 CTAs x 6 tile pairs x up to 192 KB exceeded the 129 MB L2 and sent
+// the reductions to DRAM.
+constexpr int kHerkSegTiles = 3;
+
+// Bin groups of the resident-operand tensor-core form: work items are 2 phases x groups x
+// nseg segments (a row tile and at most seg_max column tiles); the count g <= cap minimizing
+// the busiest CTA's work (ceil(items / SMs) rounds of a group's bins, each bin ~1.2 us per
+// column tile plus ~1.5 us to fill the resident operands) plus the band-sum planes' traffic
+// (write-back and final sum: ~8 B per pair, metric and group at ~6 TB/s).
+void herk_res_groups(int nseg, int seg_max, int nsel, int sms, long long P, int cap, int& groups, int& group_bins) {
+    groups = 1;
+    group_bins = nsel;
+    double best = 1e300;
+    for (int g = 1; g <= std::min(nsel, std::max(1, cap)); ++g) {
+        const int gb = (nsel + g - 1) / g;
+        if ((nsel + gb - 1) / gb != g) continue;
+        const long long rounds = (2LL * nseg * g + sms - 1) / sms;
+        const double t = (double)rounds * gb * (seg_max * 1.2e-6 + 1.5e-6) + (double)g * 3 * P * 8 / 6e12;
+        if (t < best) {
+            best = t;
+            groups = g;
+            group_bins = gb;
+        }
+    }
+}
+
 // Spectral pair sums over the whole window (bulk push, re-sum, full mode).
 fc_status stage_window(fc_session* s, int count, bool write_acc) {
     NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, 1, s->ctrl, count};
@@ -397,9 +425,18 @@ fc_status stage_window(fc_session* s, int count, bool write_acc) {
         ha.fsel0 = s->sel0;
         ha.fsel1 = s->sel1;
         ha.ctrl = s->ctrl;
+        ha.seg_a = s->seg_a;
+        ha.seg_b0 = s->seg_b0;
+        ha.seg_b1 = s->seg_b1;
+        ha.nseg = s->nseg;
+        ha.seg_max = s->seg_max;
         if (s->mask & (FC_COH | FC_IMAGCOHY | FC_PLV)) {
-            herk_groups(s->ntp128, s->sel1 - s->sel0, s->num_sms, (long long)s->P, s->herk_gcap, ha.groups,
-                        ha.group_bins);
+            if (s->seg_a)
+                herk_res_groups(s->nseg, s->seg_max, s->sel1 - s->sel0, s->num_sms, (long long)s->P, s->herk_gcap,
+                                ha.groups, ha.group_bins);
+            else
+                herk_groups(s->ntp128, s->sel1 - s->sel0, s->num_sms, (long long)s->P, s->herk_gcap, ha.groups,
+                            ha.group_bins);
             LAUNCH(FC_K_HERK_TC, launch_pack_operands(pk, s->stream));
             LAUNCH(FC_K_HERK_TC, launch_herk_tc(ha, s->stream));
             LAUNCH(FC_K_BAND_REDUCE, launch_herk_band(ha, s->stream));
@@ -857,7 +894,30 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
             TRY(alloc_zero(s, (size_t)s->nt128 * B * 4 * s->nchunks * herk_chunk_bytes(), &s->ops));
             TRY(alloc_zero(s, (size_t)B * n_nodes, &s->tiny_flags));
             int gb;
-            herk_groups(s->ntp128, B, s->num_sms, (long long)s->P, B, s->herk_gcap, gb);
+            if (s->nchunks <= herk_resident_max_chunks()) {
+                // resident-operand form: each row tile a with its column tiles b >= a in balanced
+                // segments of at most kHerkSegTiles tiles
+                std::vector<unsigned short> sa, sb0, sb1;
+                for (int ta = 0; ta < s->nt128; ++ta) {
+                    const int len = s->nt128 - ta, parts = (len + kHerkSegTiles - 1) / kHerkSegTiles;
+                    for (int q = 0; q < parts; ++q) {
+                        sa.push_back((unsigned short)ta);
+                        sb0.push_back((unsigned short)(ta + len * q / parts));
+                        sb1.push_back((unsigned short)(ta + len * (q + 1) / parts));
+                        s->seg_max = std::max(s->seg_max, (int)(sb1.back() - sb0.back()));
+                    }
+                }
+                s->nseg = (int)sa.size();
+                TRY(alloc_zero(s, sa.size(), &s->seg_a));
+                TRY(alloc_zero(s, sa.size(), &s->seg_b0));
+                TRY(alloc_zero(s, sa.size(), &s->seg_b1));
+                TRY(upload(s, s->seg_a, sa.data(), sa.size() * sizeof(unsigned short)));
+                TRY(upload(s, s->seg_b0, sb0.data(), sb0.size() * sizeof(unsigned short)));
+                TRY(upload(s, s->seg_b1, sb1.data(), sb1.size() * sizeof(unsigned short)));
+                herk_res_groups(s->nseg, s->seg_max, B, s->num_sms, (long long)s->P, B, s->herk_gcap, gb);
+            } else {
+                herk_groups(s->ntp128, B, s->num_sms, (long long)s->P, B, s->herk_gcap, gb);
+            }
             TRY(alloc_zero(s, (size_t)s->herk_gcap * 3 * s->P, &s->herk_part));
         }
         if (max_groups > 1) TRY(alloc_zero(s, (size_t)max_groups * 7 * s->P, &s->partial));

@@ -130,6 +130,10 @@ struct fc_session {
     unsigned char* tiny_flags;  // [B][n] a trial of the window has a tiny component (mixed path)
     unsigned char* cor_ops; // COR split-TF32 operand ring [slots][cor_nt][cor_nchunks][2][16 KB]
     int cor_nt, cor_ntp, cor_nchunks;
+    unsigned short* seg_a;  // resident-operand segments of the 128-node tile pairs (see HerkArgs)
+    unsigned short* seg_b0;
+    unsigned short* seg_b1;
+    int nseg, seg_max;
     float* herk_part;       // [herk_gcap][3][P] band sums of COH, IMAGCOHY, PLV per bin group
     int herk_gcap;          // bin groups the band-sum planes are allocated for
     size_t device_bytes;
@@ -246,11 +250,18 @@ struct HerkArgs {
     uint32_t mask;
     int fsel0, fsel1;     // bins entering the band average
     const FcCtrl* ctrl;
+    // resident-operand form (nchunks <= 4): segments s = (row tile seg_a[s], column tiles
+    // seg_b0[s] .. seg_b1[s] - 1); work items = 2 phases x groups x nseg
+    const unsigned short* seg_a;
+    const unsigned short* seg_b0;
+    const unsigned short* seg_b1;
+    int nseg, seg_max;
 };
 cudaError_t launch_pack_operands(const PackArgs& a, cudaStream_t st);
 cudaError_t launch_herk_tc(const HerkArgs& a, cudaStream_t st);
 cudaError_t launch_herk_band(const HerkArgs& a, cudaStream_t st);
 size_t herk_chunk_bytes();
+int herk_resident_max_chunks();
 // Non-linear sums only (signs, |Im|, Im, Im^2) with the PLI/USPLI/WPLI/DSWPLI finalize.
 // Bin groups partition the selected bins fsel0 .. fsel1 - 1 (group_bins each).
 cudaError_t launch_nonlinear_sums(const PairArgs& a, cudaStream_t st);

@@ -25,6 +25,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "df32.cuh"
 #include "fc_internal.h"
 #include "mbar.cuh"
 #include "tc.cuh"
@@ -218,22 +219,40 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
         float* sinv = sinv_all + warp * TILE;  // this warp's copy: no barrier across warps
         HerkSeq es;
         seq_unit(a, es, (int)blockIdx.x);
+        // 1/sqrt(PSD) of the next bin's nodes (this warp's two row groups of tile a and this
+        // thread's column node of tile b), loaded one bin ahead so that no phase waits on them
+        float pf_i[2], pf_j;
+        auto prefetch = [&](const HerkSeq& t) {
+            pf_i[0] = pf_i[1] = pf_j = 0.f;
+            if (t.u >= units) return;
+            const int ptp = t.u / a.groups;
+            const int pta = a.tile_a[ptp], ptb = a.tile_b[ptp];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int i = pta * TILE + (2 * rhalf + r) * 32 + (tid & 31);
+                if (i < a.n) pf_i[r] = a.inv_psd[(size_t)t.f * a.n + i];
+            }
+            const int jj = ptb * TILE + quarter * 32 + (tid & 31);
+            if (jj < a.n) pf_j = a.inv_psd[(size_t)t.f * a.n + jj];
+        };
+        prefetch(es);
+        float inv_j = 0.f;
         for (int ph = 0; ph < nphase; ++ph) {
             const int b = ph & 1;
             if (ph > 0 && b == 0) seq_next_bin(a, es);
             const int tp = es.u / a.groups, f = es.f;
             const int ta = a.tile_a[tp], tb = a.tile_b[tp];
             const int j = tb * TILE + quarter * 32 + (tid & 31);  // this thread's TMEM lane: column node j
-            if (b == 0) {  // 1/sqrt(PSD) of tile a's nodes, staged by this warp for itself
+            if (b == 0) {  // this bin's 1/sqrt(PSD), staged by this warp for itself; next bin's fetched
                 __syncwarp();
-                for (int r = 2 * rhalf; r < 2 * rhalf + 2; ++r) {  // the rows this warp reads
-                    const int i = ta * TILE + r * 32 + (tid & 31);
-                    sinv[r * 32 + (tid & 31)] = i < a.n ? a.inv_psd[(size_t)f * a.n + i] : 0.f;
-                }
+                sinv[(2 * rhalf) * 32 + (tid & 31)] = pf_i[0];
+                sinv[(2 * rhalf + 1) * 32 + (tid & 31)] = pf_i[1];
+                inv_j = pf_j;
                 __syncwarp();
+                HerkSeq nx = es;
+                seq_next_bin(a, nx);
+                prefetch(nx);
             }
-            // 1/sqrt(PSD) of this thread's column node, fetched while the MMAs run
-            const float inv_j = (b == 0 && j < a.n) ? a.inv_psd[(size_t)f * a.n + j] : 0.f;
             // warp-uniform outcome: the TMEM loads below are warp-collective
             const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accf[b], accf_ph[b]) ? 1 : 0) != 0;
             accf_ph[b] ^= 1;
@@ -263,50 +282,411 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
                 tmem_keep(rim[s4]);
             }
             if (j < a.n) {
-                // packed index of (i, j) for i = ta TILE + ibase, then p(i + 1) = p(i) + n - i - 2;
-                // the unit's first bin stores, the later ones add (atomicAdd without its result:
-                // a fire-and-forget reduction; same thread, same address, so in bin order)
-                auto emit = [&](auto first_c) {
+                // packed index of (i, j) for i = ta TILE + ibase, then p(i + 1) = p(i) + n - i - 2
+                // (below 2^31: n < 65536); the unit's first bin stores, the later ones add
+                // (atomicAdd without its result: a fire-and-forget reduction; same thread, same
+                // address, so in bin order). Off-diagonal tile pairs (ta < tb) have i < j < n for
+                // every element (tile a is not the last tile): no per-element test there.
+                // |z| = t rsqrt(t) with t = |z|^2 (a few ulp, far inside the tensor-core error).
+                auto emit = [&](auto first_c, auto full_c) {
                     constexpr bool FIRST = decltype(first_c)::value;
+                    constexpr bool FULL = decltype(full_c)::value;
                     int i = ta * TILE + ibase;
-                    long long p = packed_index(i, j, a.n);
+                    int p = (int)packed_index(i, j, a.n);
+                    float* o_a = out + (b == 0 ? 0 : 2 * a.P);
 #pragma unroll
                     for (int s4 = 0; s4 < 4; ++s4) {
 #pragma unroll
                         for (int q = 0; q < 16; ++q, p += a.n - i - 2, ++i) {
-                            if (j <= i || i >= a.n) continue;
+                            if (!FULL && (j <= i || i >= a.n)) continue;
                             const float vre = __uint_as_float(rre[s4][q]), vim = __uint_as_float(rim[s4][q]);
-                            float v0, v1 = 0.f;
-                            long long o0;
                             if (b == 0) {
-                                const float inv_i = sinv[ibase + 16 * s4 + q];
-                                const float r = __fmul_rn(__fmul_rn(vre, inv_i), inv_j);
-                                const float m = __fmul_rn(__fmul_rn(vim, inv_i), inv_j);
-                                v0 = sqrtf(__fmaf_rn(r, r, __fmul_rn(m, m)));
-                                v1 = m;
-                                o0 = p;
+                                const float sc = __fmul_rn(sinv[ibase + 16 * s4 + q], inv_j);
+                                const float r = __fmul_rn(vre, sc), m = __fmul_rn(vim, sc);
+                                const float t = __fmaf_rn(r, r, __fmul_rn(m, m));
+                                const float coh = t > 0.f ? __fmul_rn(t, rsqrtf(t)) : 0.f;
+                                if (FIRST) {
+                                    o_a[p] = coh;
+                                    o_a[a.P + p] = m;
+                                } else {
+                                    atomicAdd(o_a + p, coh);
+                                    atomicAdd(o_a + a.P + p, m);
+                                }
                             } else {
-                                v0 = __fmul_rn(sqrtf(__fmaf_rn(vre, vre, __fmul_rn(vim, vim))), inv_K);
-                                o0 = 2 * a.P + p;
-                            }
-                            if (FIRST) {
-                                out[o0] = v0;
-                                if (b == 0) out[a.P + p] = v1;
-                            } else {
-                                atomicAdd(out + o0, v0);
-                                if (b == 0) atomicAdd(out + a.P + p, v1);
+                                const float t = __fmaf_rn(vre, vre, __fmul_rn(vim, vim));
+                                const float plv = t > 0.f ? __fmul_rn(__fmul_rn(t, rsqrtf(t)), inv_K) : 0.f;
+                                if (FIRST)
+                                    o_a[p] = plv;
+                                else
+                                    atomicAdd(o_a + p, plv);
                             }
                         }
                     }
                 };
-                if (first)
-                    emit(std::true_type{});
-                else
-                    emit(std::false_type{});
+                const bool full = ta < tb;
+                if (first) {
+                    if (full)
+                        emit(std::true_type{}, std::true_type{});
+                    else
+                        emit(std::true_type{}, std::false_type{});
+                } else {
+                    if (full)
+                        emit(std::false_type{}, std::true_type{});
+                    else
+                        emit(std::false_type{}, std::false_type{});
+                }
             }
             fence_before();
             __syncwarp();
             if ((tid & 31) == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
+        }
+    }
+    fence_before();
+    const int fail_any = __syncthreads_or(failed ? 1 : 0);
+    fence_after();
+    if (fail_any && tid == 0) atomicOr(&c->timeout, 1);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ------------------------------------------------------- resident-operand form
+// The same products with one row tile's operands held in shared memory: a work item is
+// (row tile a, column tiles b0 .. b1 - 1, bin group, phase). For each bin of the group the
+// two row-side operand kinds of tile a (XR_a, XI_a in phase A; UR_a, UI_a in phase B) are
+// loaded once into resident slots, and the column-side operand of each tile b (XR_b or
+// UR_b) streams through NST 16 KB stages: per (tile pair, bin, phase) 64 KB of operands
+// move instead of 192 KB. Warp 8 issues the bulk copies, warp 9 the MMAs, warps 0-7 drain
+// TMEM (two buffers, so one unit's epilogue overlaps the next unit's MMAs). A unit's band
+// sums are written by one CTA in bin order, as in k_herk_tc.
+constexpr int RC_MAX = 4;                                   // resident K-chunks (2K <= 256 BF16 values)
+constexpr int NST = 5;                                      // streaming stages of one 16 KB block
+constexpr int RES_BYTES = RC_MAX * 2 * CHUNK_BYTES;         // 128 KB
+constexpr int RES_EPI = 8;                                  // epilogue warps: lane quarter w % 4, 64 rows each
+constexpr int RES_ROWS = TILE * 4 / RES_EPI;                // row nodes per epilogue warp
+constexpr int RES_SMEM = RES_BYTES + NST * CHUNK_BYTES + 1024 + RES_EPI * 4 * RES_ROWS;
+constexpr int RES_THREADS = 32 * RES_EPI + 64;              // warps 0-15 epilogue, 16 copies, 17 MMAs
+
+// sqrt(x), x >= 0, with the hardware approximation (relative error near 2^-23; 0 for 0).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+struct ResItem {
+    int a, b0, b1, p, g, f0, f1;
+};
+__device__ __forceinline__ ResItem res_item(const HerkArgs& A, int it) {
+    ResItem r;
+    const int per_p = A.groups * A.nseg;
+    r.p = it / per_p;
+    const int rem = it - r.p * per_p;
+    r.g = rem / A.nseg;
+    const int sg = rem - r.g * A.nseg;
+    r.a = A.seg_a[sg];
+    r.b0 = A.seg_b0[sg];
+    r.b1 = A.seg_b1[sg];
+    r.f0 = A.fsel0 + r.g * A.group_bins;
+    r.f1 = min(A.fsel1, r.f0 + A.group_bins);
+    return r;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(RES_THREADS, 1) k_herk_res(HerkArgs a) {
+    constexpr int EPI = RES_EPI;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    FcCtrl* c = const_cast<FcCtrl*>(a.ctrl);
+    if (c->bad) return;
+    const int items = 2 * a.groups * a.nseg;
+    if ((int)blockIdx.x >= items) return;
+    unsigned char* res = smem;                                  // [RC_MAX][2][16 KB]
+    unsigned char* stg = smem + RES_BYTES;                      // [NST][16 KB]
+    uint64_t* rfull = reinterpret_cast<uint64_t*>(smem + RES_BYTES + NST * CHUNK_BYTES);
+    uint64_t* rfree = rfull + RC_MAX;
+    uint64_t* sfull = rfree + RC_MAX;
+    uint64_t* sfree = sfull + NST;
+    uint64_t* accf = sfree + NST;
+    uint64_t* acce = accf + 2;
+    uint64_t* drain = acce + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    float* sinv_all = reinterpret_cast<float*>(smem + RES_BYTES + NST * CHUNK_BYTES + 1024);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int q = 0; q < RC_MAX; ++q) {
+            mbar_init(&rfull[q], 1);
+            mbar_init(&rfree[q], 1);
+        }
+        for (int q = 0; q < NST; ++q) {
+            mbar_init(&sfull[q], 1);
+            mbar_init(&sfree[q], 1);
+        }
+        mbar_init(&accf[0], 1);
+        mbar_init(&accf[1], 1);
+        mbar_init(&acce[0], EPI);
+        mbar_init(&acce[1], EPI);
+        mbar_init(drain, 1);
+        fence_mbar_init();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const long long wend = c->pushed + a.count;
+    const int K = (int)(wend - ((a.W > 0 && wend > a.W) ? wend - a.W : 0));
+    const float inv_K = 1.0f / (float)K;
+    const int nch = a.nchunks;
+    bool failed = false;
+
+    if (warp == EPI) {
+        // ---------------------------------------------------------- bulk copies
+        if ((tid & 31) == 0) {
+            uint32_t rfree_ph[RC_MAX] = {0, 0, 0, 0}, sfree_ph[NST] = {0, 0, 0, 0, 0};
+            int rloads = 0;                   // resident fills issued (one per item and bin)
+            long long sloads = 0;             // streamed blocks issued
+            long long scount[NST] = {0, 0, 0, 0, 0};
+            for (int it = (int)blockIdx.x; it < items && !failed; it += (int)gridDim.x) {
+                const ResItem I = res_item(a, it);
+                const int kr = I.p == 0 ? 0 : 2;  // row side: XR, XI or UR, UI; column side: XR or UR
+                for (int f = I.f0; f < I.f1 && !failed; ++f) {
+                    for (int q = 0; q < nch; ++q) {
+                        if (rloads > 0) {  // the MMAs of the previous bin have read this slot
+                            if (!mbar_wait_bounded(&rfree[q], rfree_ph[q])) { failed = true; break; }
+                            rfree_ph[q] ^= 1;
+                        }
+                        unsigned char* dst = res + (size_t)q * 2 * CHUNK_BYTES;
+                        mbar_expect_tx(&rfull[q], 2 * CHUNK_BYTES);
+                        bulk_g2s(dst, op_block(a, I.a, f, kr, q), CHUNK_BYTES, &rfull[q]);
+                        bulk_g2s(dst + CHUNK_BYTES, op_block(a, I.a, f, kr + 1, q), CHUNK_BYTES, &rfull[q]);
+                    }
+                    if (failed) break;
+                    ++rloads;
+                    for (int b = I.b0; b < I.b1 && !failed; ++b)
+                        for (int q = 0; q < nch; ++q) {
+                            const int st = (int)(sloads % NST);
+                            if (sloads >= NST) {
+                                if (!mbar_wait_bounded(&sfree[st], sfree_ph[st])) { failed = true; break; }
+                                sfree_ph[st] ^= 1;
+                            }
+                            mbar_expect_tx(&sfull[st], CHUNK_BYTES);
+                            bulk_g2s(stg + (size_t)st * CHUNK_BYTES, op_block(a, b, f, kr, q), CHUNK_BYTES, &sfull[st]);
+                            ++scount[st];
+                            ++sloads;
+                        }
+                }
+            }
+            // let every copy issued land before the CTA ends
+            if (rloads > 0)
+                for (int q = 0; q < nch; ++q) mbar_wait_bounded(&rfull[q], (uint32_t)((rloads - 1) & 1));
+            for (int st = 0; st < NST; ++st)
+                if (scount[st] > 0) mbar_wait_bounded(&sfull[st], (uint32_t)((scount[st] - 1) & 1));
+        }
+    } else if (warp == EPI + 1) {
+        // ---------------------------------------------------------- MMAs
+        if ((tid & 31) == 0) {
+            const uint32_t idesc = make_idesc(KIND == 1 ? 2u : (a.ab_format == 1 ? 1u : 0u), TILE, TILE);
+            uint32_t rfull_ph[RC_MAX] = {0, 0, 0, 0}, sfull_ph[NST] = {0, 0, 0, 0, 0}, acce_ph[2] = {0, 0};
+            long long sused = 0, u = 0;
+            for (int it = (int)blockIdx.x; it < items && !failed; it += (int)gridDim.x) {
+                const ResItem I = res_item(a, it);
+                for (int f = I.f0; f < I.f1 && !failed; ++f)
+                    for (int b = I.b0; b < I.b1 && !failed; ++b) {
+                        const int buf = (int)(u & 1);
+                        if (u >= 2) {  // the epilogue has drained this TMEM buffer
+                            if (!mbar_wait_bounded(&acce[buf], acce_ph[buf])) { failed = true; break; }
+                            acce_ph[buf] ^= 1;
+                            fence_after();
+                        }
+                        const uint32_t d = tmem + (uint32_t)(buf * 2 * TILE);
+                        for (int q = 0; q < nch; ++q) {
+                            if (b == I.b0) {  // this bin's resident chunk has landed
+                                if (!mbar_wait_bounded(&rfull[q], rfull_ph[q])) { failed = true; break; }
+                                rfull_ph[q] ^= 1;
+                            }
+                            const int st = (int)(sused % NST);
+                            if (!mbar_wait_bounded(&sfull[st], sfull_ph[st])) { failed = true; break; }
+                            sfull_ph[st] ^= 1;
+                            fence_after();
+                            const uint32_t sb = smem_u32(stg + (size_t)st * CHUNK_BYTES);
+                            const uint32_t r0 = smem_u32(res + (size_t)q * 2 * CHUNK_BYTES);
+#pragma unroll
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const uint32_t acc = (q > 0 || ks > 0) ? 1u : 0u;
+                                const uint32_t off = ks * 256;
+                                const uint64_t d_b = smem_desc(sb + off);                   // XR_b or UR_b
+                                const uint64_t d_ar = smem_desc(r0 + off);                  // XR_a or UR_a
+                                const uint64_t d_ai = smem_desc(r0 + CHUNK_BYTES + off);    // XI_a or UI_a
+                                mma<KIND>(d, d_b, d_ar, idesc, acc);
+                                mma<KIND>(d + TILE, d_b, d_ai, idesc, acc);
+                            }
+                            mma_commit(&sfree[st]);                 // the stage may be refilled
+                            if (b == I.b1 - 1) mma_commit(&rfree[q]);  // last tile of the bin: slot free
+                            ++sused;
+                        }
+                        if (failed) break;
+                        mma_commit(&accf[buf]);
+                        ++u;
+                    }
+            }
+            mma_commit(drain);
+            mbar_wait_bounded(drain, 0);
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue (warps 0 .. EPI-1)
+        uint32_t accf_ph[2] = {0, 0};
+        const int quarter = warp & 3, rpart = warp >> 2;  // TMEM lanes 32 quarter ..; rows RES_ROWS rpart ..
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+        float* sinv = sinv_all + warp * RES_ROWS;  // this warp's rows: no barrier across warps
+        const int ibase = rpart * RES_ROWS;
+        long long u = 0;
+        // 1/sqrt(PSD) one step ahead: the next bin's row values of this warp (loaded during the
+        // current bin) and the next unit's column value of this thread
+        constexpr int RPL = RES_ROWS / 32;  // row values per lane
+        float pf_row[RPL], pf_col = 0.f;
+        auto load_row = [&](const ResItem& I, int f) {
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int i = I.a * TILE + ibase + 32 * r + (tid & 31);
+                pf_row[r] = (I.p == 0 && i < a.n) ? a.inv_psd[(size_t)f * a.n + i] : 0.f;
+            }
+        };
+        auto load_col = [&](const ResItem& I, int f, int tb) {
+            const int jj = tb * TILE + quarter * 32 + (tid & 31);
+            return (I.p == 0 && jj < a.n) ? a.inv_psd[(size_t)f * a.n + jj] : 0.f;
+        };
+        {
+            const ResItem I0 = res_item(a, (int)blockIdx.x);
+            load_row(I0, I0.f0);
+            pf_col = load_col(I0, I0.f0, I0.b0);
+        }
+        for (int it = (int)blockIdx.x; it < items && !failed; it += (int)gridDim.x) {
+            const ResItem I = res_item(a, it);
+            const int ta = I.a;
+            float* out = a.part + (size_t)I.g * 3 * a.P + (I.p == 0 ? 0 : 2 * a.P);  // this group's band sums
+            for (int f = I.f0; f < I.f1 && !failed; ++f) {
+                const bool first = f == I.f0;  // the group's first bin stores, later bins add
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) sinv[32 * r + (tid & 31)] = pf_row[r];
+                __syncwarp();
+                {  // the next bin of this item, or the first bin of the next item
+                    const int itn = f + 1 < I.f1 ? it : it + (int)gridDim.x;
+                    if (itn < items) {
+                        const ResItem In = itn == it ? I : res_item(a, itn);
+                        load_row(In, itn == it ? f + 1 : In.f0);
+                    }
+                }
+                for (int tb = I.b0; tb < I.b1; ++tb) {
+                    const int buf = (int)(u & 1);
+                    const int j = tb * TILE + quarter * 32 + (tid & 31);  // this thread's TMEM lane: column node j
+                    const float inv_j = pf_col;
+                    {  // the next unit's column value
+                        int nit = it, nf = f, ntb = tb + 1;
+                        if (ntb >= I.b1) { ntb = I.b0; ++nf; }
+                        if (nf >= I.f1) nit = it + (int)gridDim.x;
+                        if (nit < items) {
+                            const ResItem In = nit == it ? I : res_item(a, nit);
+                            if (nit != it) { nf = In.f0; ntb = In.b0; }
+                            pf_col = load_col(In, nf, ntb);
+                        }
+                    }
+                    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accf[buf], accf_ph[buf]) ? 1 : 0) != 0;
+                    accf_ph[buf] ^= 1;
+                    if (!ok) {
+                        failed = true;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t col = (uint32_t)(buf * 2 * TILE);
+                    // this warp's RES_ROWS rows in two halves of NG groups of 16 TMEM columns (the
+                    // register file, split over the four schedulers, allows ~170 registers here)
+                    constexpr int NG = RES_ROWS / 32;
+#pragma unroll 1
+                    for (int hh = 0; hh < 2; ++hh) {
+                    const int hbase = ibase + hh * (RES_ROWS / 2);
+                    uint32_t rre[NG][16], rim[NG][16];
+#pragma unroll
+                    for (int s4 = 0; s4 < NG; ++s4) {
+                        tmem_ld16_issue(lane_base + col + hbase + 16 * s4, rre[s4]);
+                        tmem_ld16_issue(lane_base + col + TILE + hbase + 16 * s4, rim[s4]);
+                    }
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int s4 = 0; s4 < NG; ++s4) {
+                        tmem_keep(rre[s4]);
+                        tmem_keep(rim[s4]);
+                    }
+                    if (j < a.n) {
+                        // as in k_herk_tc: packed index p(i + 1) = p(i) + n - i - 2; off-diagonal tile
+                        // pairs (ta < tb) need no per-element test
+                        auto emit = [&](auto first_c, auto full_c, auto phase_c) {
+                            constexpr bool FIRST = decltype(first_c)::value;
+                            constexpr bool FULL = decltype(full_c)::value;
+                            constexpr int PH = decltype(phase_c)::value;
+                            int i = ta * TILE + hbase;
+                            int pk = (int)packed_index(i, j, a.n);
+                            float* out2 = out + a.P;  // IMAGCOHY plane (phase A)
+                            const float2 invj2 = make_float2(inv_j, inv_j);
+                            // one value per element: the first bin stores, later bins reduce
+                            auto put = [&](float* base, int at, float v) {
+                                if (FIRST) base[at] = v;
+                                else atomicAdd(base + at, v);
+                            };
+#pragma unroll
+                            for (int s4 = 0; s4 < NG; ++s4) {
+#pragma unroll
+                                for (int q = 0; q < 16; q += 2) {
+                                    // two row nodes i, i + 1 per packed FP32x2 operation
+                                    const float2 vre = make_float2(__uint_as_float(rre[s4][q]), __uint_as_float(rre[s4][q + 1]));
+                                    const float2 vim = make_float2(__uint_as_float(rim[s4][q]), __uint_as_float(rim[s4][q + 1]));
+                                    float2 v0, v1;
+                                    if (PH == 0) {
+                                        const float2 sc = mul2(*reinterpret_cast<const float2*>(&sinv[hh * (RES_ROWS / 2) + 16 * s4 + q]), invj2);
+                                        const float2 r = mul2(vre, sc), m = mul2(vim, sc);
+                                        const float2 t = fma2(r, r, mul2(m, m));
+                                        v0 = make_float2(sqrt_approx(t.x), sqrt_approx(t.y));
+                                        v1 = m;
+                                    } else {
+                                        const float2 t = fma2(vre, vre, mul2(vim, vim));
+                                        v0 = make_float2(__fmul_rn(sqrt_approx(t.x), inv_K), __fmul_rn(sqrt_approx(t.y), inv_K));
+                                        v1 = v0;
+                                    }
+#pragma unroll
+                                    for (int e = 0; e < 2; ++e, pk += a.n - i - 2, ++i) {
+                                        if (!FULL && (j <= i || i >= a.n)) continue;
+                                        put(out, pk, e ? v0.y : v0.x);
+                                        if (PH == 0) put(out2, pk, e ? v1.y : v1.x);
+                                    }
+                                }
+                            }
+                        };
+                        const bool full = ta < tb;
+                        using T = std::true_type;
+                        using F = std::false_type;
+                        using P0 = std::integral_constant<int, 0>;
+                        using P1 = std::integral_constant<int, 1>;
+                        if (I.p == 0) {
+                            if (first) { if (full) emit(T{}, T{}, P0{}); else emit(T{}, F{}, P0{}); }
+                            else { if (full) emit(F{}, T{}, P0{}); else emit(F{}, F{}, P0{}); }
+                        } else {
+                            if (first) { if (full) emit(T{}, T{}, P1{}); else emit(T{}, F{}, P1{}); }
+                            else { if (full) emit(F{}, T{}, P1{}); else emit(F{}, F{}, P1{}); }
+                        }
+                    }
+                    }  // halves
+                    fence_before();
+                    __syncwarp();
+                    if ((tid & 31) == 0)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[buf])) : "memory");
+                    ++u;
+                }
+            }
         }
     }
     fence_before();
@@ -419,9 +799,23 @@ cudaError_t launch_pack_operands(const PackArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_herk_tc(const HerkArgs& a, cudaStream_t st) {
+    cudaError_t e;
+    if (a.seg_a && a.nchunks <= RC_MAX) {  // resident-operand form
+        const int items = 2 * a.groups * a.nseg;
+        const int ctas = items < a.grid_ctas ? items : a.grid_ctas;
+        if (a.ab_format == 2) {
+            e = cudaFuncSetAttribute(k_herk_res<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, RES_SMEM);
+            if (e != cudaSuccess) return e;
+            k_herk_res<1><<<ctas, RES_THREADS, RES_SMEM, st>>>(a);
+        } else {
+            e = cudaFuncSetAttribute(k_herk_res<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, RES_SMEM);
+            if (e != cudaSuccess) return e;
+            k_herk_res<0><<<ctas, RES_THREADS, RES_SMEM, st>>>(a);
+        }
+        return cudaGetLastError();
+    }
     const int units = a.ntp * a.groups;
     const int ctas = units < a.grid_ctas ? units : a.grid_ctas;
-    cudaError_t e;
     if (a.ab_format == 2) {
         e = cudaFuncSetAttribute(k_herk_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
         if (e != cudaSuccess) return e;
@@ -440,3 +834,4 @@ cudaError_t launch_herk_band(const HerkArgs& a, cudaStream_t st) {
 }
 
 size_t herk_chunk_bytes() { return CHUNK_BYTES; }
+int herk_resident_max_chunks() { return RC_MAX; }

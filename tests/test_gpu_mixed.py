@@ -81,17 +81,25 @@ def test_mixed_full_window_meg_sampled(prec):
         _check(s, K, I, J, prec=prec)
 
 
-def _herk_groups(ntp128, nsel, sms, P, cap):
-    """Bin groups the library picks for the tensor-core band sums (its makespan model:
-    ceil(units / SMs) rounds of a group's bins at ~17 us per tile pair and bin, plus the
-    band-sum planes' traffic), restated here only to assert that a case runs several groups."""
+def _herk_groups(nt128, nsel, sms, P, cap):
+    """Bin groups the library picks for the tensor-core band sums of a window whose operands
+    fit the resident form (its makespan model over work items of a row tile and at most three
+    column tiles: ceil(items / SMs) rounds of a group's bins at ~1.2 us per column tile and
+    ~1.5 us per resident fill, plus the band-sum planes' traffic), restated here only to
+    assert that a case runs several groups."""
+    segs = []
+    for ta in range(nt128):
+        length = nt128 - ta
+        parts = (length + 2) // 3
+        segs += [length * (q + 1) // parts - length * q // parts for q in range(parts)]
+    nseg, seg_max = len(segs), max(segs)
     best, groups = None, 1
     for g in range(1, min(nsel, max(1, cap)) + 1):
         gb = -(-nsel // g)
         if -(-nsel // gb) != g:
             continue
-        rounds = -(-(ntp128 * g) // sms)
-        t = rounds * gb * 17e-6 + g * 3 * P * 8 / 6e12
+        rounds = -(-(2 * nseg * g) // sms)
+        t = rounds * gb * (seg_max * 1.2e-6 + 1.5e-6) + g * 3 * P * 8 / 6e12
         if best is None or t < best:
             best, groups = t, g
     return groups
@@ -101,14 +109,16 @@ def _herk_groups(ntp128, nsel, sms, P, cap):
 def test_mixed_band_groups_against_oracle(prec):
     """1100 nodes x 40 bins: the tensor-core band sums run over several bin groups (the first
     bin of a (tile pair, bin group) unit stores its values, the later bins add to them by
-    reductions), over nine 128-node tiles of which the last is ragged (76 nodes). Sampled
+    reductions), over nine 128-node tiles of which the last is ragged (76 nodes), with the
+    row tile's operands resident across segments of column tiles. Sampled
     pairs, including pairs across the 128-node tile edges, inside diagonal tiles and in the
     ragged tile, against the oracle on the GPU's spectra: COH, IMAGCOHY, PLV within 5e-3,
     PLI, USPLI, WPLI, DSWPLI within 1e-5 with exact sign sums."""
     n, N, W = 1100, 500, 20
     nt = -(-n // 128)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert _herk_groups(nt * (nt + 1) // 2, 40, sms, n * (n - 1) // 2, 40) > 1
+    groups = _herk_groups(nt, 40, sms, n * (n - 1) // 2, 40)
+    assert 1 < groups < 40  # several groups of several bins
     x = white_trials(33, W, n, N)
     x[:, 7] += 0.8 * x[:, 1090]  # a coupled pair reaching into the ragged tile
     rng = np.random.default_rng(5)

@@ -288,7 +288,7 @@ def band_bin_count(band, fs):
     return sum(1 for k in range(band[2] // 2 + 1) if band[0] * band[2] <= k * fs < band[1] * band[2])
 
 
-def serving_leg(fc, plain, duration_s, seed, saturate=False):
+def serving_leg(fc, plain, duration_s, seed, saturate=False, precision=0):
     """Replay the serving trace through one fc_server (batched streaming, or plain FP32).
 
     Every session gets one untimed trial first (calibration, module load). In replay mode
@@ -301,7 +301,7 @@ def serving_leg(fc, plain, duration_s, seed, saturate=False):
     trace = serving_trace(seed, duration_s)
     N, fs = SERVING["N"], SERVING["fs"]
     pools = {n: white_trials(1000 + n, SERVING["pool"], n, N) for n in sorted({s.n_nodes for s in trace})}
-    sv = fc.fc_server_create(plain=plain)
+    sv = fc.fc_server_create(plain=plain, precision=precision)
     try:
         ids = [fc.fc_server_open(sv, s.n_nodes, N, fs, serving_band(s.n_nodes), "hann", fc.FC_SPECTRAL_METRICS,
                                  s.window) for s in trace]
@@ -652,6 +652,7 @@ def run_ours(args, w, wname):
     # plain FP32 comparator: CUDA-core full-window recompute per push, no accumulators
     plain = None
     mixed = None
+    mixed_stream = None
     if not args.no_plain:
         ps = fc.Session(n, N, w["fs"], B_band, "hann", mask, W, mode=fc.FC_MODE_FULL, stream=stream.cuda_stream)
         fc.fc_push_trials(ps.handle, dev[:W].contiguous(), W)
@@ -714,6 +715,38 @@ def run_ours(args, w, wname):
                                "note": "algorithmic flops (16 per pair-bin-trial) over the operand pack + MMA "
                                        "kernel time per push"}
         ms.close()
+        del ms
+        # mixed-precision streaming: the exact streaming update, drift re-sum slices with the
+        # linear sums on the tensor cores (BF16 operand ring)
+        torch.cuda.synchronize()
+        ss = fc.Session(n, N, w["fs"], B_band, "hann", mask, W, mode=fc.FC_MODE_STREAM, precision=fc.FC_PREC_BF16,
+                        stream=stream.cuda_stream)
+        fc.fc_push_trials(ss.handle, dev[:W].contiguous(), W)
+        for k in range(warmup):
+            fc.fc_push_trial(ss.handle, trial(W + k))
+        fc.fc_sync(ss.handle)
+        fc.fc_set_profiling(ss.handle, True)
+        fc.fc_kernel_times(ss.handle, reset=True)
+        sst = max(3, steps)
+        sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(sst)]
+        for k in range(sst):
+            sev[k][0].record(stream)
+            fc.fc_push_trial(ss.handle, trial(W + warmup + k))
+            sev[k][1].record(stream)
+        torch.cuda.synchronize()
+        skt = fc.fc_kernel_times(ss.handle, reset=True)
+        sl = sorted(a.elapsed_time(b) for a, b in sev)
+        sms_ = sum(sl) / len(sl)
+        kms = {k: v[1] / sst for k, v in skt.items() if v[0]}
+        mixed_stream = {"value": world * units / (sms_ / 1000.0), "unit": UNIT, "ms_per_step": sms_,
+                        "latency_ms": {"p50": sl[len(sl) // 2], "p99": sl[-1]}, "steps": sst,
+                        "path": "exact streaming update (FP32 terms, double-float sums); drift re-sum slice: "
+                                "tcgen05 BF16 linear sums over the operand ring + exact CUDA-core non-linear sums",
+                        "kernels_ms_per_push": {k: round(v, 4) for k, v in kms.items()},
+                        "tensor_core_share_of_push": kms.get("herk_tc", 0.0) / sms_,
+                        "resum_slice_ms_per_push": kms.get("herk_tc", 0.0) + kms.get("window", 0.0)}
+        ss.close()
+        del ss
 
     # serving: many concurrent sessions, continuous batching vs plain FP32 one trial at a time
     serving = None
@@ -721,6 +754,7 @@ def run_ours(args, w, wname):
         del dev
         torch.cuda.empty_cache()
         rep_b = serving_leg(fc, False, args.serving_seconds, 11)
+        rep_m = serving_leg(fc, False, args.serving_seconds, 11, precision=fc.FC_PREC_BF16)
         rep_p = serving_leg(fc, True, args.serving_seconds, 11)
         burst = serving_leg(fc, False, args.serving_seconds, 11, saturate=True)
         serving = {"trace": SERVING["desc"], "seconds": args.serving_seconds,
@@ -729,15 +763,20 @@ def run_ours(args, w, wname):
                                "value = pair-bin updates of all completed pushes / span",
                        "batched": {"p50_ms": rep_b["latency_ms"]["p50"], "p99_ms": rep_b["latency_ms"]["p99"],
                                    "value": rep_b["value"], "unit": UNIT},
+                       "batched_mixed_bf16": {"p50_ms": rep_m["latency_ms"]["p50"], "p99_ms": rep_m["latency_ms"]["p99"],
+                                              "value": rep_m["value"], "unit": UNIT},
                        "plain_fp32": {"p50_ms": rep_p["latency_ms"]["p50"], "p99_ms": rep_p["latency_ms"]["p99"],
                                       "value": rep_p["value"], "unit": UNIT},
                        "p99_ratio_plain_over_batched": rep_p["latency_ms"]["p99"] / max(1e-9, rep_b["latency_ms"]["p99"]),
                        "burst_peak_value": burst["value"],
                    },
                    "batched_replay": rep_b,
+                   "batched_mixed_bf16_replay": rep_m,
                    "plain_fp32_replay": rep_p,
                    "burst_all_submitted_at_once": burst,
                    "batched_path": "streaming add/subtract update, up to 32 sessions per launch of the persistent kernel",
+                   "batched_mixed_path": "the same with BF16 sessions: exact streaming update, drift re-sum slices "
+                                         "with tcgen05 linear sums",
                    "plain_path": "one trial at a time, full-window FP32 recompute (FC_MODE_FULL), no batching",
                    "burst_note": "every trial of the trace submitted at t = 0: peak aggregate throughput; its "
                                  "latencies are queueing behind the whole burst, not the serving latency"}
@@ -776,7 +815,8 @@ def run_ours(args, w, wname):
                    "l2": "inputs larger than L2 (27.8 GB resident state), no flush",
                    "parallelism": f"{world} independent session(s), one per GPU"},
         "latency_ms": {"p50": p50, "p99": p99, "what": "device time from push enqueue to network ready"},
-        "plain_fp32": plain, "mixed_bf16_full_window": mixed, "serving": serving, "configs": configs,
+        "plain_fp32": plain, "mixed_bf16_full_window": mixed, "mixed_bf16_stream": mixed_stream,
+        "serving": serving, "configs": configs,
         "roofline": roofline, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
         "clocks": clocks.summary(), "gpu_launches": launches,
     }

@@ -86,7 +86,11 @@ typedef struct {
 
 typedef enum {
     FC_PREC_FP32 = 0, /* every sum from exactly rounded FP32 terms, FP64-class accumulation */
-    FC_PREC_TF32 = 1, /* full-window linear sums on tensor cores, TF32 operands, FP32 accumulate */
+    FC_PREC_TF32 = 1, /* linear sums (CSD, phasors) on tensor cores, TF32 operands, FP32 accumulate:
+                         FC_MODE_FULL recomputes them each push; FC_MODE_STREAM (sliding window,
+                         resum_period >= 0) keeps the exact streaming update and takes them from the
+                         tensor cores in its drift re-sum (COH and PLV then carry the operand
+                         rounding; IMAGCOHY, PLI, USPLI, WPLI, DSWPLI stay exact-term sums) */
     FC_PREC_BF16 = 2, /* same with BF16 operands */
     FC_PREC_FP16 = 3  /* same with FP16 operands */
 } fc_precision;
@@ -343,6 +347,9 @@ typedef struct {
                           each a full-window recompute (no batching, no streaming sums) */
     int launch_blocks; /* state blocks (one 32 x 32 tile pair x one bin, 106 KB of traffic)
                           per launch: 0 = 65536 (about 1.2 ms on GB300); < 0 = no limit */
+    fc_precision precision; /* streaming sessions (plain = 0): FC_PREC_FP32 (default), or a
+                          tensor-core precision whose drift re-sum takes the linear sums from
+                          the tensor cores (see fc_config.precision) */
 } fc_server_config;
 
 typedef struct {
@@ -371,7 +378,7 @@ double fc_server_now_ms(void);
 
 fc_status fc_server_create(const fc_server_config* cfg, fc_server** out);
 
-/* Open a session (same settings as fc_session_create, streaming mode, FP32). Returns
+/* Open a session (same settings as fc_session_create, streaming mode, the server's precision). Returns
  * FC_ERR_ADMISSION without allocating when its device memory would exceed the budget;
  * the caller may retry after closing sessions. *session_id receives the id. */
 fc_status fc_server_open(fc_server* sv, int n_nodes, int n_samples, double fs, fc_band band,

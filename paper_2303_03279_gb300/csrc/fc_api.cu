@@ -388,9 +388,10 @@ void herk_res_groups(int nseg, int seg_max, int nsel, int sms, long long P, int 
 // Spectral pair sums over the whole window (bulk push, re-sum, full mode).
 fc_status stage_window(fc_session* s, int count, bool write_acc) {
     NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, 1, s->ctrl, count};
-    if (s->ops && !write_acc) na.tiny = s->tiny_flags;  // read by the non-linear sums
+    const bool mixed_full = s->ops && !s->mixed_stream && !write_acc;
+    if (mixed_full) na.tiny = s->tiny_flags;  // read by the non-linear sums
     LAUNCH(FC_K_NODE, launch_node(na, s->stream));
-    if (s->ops && !write_acc) {
+    if (mixed_full) {
         // mixed precision: linear sums (COH, IMAGCOHY, PLV) on the tensor cores, the
         // non-linear sums (PLI, USPLI, WPLI, DSWPLI) on the CUDA cores
         PackArgs pk{};
@@ -470,11 +471,72 @@ bool resum_on(const fc_session* s) { return s->W > 0 && s->cfg.resum_period >= 0
 
 int push_node_mode(const fc_session* s) { return (resum_on(s) && s->resum_phase == 0) ? 1 : 0; }
 
+PackArgs ring_pack_args(fc_session* s, int count) {
+    PackArgs pk{};
+    pk.ring = s->ring;
+    pk.ops = s->ops;
+    pk.n = s->n;
+    pk.B = s->B;
+    pk.W = s->W;
+    pk.slots = s->slots;
+    pk.ntiles = s->nt128;
+    pk.nchunks = s->nchunks;
+    pk.count = count;
+    pk.ab_format = s->ab_format;
+    pk.ctrl = s->ctrl;
+    return pk;
+}
+
+// Mixed-precision streaming: push r of a period re-sums the 128-node tile pairs
+// [ntp128 r / R, ntp128 (r + 1) / R): their linear sums (CSD re, phasor re and im) from the
+// tensor cores over the operand ring, their non-linear sums (sum Im, sum |Im|, sum Im^2,
+// signs) from the exact window kernel on the 32-node tile pairs inside them. The ring takes
+// this push's trial first (and drops the one leaving the window).
+fc_status stage_resum_slice_mixed(fc_session* s, long long r, long long R) {
+    PackArgs pk = ring_pack_args(s, 1);
+    LAUNCH(FC_K_HERK_TC, launch_pack_ring(pk, 0, s->stream));
+    const int p0 = (int)(s->ntp128 * r / R), p1 = (int)(s->ntp128 * (r + 1) / R);
+    if (p1 <= p0) return FC_OK;
+    HerkArgs ha{};
+    ha.ops = s->ops;
+    ha.tile_a = s->tile_a128;
+    ha.tile_b = s->tile_b128;
+    ha.inv_psd = s->inv_psd;
+    ha.n = s->n;
+    ha.B = s->B;
+    ha.ntp = p1 - p0;
+    ha.tp0 = p0;
+    ha.nchunks = s->nchunks;
+    ha.W = s->W;
+    ha.count = 1;
+    ha.ab_format = s->ab_format;
+    ha.grid_ctas = s->num_sms;
+    ha.groups = s->B;  // one bin per unit: no band order to keep
+    ha.group_bins = 1;
+    ha.P = s->P;
+    ha.mask = s->mask;
+    ha.fsel0 = 0;      // every computed bin: these are the accumulators, not the band average
+    ha.fsel1 = s->B;
+    ha.ctrl = s->ctrl;
+    ha.acc_out = s->acc;
+    ha.nt32 = s->nt;
+    LAUNCH(FC_K_HERK_TC, launch_herk_tc(ha, s->stream));
+    PairArgs pa = pair_args(s, false, 1);
+    pa.tp_list = s->list32;
+    pa.tp0 = s->list32_off[p0];
+    pa.tp_count = s->list32_off[p1] - s->list32_off[p0];
+    pa.groups = s->B;
+    pa.group_bins = 1;
+    LAUNCH(FC_K_WINDOW, launch_window_nonlinear_acc(pa, s->stream));
+    return FC_OK;
+}
+
 fc_status stage_resum_slice(fc_session* s) {
     if (!resum_on(s)) return FC_OK;
     const long long R = s->cfg.resum_period > 0 ? s->cfg.resum_period : s->W;
     const long long r = s->resum_phase % R;
     s->resum_phase = (r + 1) % R;
+    if (s->mixed_stream) return stage_resum_slice_mixed(s, r, R);
     const int tp0 = (int)(s->ntp * r / R), tp1 = (int)(s->ntp * (r + 1) / R);
     if (tp1 <= tp0) return FC_OK;
     PairArgs pa = pair_args(s, false, 1);
@@ -525,6 +587,10 @@ fc_status push_bulk(fc_session* s, const float* x, int count, bool write_acc) {
         if (st != FC_OK) return st;
         st = stage_window(s, count, write_acc);
         if (st != FC_OK) return st;
+        if (s->mixed_stream) {  // the operand ring of the new window
+            PackArgs pk = ring_pack_args(s, count);
+            LAUNCH(FC_K_HERK_TC, launch_pack_ring(pk, 1, s->stream));
+        }
     }
     st = stage_time_metrics(s, x, count, write_from, 1);
     if (st != FC_OK) return st;
@@ -694,7 +760,7 @@ fc_status fc_push_batch_post(fc_session* const* ss, FcCtrl* const* snap, int cou
 void fc_count_launch(fc_session* s) { s->launches++; }
 
 // Device bytes fc_session_create would allocate for these settings (mirrors its allocations).
-size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode mode) {
+size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode mode, fc_precision prec) {
     const size_t nt = (n + FC_T - 1) / FC_T, ntp = nt * (nt + 1) / 2;
     const size_t P = (size_t)n * (n - 1) / 2;
     const size_t slots = mode == FC_MODE_FULL ? W : (W > 0 ? W + 1 : 1);
@@ -702,6 +768,13 @@ size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode 
     if (mask & FC_SPECTRAL_METRICS) {
         b += (size_t)N * B * 8 + slots * B * n * 8 + (size_t)B * n * 12 + ntp * 4;
         if (mode == FC_MODE_STREAM) b += ntp * B * FC_BLOCK_WORDS * 4;
+        if (mode == FC_MODE_STREAM && prec != FC_PREC_FP32) {
+            // operand ring, 128-node tile lists and the 32-in-128 tile-pair list
+            const size_t nt128 = (n + 127) / 128, ntp128 = nt128 * (nt128 + 1) / 2;
+            const size_t per_chunk = prec == FC_PREC_TF32 ? 32 : 64;
+            const size_t nchunks = (2 * slots + per_chunk - 1) / per_chunk;
+            b += nt128 * B * 4 * nchunks * herk_chunk_bytes() + ntp128 * 4 + ntp * 4;
+        }
         int wg, wgb;
         const int sms = fc_device_sms();
         window_groups((long long)ntp, B, (long long)P, W, sms, wg, wgb);
@@ -765,9 +838,10 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
     if (cfg.mode != FC_MODE_STREAM && cfg.mode != FC_MODE_FULL) return fail(FC_ERR_INVALID_ARG, "bad mode");
     if (cfg.mode == FC_MODE_FULL && window < 1) return fail(FC_ERR_INVALID_ARG, "full mode needs window >= 1");
     if (cfg.precision < FC_PREC_FP32 || cfg.precision > FC_PREC_FP16) return fail(FC_ERR_INVALID_ARG, "bad precision");
-    if (cfg.precision != FC_PREC_FP32 && cfg.mode != FC_MODE_FULL)
+    if (cfg.precision != FC_PREC_FP32 && cfg.mode == FC_MODE_STREAM && (window < 1 || cfg.resum_period < 0))
         return fail(FC_ERR_UNSUPPORTED,
-                    "tensor-core precisions apply to FC_MODE_FULL; the streaming sums stay exact FP32 terms");
+                    "a tensor-core precision in stream mode applies to the drift re-sum of a sliding window "
+                    "(window >= 1, resum_period >= 0)");
     if ((cfg.dev_alloc == nullptr) != (cfg.dev_free == nullptr))
         return fail(FC_ERR_INVALID_ARG, "dev_alloc and dev_free must be given together");
     // band bins: f_lo <= k fs / nfft < f_hi
@@ -875,7 +949,37 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
             TRY(upload(s, s->tile_b, tb.data(), tb.size() * sizeof(unsigned short)));
         }
         if (cfg.mode == FC_MODE_STREAM) TRY(alloc_zero(s, (size_t)s->ntp * B * FC_BLOCK_WORDS, &s->acc));
-        if (cfg.precision != FC_PREC_FP32) {
+        if (cfg.precision != FC_PREC_FP32 && cfg.mode == FC_MODE_STREAM) {
+            // mixed-precision streaming: the drift re-sum takes the linear sums from the tensor
+            // cores over an operand ring of the window (inner dimension 2 (W + 1): ring slots)
+            s->mixed_stream = true;
+            s->ab_format = cfg.precision == FC_PREC_BF16 ? 1 : (cfg.precision == FC_PREC_FP16 ? 0 : 2);
+            const int per_chunk = s->ab_format == 2 ? 32 : 64;
+            s->nchunks = (2 * s->slots + per_chunk - 1) / per_chunk;
+            s->nt128 = (n_nodes + 127) / 128;
+            s->ntp128 = s->nt128 * (s->nt128 + 1) / 2;
+            std::vector<unsigned short> ta, tb;
+            std::vector<int> l32;
+            s->list32_off.assign(1, 0);
+            for (int a = 0; a < s->nt128; ++a)
+                for (int b = a; b < s->nt128; ++b) {
+                    ta.push_back((unsigned short)a);
+                    tb.push_back((unsigned short)b);
+                    // the 32-node tile pairs inside this 128-node tile pair
+                    for (int x = 4 * a; x < std::min(4 * a + 4, s->nt); ++x)
+                        for (int y = std::max(x, 4 * b); y < std::min(4 * b + 4, s->nt); ++y)
+                            l32.push_back(x * s->nt - x * (x - 1) / 2 + (y - x));
+                    s->list32_off.push_back((int)l32.size());
+                }
+            TRY(alloc_zero(s, ta.size(), &s->tile_a128));
+            TRY(alloc_zero(s, tb.size(), &s->tile_b128));
+            TRY(upload(s, s->tile_a128, ta.data(), ta.size() * sizeof(unsigned short)));
+            TRY(upload(s, s->tile_b128, tb.data(), tb.size() * sizeof(unsigned short)));
+            TRY(alloc_zero(s, l32.size(), &s->list32));
+            TRY(upload(s, s->list32, l32.data(), l32.size() * sizeof(int)));
+            TRY(alloc_zero(s, (size_t)s->nt128 * B * 4 * s->nchunks * herk_chunk_bytes(), &s->ops));
+        }
+        if (cfg.precision != FC_PREC_FP32 && cfg.mode == FC_MODE_FULL) {
             s->ab_format = cfg.precision == FC_PREC_BF16 ? 1 : (cfg.precision == FC_PREC_FP16 ? 0 : 2);
             const int per_chunk = s->ab_format == 2 ? 32 : 64;  // inner elements per 128-byte K-chunk
             s->nchunks = (2 * window + per_chunk - 1) / per_chunk;

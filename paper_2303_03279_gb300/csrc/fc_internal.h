@@ -128,6 +128,9 @@ struct fc_session {
     unsigned short* tile_b128;
     unsigned char* ops;     // packed operands [nt128][B][4][nchunks][16 KB]
     unsigned char* tiny_flags;  // [B][n] a trial of the window has a tiny component (mixed path)
+    bool mixed_stream;      // streaming session whose re-sum takes the linear sums from the tensor cores
+    int* list32;            // mixed streaming: 32-node tile pairs grouped by 128-node tile pair
+    std::vector<int> list32_off;  // (host) first list entry of each 128-node tile pair, [ntp128 + 1]
     unsigned char* cor_ops; // COR split-TF32 operand ring [slots][cor_nt][cor_nchunks][2][16 KB]
     int cor_nt, cor_ntp, cor_nchunks;
     unsigned short* seg_a;  // resident-operand segments of the 128-node tile pairs (see HerkArgs)
@@ -211,7 +214,11 @@ struct PairArgs {
     int grid_ctas;     // persistent grid size of the streaming kernel
     const FcCtrl* ctrl;
     const unsigned char* tiny;  // non-linear sums: [B][n] tiny-component flags of the window (k_node)
+    const int* tp_list;         // window kernel, optional: tile pairs tp_list[tp0 ..] instead of tp0 ..
 };
+// The window kernel's non-linear fields only (sum Im, sum |Im|, sum Im^2, sign count) into the
+// accumulators; the linear fields are left as they are.
+cudaError_t launch_window_nonlinear_acc(const PairArgs& a, cudaStream_t st);
 cudaError_t launch_stream_update(const PairArgs& a, cudaStream_t st);
 
 // A batch of sessions updated by one launch of the streaming kernel (passed by value as
@@ -256,8 +263,18 @@ struct HerkArgs {
     const unsigned short* seg_b0;
     const unsigned short* seg_b1;
     int nseg, seg_max;
+    // accumulator mode (drift re-sum of a mixed-precision streaming session): the products of
+    // 128-node tile pairs tp0 .. tp0 + ntp - 1 are written as the linear sums (CSD re, phasor
+    // re and im) of the streaming accumulators acc (nt32 node tiles of 32), not as metrics
+    float* acc_out;
+    int tp0, nt32;
 };
 cudaError_t launch_pack_operands(const PackArgs& a, cudaStream_t st);
+// Operand ring of a mixed-precision streaming session (inner position k < slots: ring slot k,
+// first half; slots <= k < 2 slots: second half; slots outside the window hold zeros).
+// mode 0: the newest trial's slot is written and the slot of the trial leaving the window
+// cleared; mode 1: every slot rebuilt from the window (after a bulk push).
+cudaError_t launch_pack_ring(const PackArgs& a, int mode, cudaStream_t st);
 cudaError_t launch_herk_tc(const HerkArgs& a, cudaStream_t st);
 cudaError_t launch_herk_band(const HerkArgs& a, cudaStream_t st);
 size_t herk_chunk_bytes();
@@ -394,7 +411,8 @@ PairArgs fc_push_stream_args(fc_session* s);
 fc_status fc_push_batch_pre(fc_session* const* ss, const float* const* x, int count, cudaStream_t st);
 fc_status fc_push_batch_post(fc_session* const* ss, FcCtrl* const* snap, int count, cudaStream_t st);
 void fc_count_launch(fc_session* s);
-size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode mode);
+size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode mode,
+                             fc_precision prec = FC_PREC_FP32);
 int fc_band_bins(double fs, fc_band band, int* first);
 
 cudaError_t launch_expand_dense(const float* packed, float* dense, int n, int antisym,

@@ -404,6 +404,10 @@ fc_status fc_server_create(const fc_server_config* cfg, fc_server** out) {
         delete sv;
         return sfail(FC_ERR_INVALID_ARG, "max_batch must be 0..32");
     }
+    if (sv->cfg.precision < FC_PREC_FP32 || sv->cfg.precision > FC_PREC_FP16) {
+        delete sv;
+        return sfail(FC_ERR_INVALID_ARG, "bad precision");
+    }
     cudaGetDevice(&sv->device);
     sv->num_sms = fc_device_sms(sv->device);
     if (cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -422,6 +426,10 @@ fc_status fc_server_open(fc_server* sv, int n_nodes, int n_samples, double fs, f
     size_t need = 0;
     fc_status st = fc_server_session_bytes(n_nodes, n_samples, fs, band, metric_mask, window, sv->cfg.plain, &need);
     if (st != FC_OK) return st;
+    if (!sv->cfg.plain && sv->cfg.precision != FC_PREC_FP32) {  // the operand ring of a mixed-precision session
+        const int B = fc_band_bins(fs, band, nullptr);
+        need = fc_plan_session_bytes(n_nodes, n_samples, B, window, metric_mask, FC_MODE_STREAM, sv->cfg.precision);
+    }
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         if (sv->cfg.hbm_budget && sv->used + need > sv->cfg.hbm_budget)
@@ -432,6 +440,7 @@ fc_status fc_server_open(fc_server* sv, int n_nodes, int n_samples, double fs, f
     fc_config_default(&cfg);
     cfg.stream = sv->stream;
     cfg.mode = sv->cfg.plain ? FC_MODE_FULL : FC_MODE_STREAM;
+    if (!sv->cfg.plain) cfg.precision = sv->cfg.precision;
     fc_session* s = nullptr;
     {
         std::lock_guard<std::mutex> dk(sv->dev_mu);

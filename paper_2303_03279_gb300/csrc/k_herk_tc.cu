@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
                 const int ch = (int)(loads % a.nchunks);
                 for (; lph < ph; ++lph)
                     if (lph & 1) seq_next_bin(a, ls);  // after phase B: the next bin
-                const int tp = ls.u / a.groups, f = ls.f;
+                const int tp = a.tp0 + ls.u / a.groups, f = ls.f;
                 const int ta = a.tile_a[tp], tb = a.tile_b[tp];
                 const int k0 = (ph & 1) ? 2 : 0;  // phase A: X operands, phase B: U operands
                 unsigned char* dst = smem + st * STAGE_BYTES;
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
         auto prefetch = [&](const HerkSeq& t) {
             pf_i[0] = pf_i[1] = pf_j = 0.f;
             if (t.u >= units) return;
-            const int ptp = t.u / a.groups;
+            const int ptp = a.tp0 + t.u / a.groups;
             const int pta = a.tile_a[ptp], ptb = a.tile_b[ptp];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
         for (int ph = 0; ph < nphase; ++ph) {
             const int b = ph & 1;
             if (ph > 0 && b == 0) seq_next_bin(a, es);
-            const int tp = es.u / a.groups, f = es.f;
+            const int tp = a.tp0 + es.u / a.groups, f = es.f;
             const int ta = a.tile_a[tp], tb = a.tile_b[tp];
             const int j = tb * TILE + quarter * 32 + (tid & 31);  // this thread's TMEM lane: column node j
             if (b == 0) {  // this bin's 1/sqrt(PSD), staged by this warp for itself; next bin's fetched
@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
             }
             fence_after();
             const uint32_t col = (uint32_t)(b * 2 * TILE);
-            float* out = a.part + (size_t)(es.u % a.groups) * 3 * a.P;  // this group's band sums
+            // this group's band sums (none in accumulator mode)
+            float* out = a.acc_out ? nullptr : a.part + (size_t)(es.u % a.groups) * 3 * a.P;
             // the unit's first bin writes its values, the later bins add to them (same thread,
             // same address: the reductions land after the store and in bin order)
             const bool first = f == a.fsel0 + (es.u % a.groups) * a.group_bins;
@@ -281,7 +282,36 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
                 tmem_keep(rre[s4]);
                 tmem_keep(rim[s4]);
             }
-            if (j < a.n) {
+            if (a.acc_out && j < a.n) {
+                // accumulator mode: the raw sums of pair (i, j) (i < j) into the streaming
+                // accumulator block of its 32-node tile pair, word (i % 32) 32 + j % 32: phase A the
+                // CSD real part (field 0), phase B the phasor sums (fields 2, 3); hi word the
+                // FP32 sum, lo word 0
+                const int tb32 = j >> 5;
+#pragma unroll
+                for (int s4 = 0; s4 < 4; ++s4) {
+                    const int i0 = ta * TILE + ibase + 16 * s4;
+                    const int ta32 = i0 >> 5;
+                    const long long tp32 = (long long)ta32 * a.nt32 - (long long)ta32 * (ta32 - 1) / 2 + (tb32 - ta32);
+                    float* blk = a.acc_out + ((size_t)tp32 * a.B + f) * FC_BLOCK_WORDS;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int i = i0 + q;
+                        if (j <= i || i >= a.n) continue;
+                        const int w = (i & 31) * 32 + (j & 31);
+                        const float vre = __uint_as_float(rre[s4][q]), vim = __uint_as_float(rim[s4][q]);
+                        if (b == 0) {
+                            blk[0 * FC_TT + w] = vre;
+                            blk[1 * FC_TT + w] = 0.f;
+                        } else {
+                            blk[4 * FC_TT + w] = vre;
+                            blk[5 * FC_TT + w] = 0.f;
+                            blk[6 * FC_TT + w] = vim;
+                            blk[7 * FC_TT + w] = 0.f;
+                        }
+                    }
+                }
+            } else if (j < a.n) {
                 // packed index of (i, j) for i = ta TILE + ibase, then p(i + 1) = p(i) + n - i - 2
                 // (below 2^31: n < 65536); the unit's first bin stores, the later ones add
                 // (atomicAdd without its result: a fire-and-forget reduction; same thread, same
@@ -775,6 +805,61 @@ __global__ void k_pack_operands(PackArgs a) {
     }
 }
 
+// Operand ring of a mixed-precision streaming session. Element (tile row m, inner k) of the
+// block (tile, bin, kind, chunk) as in k_pack_operands, with the ring slot s of a trial at
+// inner positions s (first half) and slots + s (second half). One thread per (slot entry,
+// bin, node) writes that element of all four kinds; slots outside the window hold zeros.
+__device__ __forceinline__ void put_elem(unsigned char* ops, const PackArgs& a, int tile, int f, int kind, int m,
+                                         int k, float v) {
+    const int esize = a.ab_format == 2 ? 4 : 2;
+    const int per16 = 16 / esize;
+    const int chunk = k / (8 * per16), kc = (k / per16) % 8, e16 = k % per16;
+    unsigned char* dst = ops + ((((size_t)tile * a.B + f) * 4 + kind) * a.nchunks + chunk) * (size_t)CHUNK_BYTES +
+                         (size_t)((m / 8) * 8 + kc) * 128 + (m % 8) * 16 + e16 * esize;
+    if (a.ab_format == 2) {
+        uint32_t t;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
+        *reinterpret_cast<uint32_t*>(dst) = t;
+    } else if (a.ab_format == 1) {
+        *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
+    } else {
+        *reinterpret_cast<__half*>(dst) = __float2half_rn(v);
+    }
+}
+
+__global__ void k_pack_ring(PackArgs a, int mode) {
+    const FcCtrl* c = a.ctrl;
+    if (c->bad) return;
+    const long long end = c->pushed + a.count;  // window after this call: [end - W, end)
+    const long long start = end > a.W ? end - a.W : 0;
+    const int nslot = mode == 0 ? 2 : a.slots;
+    const long long total = (long long)nslot * a.B * a.n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int node = (int)(e % a.n);
+        const int f = (int)((e / a.n) % a.B);
+        const int q = (int)(e / ((long long)a.n * a.B));
+        // mode 0: q = 0 the newest trial's slot, q = 1 the slot of the trial that left
+        const int s = mode == 0 ? (int)((q == 0 ? end - 1 : end) % a.slots) : q;
+        bool in_window = false;
+        if (mode == 0) {
+            in_window = q == 0;
+        } else {
+            // the window's trial in slot s, if any: t = s (mod slots), start <= t < end
+            const long long t = end - 1 - (((end - 1 - s) % a.slots) + a.slots) % a.slots;
+            in_window = t >= start && t >= 0;
+        }
+        float2 X = make_float2(0.f, 0.f);
+        if (in_window) X = a.ring[((size_t)s * a.B + f) * a.n + node];
+        const float2 u = phasor_of_x(X);
+        const int tile = node / TILE, m = node % TILE;
+        const float v[2][4] = {{X.x, X.y, u.x, u.y}, {X.y, -X.x, u.y, -u.x}};
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int kind = 0; kind < 4; ++kind) put_elem(a.ops, a, tile, f, kind, m, h * a.slots + s, v[h][kind]);
+    }
+}
+
 // Band average of COH, IMAGCOHY, PLV: the bin groups' sums added in group order, times 1/bins.
 __global__ void k_herk_band(HerkArgs a) {
     const FcCtrl* c = a.ctrl;
@@ -825,6 +910,15 @@ cudaError_t launch_herk_tc(const HerkArgs& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         k_herk_tc<0><<<ctas, THREADS, SMEM_BYTES, st>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_ring(const PackArgs& a, int mode, cudaStream_t st) {
+    const long long total = (long long)(mode == 0 ? 2 : a.slots) * a.B * a.n;
+    long long blocks = (total + 255) / 256;
+    const long long cap = 8LL * fc_device_sms();
+    if (blocks > cap) blocks = cap;
+    k_pack_ring<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(a, mode);
     return cudaGetLastError();
 }
 

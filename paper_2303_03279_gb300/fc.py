@@ -76,7 +76,7 @@ class fc_top_info(C.Structure):
 
 class fc_server_config(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_batch", C.c_int), ("plain", C.c_int),
-                ("launch_blocks", C.c_int)]
+                ("launch_blocks", C.c_int), ("precision", C.c_int)]
 
 
 class fc_result(C.Structure):
@@ -432,8 +432,9 @@ def fc_server_now_ms() -> float:
     return float(load().fc_server_now_ms())
 
 
-def fc_server_create(hbm_budget: int = 0, max_batch: int = 0, plain: bool = False, launch_blocks: int = 0):
-    cfg = fc_server_config(int(hbm_budget), int(max_batch), 1 if plain else 0, int(launch_blocks))
+def fc_server_create(hbm_budget: int = 0, max_batch: int = 0, plain: bool = False, launch_blocks: int = 0,
+                     precision: int = 0):
+    cfg = fc_server_config(int(hbm_budget), int(max_batch), 1 if plain else 0, int(launch_blocks), int(precision))
     out = C.c_void_p()
     _check(load().fc_server_create(C.byref(cfg), C.byref(out)))
     return out

@@ -148,8 +148,14 @@ def test_mixed_window_fill_and_slide():
                 _check(s, min(t + 1, W))
 
 
-def test_streaming_rejects_tensor_core_precision():
-    with pytest.raises(fc.FcError) as e:
-        fc.Session(40, 64, 128.0, (4.0, 40.0, 64), "hann", fc.FC_SPECTRAL_METRICS, 4,
-                   mode=fc.FC_MODE_STREAM, precision=fc.FC_PREC_BF16)
-    assert e.value.status == fc.FC_ERR_UNSUPPORTED
+def test_streaming_tensor_core_precision_needs_a_sliding_window_with_resum():
+    """In stream mode a tensor-core precision applies to the drift re-sum of a sliding window:
+    a cumulative window (0) or a session without re-sums is refused."""
+    for window, period in ((0, 0), (4, -1)):
+        with pytest.raises(fc.FcError) as e:
+            fc.Session(40, 64, 128.0, (4.0, 40.0, 64), "hann", fc.FC_SPECTRAL_METRICS, window,
+                       mode=fc.FC_MODE_STREAM, precision=fc.FC_PREC_BF16, resum_period=period)
+        assert e.value.status == fc.FC_ERR_UNSUPPORTED
+    with fc.Session(40, 64, 128.0, (4.0, 40.0, 64), "hann", fc.FC_SPECTRAL_METRICS, 4,
+                    mode=fc.FC_MODE_STREAM, precision=fc.FC_PREC_BF16) as s:
+        assert s.info().precision == fc.FC_PREC_BF16

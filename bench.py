@@ -456,8 +456,43 @@ def config_legs(fc, torch, stream):
     return out
 
 
+def run_project_case(args):
+    """Source projection of sensor trials (the paper's source-level pipeline): 306 MEG-sized
+    channels onto 5124 sources, 500-sample trials, 40 bins, W = 20, streaming pushes. The
+    spectral-only session projects band spectra (frequency domain); a session that also
+    holds COR projects the time series. Per push: device time of the projection and
+    spectrum kernels of each path."""
+    import torch
+    from paper_2303_03279_gb300 import fc
+    from synth import white_trials
+
+    fc.load()
+    n, C, N, W, pushes = 5124, 306, 500, 20, 5
+    M = (np.random.default_rng(9).standard_normal((n, C)) / np.sqrt(C)).astype(np.float32)
+    x = torch.from_numpy(white_trials(7, W + pushes, C, N)).cuda()
+    out = {"case": "project_5124", "description": run_project_case.__doc__.split("\n\n")[0].replace("\n    ", " ")}
+    for name, mask in (("frequency_domain (spectral metrics)", fc.FC_SPECTRAL_METRICS),
+                       ("time_domain (spectral metrics + COR)", fc.FC_SPECTRAL_METRICS | fc.FC_COR)):
+        with fc.Session(n, N, 1000.0, (4.0, 44.0, 1000), "hann", mask, W) as s:
+            fc.fc_set_projection(s.handle, torch.from_numpy(M).cuda())
+            fc.fc_push_trials(s.handle, x[:W].contiguous(), W)
+            fc.fc_sync(s.handle)
+            fc.fc_set_profiling(s.handle, True)
+            fc.fc_kernel_times(s.handle, reset=True)
+            for k in range(pushes):
+                fc.fc_push_trial(s.handle, x[W + k])
+            fc.fc_sync(s.handle)
+            kt = fc.fc_kernel_times(s.handle, reset=True)
+        out[name] = {k: round(v[1] / pushes, 4) for k, v in kt.items() if k in ("project", "spectrum") and v[0]}
+    out["flops_per_trial"] = {"frequency_domain": 2 * n * C * 2 * 40, "time_domain": 2 * n * C * N}
+    print(json.dumps(out))
+    return 0
+
+
 def run_case(args):
     """One small named case (the profiler captures' workloads); prints its timing per push."""
+    if args.case == "project_5124":
+        return run_project_case(args)
     import torch
     from paper_2303_03279_gb300 import fc
     from synth import meg_pink_trials, white_trials
@@ -844,7 +879,8 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="skip the EEG, MEG and source-space legs")
     ap.add_argument("--no-cpu-all-core", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="print the paper-style performance sweep instead")
-    ap.add_argument("--case", choices=sorted(CASES), help="run one small named case (profiler captures)")
+    ap.add_argument("--case", choices=sorted(CASES) + ["project_5124"],
+                    help="run one small named case (profiler captures)")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -238,7 +238,26 @@ XcorArgs xcor_args(fc_session* s, const float* x, int count, int write_from, int
 // ------------------------------------------------------------------ push stages
 fc_status stage_spectra(fc_session* s, const float* x, int count, int write_from) {
     SpectrumArgs sa = spectrum_args(s, x, count, write_from);
-    LAUNCH(FC_K_SPECTRUM, launch_spectrum(sa, s->stream));
+    if (s->spec_project) {
+        // x holds sensor trials: their band spectra, then the projection into the ring
+        const int keep = count - write_from;
+        if (s->sens_trials < keep) {
+            if (s->sens_spec) cudaFree(s->sens_spec);
+            s->sens_spec = nullptr;
+            s->sens_trials = 0;
+            CK(cudaMalloc(&s->sens_spec, (size_t)keep * s->B * s->proj_C * sizeof(float2)));
+            s->sens_trials = keep;
+        }
+        SpectrumArgs ss = sa;
+        ss.n = s->proj_C;
+        ss.ring = s->sens_spec;
+        ss.direct = 1;
+        LAUNCH(FC_K_SPECTRUM, launch_spectrum(ss, s->stream));
+        LAUNCH(FC_K_PROJECT, launch_project_spectra(s->proj, s->sens_spec, s->ring, s->n, s->proj_C, s->B, keep,
+                                                    write_from, s->slots, s->ctrl, s->stream));
+    } else {
+        LAUNCH(FC_K_SPECTRUM, launch_spectrum(sa, s->stream));
+    }
     if (!s->calibrated) {
         for (int ph = 0; ph < 3; ++ph) LAUNCH(FC_K_CALIBRATE, launch_calibrate(sa, s->stream, ph));
     }
@@ -552,7 +571,7 @@ fc_status stage_resum_slice(fc_session* s) {
 
 // One trial through the streaming path: x points at one [n][N] trial on the device.
 fc_status push_one_stream(fc_session* s, const float* x, bool finalize) {
-    const long long nx = (long long)s->n * s->N;
+    const long long nx = (long long)(s->spec_project ? s->proj_C : s->n) * s->N;
     LAUNCH(FC_K_OTHER, launch_validate(x, nx, s->ctrl, s->stream));
     fc_status st;
     if (s->spectral) {
@@ -577,7 +596,7 @@ fc_status push_one_stream(fc_session* s, const float* x, bool finalize) {
 
 // Many trials at once, then one window computation (stream bulk or full mode).
 fc_status push_bulk(fc_session* s, const float* x, int count, bool write_acc) {
-    const long long nx = (long long)s->n * s->N;
+    const long long nx = (long long)(s->spec_project ? s->proj_C : s->n) * s->N;
     LAUNCH(FC_K_OTHER, launch_validate(x, nx * count, s->ctrl, s->stream));
     const int keep = s->W > 0 ? std::min(count, s->W) : count;
     const int write_from = count - keep;
@@ -1077,6 +1096,7 @@ fc_status fc_session_destroy(fc_session* s) {
     if (s->post_scratch) cudaFree(s->post_scratch);
     if (s->proj) cudaFree(s->proj);
     if (s->proj_in) cudaFree(s->proj_in);
+    if (s->sens_spec) cudaFree(s->sens_spec);
     if (s->cor_part) cudaFree(s->cor_part);
     for (int b = 0; b < 2; ++b) {
         if (s->x_in[b]) cudaFree(s->x_in[b]);
@@ -1111,6 +1131,23 @@ fc_status fc_push_trials(fc_session* s, const float* x, int count, int x_on_devi
             }
             CK(cudaMemcpyAsync(s->proj_in, x, per_in * count * sizeof(float), cudaMemcpyHostToDevice, s->stream));
             xin = s->proj_in;
+        }
+        if (!s->time_mask) {
+            // spectral metrics only: the sensor trials go to the spectrum stage, which
+            // projects their band spectra (M commutes with the taper and the DFT)
+            s->spec_project = true;
+            const int bulk_min = std::max(2, s->W / 4);
+            fc_status st;
+            if (s->cfg.mode == FC_MODE_FULL)
+                st = push_bulk(s, xin, count, false);
+            else if (s->W > 0 && count >= bulk_min)
+                st = push_bulk(s, xin, count, true);
+            else {
+                st = FC_OK;
+                for (int u = 0; u < count && st == FC_OK; ++u) st = push_one_stream(s, xin + per_in * u, u == count - 1);
+            }
+            s->spec_project = false;
+            return st;
         }
         fc_status st = ensure_stage(s, count);
         if (st != FC_OK) return st;

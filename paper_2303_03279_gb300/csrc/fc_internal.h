@@ -98,6 +98,9 @@ struct fc_session {
     int proj_C;
     float* proj_in;         // staged sensor trials [proj_in_trials][proj_C][N]
     int proj_in_trials;
+    bool spec_project;      // this push projects band spectra (a projection and no COR / XCOR)
+    float2* sens_spec;      // sensor band spectra of the trials of one push [sens_trials][B][proj_C]
+    int sens_trials;
 
     // device buffers
     FcCtrl* ctrl;
@@ -175,6 +178,7 @@ struct SpectrumArgs {
     float2* ring;
     int slots, n, N, B;
     FcCtrl* ctrl;
+    int direct;            // 1: trial write_from + t into slot t of `ring`, unscaled (sensor spectra)
 };
 cudaError_t launch_validate(const float* x, long long count, FcCtrl* ctrl, cudaStream_t st);
 cudaError_t launch_spectrum(const SpectrumArgs& a, cudaStream_t st);
@@ -387,6 +391,11 @@ cudaError_t launch_wait_probe(FcCtrl* ctrl, unsigned long long limit_ns, cudaStr
 // Y[k] = M X[k] for count trials: M [n][C], X [count][C][N], Y [count][n][N].
 cudaError_t launch_project(const float* M, const float* X, float* Y, int n, int C, int N, int count,
                            cudaStream_t st);
+// Projection of band spectra: ring slot (pushed + write_from + t) % slots, [B][n], receives
+// scale * M Xs[t] for t < count, Xs [count][B][C] (sensor spectra); scale = the session's
+// prescale (1 before calibration).
+cudaError_t launch_project_spectra(const float* M, const float2* Xs, float2* ring, int n, int C, int B, int count,
+                                   int write_from, int slots, const FcCtrl* ctrl, cudaStream_t st);
 // Kept normalized weights out[P], keep flags, degree[n] and strength[n] (both optional);
 // synchronizes the stream.
 cudaError_t launch_network_top(const float* w, long long P, int n, long long k, void* scratch, float* out,

@@ -8,6 +8,13 @@
 //
 // CTA: one 64 x 64 tile of Y (sources x samples) of one trial; 256 threads, 4 x 4 outputs
 // each; the inner dimension in chunks of 16 staged in shared memory; FMA in a fixed order.
+//
+// Sessions whose metrics are all spectral project in the frequency domain instead: the taper
+// and the band DFT act on the sample axis and M on the node axis, so the band spectra of the
+// source trials are M times the band spectra of the sensor trials. The C sensor channels are
+// transformed (k_spectrum, direct mode) and their spectra projected: 2 n C 2B flops per trial
+// instead of 2 n C N (B band bins, N samples; 80 against 500 at 40 bins of 500-sample
+// trials), the same GEMM tiling with the 2B real and imaginary parts as columns.
 #include "fc_internal.h"
 
 namespace {
@@ -66,6 +73,73 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ M, co
     }
 }
 
+// Projected band spectra of trial blockIdx.z: columns 2 b + h of the product are the real
+// (h = 0) and imaginary (h = 1) parts of bin b; written into the session's ring slot with its
+// prescale.
+__global__ void __launch_bounds__(256) k_project_spectra(const float* __restrict__ M, const float2* __restrict__ Xs,
+                                                         float2* __restrict__ ring, int n, int C, int B,
+                                                         int write_from, int slots, const FcCtrl* ctrl) {
+    if (ctrl->bad) return;
+    __shared__ float sm[TK][TM + 4];  // M tile, transposed: [k][row]
+    __shared__ float sx[TK][TN + 4];  // spectra tile: [channel][2 bin + part]
+    const int t = blockIdx.z;
+    const float2* Xt = Xs + (size_t)t * B * C;
+    const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;  // c0: first column (even)
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int cols = 2 * B;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < C; k0 += TK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * 256;
+            const int mr = e / TK, mk = e % TK;
+            const int gr = r0 + mr, gk = k0 + mk;
+            sm[mk][mr] = (gr < n && gk < C) ? M[(size_t)gr * C + gk] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {  // 16 channels x 32 bins of (re, im)
+            const int e = tid + q * 256;
+            const int xk = e / (TN / 2), xb = e % (TN / 2);
+            const int hk = k0 + xk, b = c0 / 2 + xb;
+            const float2 v = (hk < C && b < B) ? Xt[(size_t)b * C + hk] : make_float2(0.f, 0.f);
+            sx[xk][2 * xb] = v.x;
+            sx[xk][2 * xb + 1] = v.y;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < TK; ++k) {
+            float a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = sm[k][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = sx[k][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = __fmaf_rn(a[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    float scale = ctrl->scale;
+    if (scale == 0.f) scale = 1.f;
+    const int slot = (int)((ctrl->pushed + write_from + t) % slots);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gr = r0 + ty * 4 + i;
+        if (gr >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j += 2) {
+            const int b = (c0 + tx * 4 + j) / 2;
+            if (2 * b < cols)
+                ring[((size_t)slot * B + b) * n + gr] = make_float2(__fmul_rn(acc[i][j], scale), __fmul_rn(acc[i][j + 1], scale));
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_project(const float* M, const float* X, float* Y, int n, int C, int N, int count,
@@ -73,5 +147,13 @@ cudaError_t launch_project(const float* M, const float* X, float* Y, int n, int 
     if (n <= 0 || C <= 0 || N <= 0 || count <= 0 || count > 65535) return cudaErrorInvalidValue;
     dim3 grid((N + TN - 1) / TN, (n + TM - 1) / TM, count);
     k_project<<<grid, 256, 0, st>>>(M, X, Y, n, C, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_spectra(const float* M, const float2* Xs, float2* ring, int n, int C, int B, int count,
+                                   int write_from, int slots, const FcCtrl* ctrl, cudaStream_t st) {
+    if (n <= 0 || C <= 0 || B <= 0 || count <= 0 || count > 65535) return cudaErrorInvalidValue;
+    dim3 grid((2 * B + TN - 1) / TN, (n + TM - 1) / TM, count);
+    k_project_spectra<<<grid, 256, 0, st>>>(M, Xs, ring, n, C, B, write_from, slots, ctrl);
     return cudaGetLastError();
 }

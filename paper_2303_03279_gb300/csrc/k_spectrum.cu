@@ -95,10 +95,9 @@ __device__ __forceinline__ void spectrum_tile(const SpectrumArgs& a, int bx, int
     }
     const int node = node0 + ty;
     if (node >= a.n) return;
-    float scale = a.ctrl->scale;
+    float scale = a.direct ? 1.f : a.ctrl->scale;
     if (scale == 0.f) scale = 1.f;
-    const long long g = a.ctrl->pushed + trial;
-    const int slot = (int)(g % a.slots);
+    const int slot = a.direct ? bz : (int)((a.ctrl->pushed + trial) % a.slots);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         int b = bin0 + tx * 4 + q;

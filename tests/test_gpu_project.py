@@ -74,3 +74,34 @@ def test_projection_from_device_operator_and_removal():
                      what="after removal")
         with pytest.raises(fc.FcError):
             fc.fc_set_projection(s.handle, np.zeros((N_SRC, 0), np.float32))
+
+
+@pytest.mark.parametrize("mode", [fc.FC_MODE_STREAM, fc.FC_MODE_FULL])
+def test_spectral_projection_in_the_frequency_domain(mode):
+    """A session whose metrics are all spectral projects the band spectra of the sensor
+    trials (the operator acts on the node axis, the taper and the DFT on the sample axis, so
+    they commute): its networks equal the FP64 oracle pipeline (projection in the time
+    domain, then spectra) and those of a session that also holds COR (time-domain path)."""
+    M = _operator(3)
+    x = white_trials(34, W + 4, N_CH, N)
+    spec = fc.FC_SPECTRAL_METRICS
+    nets, X = {}, None
+    for mask in (spec, spec | fc.FC_COR):
+        with fc.Session(N_SRC, N, FS, BAND, "hann", mask, W, mode=mode) as s:
+            fc.fc_set_projection(s.handle, M)
+            s.push(x[:W])
+            for t in range(W, W + 4):
+                s.push(x[t])
+            nets[mask] = {m: s.network(m, packed=True)[0] for m in
+                          ("COH", "IMAGCOHY", "PLV", "PLI", "USPLI", "WPLI", "DSWPLI")}
+            if mask == spec:
+                X = window_spectra(s, W)
+    iu = np.triu_indices(N_SRC, 1)
+    ref = O.networks_dense(O.project(M, x[4:]), FS, BAND[2], BAND[0], BAND[1],
+                           metrics=("COH", "IMAGCOHY", "PLV", "WPLI"))
+    ref_gpu = oracle_spectral(X.astype(np.complex128))
+    for m in ("COH", "IMAGCOHY", "PLV", "WPLI"):
+        assert_close(nets[spec][m], ref[m][iu], what=f"frequency-domain projection {m}")
+        assert_close(nets[spec][m], nets[spec | fc.FC_COR][m], what=f"frequency vs time domain {m}")
+    for m in ("PLI", "USPLI", "DSWPLI"):
+        assert_close(nets[spec][m], ref_gpu[m], what=f"frequency-domain projection {m} (GPU spectra)")

@@ -776,7 +776,8 @@ def run_ours(args, w, wname):
         mixed_stream = {"value": world * units / (sms_ / 1000.0), "unit": UNIT, "ms_per_step": sms_,
                         "latency_ms": {"p50": sl[len(sl) // 2], "p99": sl[-1]}, "steps": sst,
                         "path": "exact streaming update (FP32 terms, double-float sums); drift re-sum slice: "
-                                "tcgen05 BF16 linear sums over the operand ring + exact CUDA-core non-linear sums",
+                                "tcgen05 BF16 linear sums over the operand ring + CUDA-core non-linear sums (exact "
+                                "signs; FP32 partial sums of <= 36 trials into double words)",
                         "kernels_ms_per_push": {k: round(v, 4) for k, v in kms.items()},
                         "tensor_core_share_of_push": kms.get("herk_tc", 0.0) / sms_,
                         "resum_slice_ms_per_push": kms.get("herk_tc", 0.0) + kms.get("window", 0.0)}

@@ -408,7 +408,7 @@ void herk_res_groups(int nseg, int seg_max, int nsel, int sms, long long P, int 
 fc_status stage_window(fc_session* s, int count, bool write_acc) {
     NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, 1, s->ctrl, count};
     const bool mixed_full = s->ops && !s->mixed_stream && !write_acc;
-    if (mixed_full) na.tiny = s->tiny_flags;  // read by the non-linear sums
+    if (mixed_full || s->mixed_stream) na.tiny = s->tiny_flags;  // read by the non-linear sums
     LAUNCH(FC_K_NODE, launch_node(na, s->stream));
     if (mixed_full) {
         // mixed precision: linear sums (COH, IMAGCOHY, PLV) on the tensor cores, the
@@ -540,13 +540,19 @@ fc_status stage_resum_slice_mixed(fc_session* s, long long r, long long R) {
     ha.acc_out = s->acc;
     ha.nt32 = s->nt;
     LAUNCH(FC_K_HERK_TC, launch_herk_tc(ha, s->stream));
+    // the non-linear sums of the same 32-node tile pairs, every bin (accumulators, not the band)
     PairArgs pa = pair_args(s, false, 1);
     pa.tp_list = s->list32;
     pa.tp0 = s->list32_off[p0];
     pa.tp_count = s->list32_off[p1] - s->list32_off[p0];
-    pa.groups = s->B;
-    pa.group_bins = 1;
-    LAUNCH(FC_K_WINDOW, launch_window_nonlinear_acc(pa, s->stream));
+    pa.tiny = s->tiny_flags;
+    pa.fsel0 = 0;
+    pa.fsel1 = s->B;
+    // bins per CTA: as many as keep about eight waves of resident CTAs
+    const long long waves = 8LL * s->num_sms * nonlinear_ctas_per_sm();
+    pa.group_bins = (int)std::max(1LL, std::min<long long>(s->B, (long long)pa.tp_count * s->B / std::max(1LL, waves)));
+    pa.groups = (s->B + pa.group_bins - 1) / pa.group_bins;
+    LAUNCH(FC_K_WINDOW, launch_nonlinear_acc(pa, s->stream));
     return FC_OK;
 }
 
@@ -578,6 +584,7 @@ fc_status push_one_stream(fc_session* s, const float* x, bool finalize) {
         st = stage_spectra(s, x, 1, 0);
         if (st != FC_OK) return st;
         NodeArgs na{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, push_node_mode(s), s->ctrl, 1};
+        if (s->mixed_stream) na.tiny = s->tiny_flags;
         LAUNCH(FC_K_NODE, launch_node(na, s->stream));
         PairArgs pa = pair_args(s, true, 1);
         pa.finalize = (finalize && (s->mask & FC_SPECTRAL_METRICS)) ? 1 : 0;
@@ -745,6 +752,7 @@ fc_status fc_push_batch_pre(fc_session* const* ss, const float* const* x, int co
         fc_session* s = ss[i];
         b.sp[i] = spectrum_args(s, x[i], 1, 0);
         b.nd[i] = NodeArgs{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, push_node_mode(s), s->ctrl, 1};
+        if (s->mixed_stream) b.nd[i].tiny = s->tiny_flags;
         b.val_prefix[i + 1] = b.val_prefix[i] + (long long)s->n * s->N;
         b.spec_prefix[i + 1] = b.spec_prefix[i] + ((s->n + 31) / 32) * ((s->B + 31) / 32);
         b.node_prefix[i + 1] = b.node_prefix[i] + s->B * s->n;
@@ -788,11 +796,11 @@ size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode 
         b += (size_t)N * B * 8 + slots * B * n * 8 + (size_t)B * n * 12 + ntp * 4;
         if (mode == FC_MODE_STREAM) b += ntp * B * FC_BLOCK_WORDS * 4;
         if (mode == FC_MODE_STREAM && prec != FC_PREC_FP32) {
-            // operand ring, 128-node tile lists and the 32-in-128 tile-pair list
+            // operand ring, 128-node tile lists, the 32-in-128 tile-pair list, tiny-node flags
             const size_t nt128 = (n + 127) / 128, ntp128 = nt128 * (nt128 + 1) / 2;
             const size_t per_chunk = prec == FC_PREC_TF32 ? 32 : 64;
             const size_t nchunks = (2 * slots + per_chunk - 1) / per_chunk;
-            b += nt128 * B * 4 * nchunks * herk_chunk_bytes() + ntp128 * 4 + ntp * 4;
+            b += nt128 * B * 4 * nchunks * herk_chunk_bytes() + ntp128 * 4 + ntp * 4 + (size_t)B * n;
         }
         int wg, wgb;
         const int sms = fc_device_sms();
@@ -997,6 +1005,7 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
             TRY(alloc_zero(s, l32.size(), &s->list32));
             TRY(upload(s, s->list32, l32.data(), l32.size() * sizeof(int)));
             TRY(alloc_zero(s, (size_t)s->nt128 * B * 4 * s->nchunks * herk_chunk_bytes(), &s->ops));
+            TRY(alloc_zero(s, (size_t)B * n_nodes, &s->tiny_flags));
         }
         if (cfg.precision != FC_PREC_FP32 && cfg.mode == FC_MODE_FULL) {
             s->ab_format = cfg.precision == FC_PREC_BF16 ? 1 : (cfg.precision == FC_PREC_FP16 ? 0 : 2);

@@ -192,7 +192,8 @@ struct NodeArgs {
     int mode;   // 0 = add newest / subtract leaving, 1 = recompute from the window
     FcCtrl* ctrl;
     int count;  // trials pushed by this call (mode 1: the window ends at pushed + count)
-    unsigned char* tiny;  // mode 1, optional: [B][n] 1 where a trial of the window has a tiny component
+    unsigned char* tiny;  // optional [B][n] tiny-component flags: mode 1 sets them for the window's
+                          // trials, mode 0 adds the new trial's (flags of leaving trials stay set)
 };
 cudaError_t launch_node(const NodeArgs& a, cudaStream_t st);
 
@@ -218,11 +219,12 @@ struct PairArgs {
     int grid_ctas;     // persistent grid size of the streaming kernel
     const FcCtrl* ctrl;
     const unsigned char* tiny;  // non-linear sums: [B][n] tiny-component flags of the window (k_node)
-    const int* tp_list;         // window kernel, optional: tile pairs tp_list[tp0 ..] instead of tp0 ..
+    const int* tp_list;         // non-linear re-sum: tile pairs tp_list[tp0 .. tp0 + tp_count - 1]
 };
-// The window kernel's non-linear fields only (sum Im, sum |Im|, sum Im^2, sign count) into the
-// accumulators; the linear fields are left as they are.
-cudaError_t launch_window_nonlinear_acc(const PairArgs& a, cudaStream_t st);
+// The non-linear sums kernel storing its window sums (sum Im, sum |Im|, sum Im^2, sign count)
+// into the accumulators of tile pairs tp_list[tp0 .. tp0 + tp_count - 1] (the linear fields
+// are left as they are): the re-sum of a mixed-precision streaming session.
+cudaError_t launch_nonlinear_acc(const PairArgs& a, cudaStream_t st);
 cudaError_t launch_stream_update(const PairArgs& a, cudaStream_t st);
 
 // A batch of sessions updated by one launch of the streaming kernel (passed by value as

@@ -16,6 +16,12 @@
 // both differences are exactly 0 (sum_{k != l} of products), and DSWPLI is 0, as the
 // definition's zero denominator gives; the counts decide this exactly.
 //
+// Accumulator mode (ACC): the window sums of each bin are stored into the streaming
+// accumulators (sum Im, sum |Im|, sum Im^2 as double words, the sign count) of the tile pairs
+// of a list; this is the drift re-sum of a mixed-precision streaming session, whose linear
+// sums come from the tensor cores. Its sums carry the chunked FP32 rounding (NK terms per
+// partial sum), well inside the operand rounding of those linear sums.
+//
 // Work split: a CTA of 128 threads takes one 32 x 32 tile pair and a group of bins; each
 // thread holds a 2 x 4 register tile of pairs (rows 2 rg, 2 rg + 1; columns 4 cg .. 4 cg + 3),
 // so every staged spectrum value feeds 4 or 2 pairs per load. Row spectra are staged as
@@ -65,6 +71,7 @@ struct NlSmem {
     float band[4][FC_T][FC_T];  // band sums of PLI, USPLI, WPLI, DSWPLI per pair
 };
 
+template <bool ACC>
 __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
@@ -78,7 +85,7 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
 
     // bin group g: selected bins fsel0 + g group_bins .. (bins outside the selected band take
     // no part in the average and are not computed)
-    const int tp = blockIdx.x, g = blockIdx.y;
+    const int tp = ACC ? a.tp_list[a.tp0 + blockIdx.x] : blockIdx.x, g = blockIdx.y;
     const int fa = a.fsel0 + g * a.group_bins, fb = min(a.fsel1, fa + a.group_bins);
     const int ta = a.tile_a[tp], tb = a.tile_b[tp];
     const int tid = threadIdx.x, rg = tid >> 3, cg = tid & 7;
@@ -218,6 +225,28 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
                 renorm2(abh[q], abl[q]);
                 renorm2(sqh[q], sql[q]);
             }
+            if constexpr (ACC) {
+                // accumulator block of (tile pair, bin): planes 2k, 2k + 1 = hi, lo of field k
+                // (1 sum Im, 4 sum |Im|, 5 sum Im^2), plane 12 the sign count
+                float* blk = a.acc + ((size_t)tp * a.B + f) * FC_BLOCK_WORDS;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int w0 = (li0 + r) * FC_T + lj0, q0 = 2 * r, q1 = 2 * r + 1;
+                    auto put = [&](int k, const float2* h, const float2* l) {
+                        __stcs(reinterpret_cast<float4*>(blk + (2 * k) * FC_TT + w0),
+                               make_float4(h[q0].x, h[q0].y, h[q1].x, h[q1].y));
+                        __stcs(reinterpret_cast<float4*>(blk + (2 * k + 1) * FC_TT + w0),
+                               make_float4(l[q0].x, l[q0].y, l[q1].x, l[q1].y));
+                    };
+                    put(1, imh, iml);
+                    put(4, abh, abl);
+                    put(5, sqh, sql);
+                    __stcs(reinterpret_cast<int4*>(blk + 12 * FC_TT + w0),
+                           make_int4((int)pos[q0].x - (int)neg[q0].x, (int)pos[q0].y - (int)neg[q0].y,
+                                     (int)pos[q1].x - (int)neg[q1].x, (int)pos[q1].y - (int)neg[q1].y));
+                }
+                continue;
+            }
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 float4 acc[4];
@@ -262,7 +291,7 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
             }
         }
     }
-    if (!vmask) return;
+    if (ACC || !vmask) return;
     const float invB = 1.0f / (float)(a.fsel1 - a.fsel0);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -286,10 +315,23 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
 
 cudaError_t launch_nonlinear_sums(const PairArgs& a, cudaStream_t st) {
     const int smem = (int)sizeof(NlSmem);
-    cudaError_t e = cudaFuncSetAttribute(k_nonlin, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_nonlin<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     dim3 grid(a.ntp, a.groups);
-    k_nonlin<<<grid, NL_THREADS, smem, st>>>(a);
+    k_nonlin<false><<<grid, NL_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nonlinear_acc(const PairArgs& a, cudaStream_t st) {
+    if (a.tp_count <= 0) return cudaSuccess;
+    PairArgs b = a;
+    b.finalize = 0;
+    b.write_acc = 1;
+    const int smem = (int)sizeof(NlSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_nonlin<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(b.tp_count, b.groups);
+    k_nonlin<true><<<grid, NL_THREADS, smem, st>>>(b);
     return cudaGetLastError();
 }
 

@@ -31,6 +31,8 @@ __device__ __forceinline__ void node_elem(const NodeArgs& a, int e) {
         const long long t = c->pushed;  // the new trial
         const float2 Xn = a.ring[((size_t)(t % a.slots) * a.B + f) * a.n + i];
         s = a.psd[e] + ((double)Xn.x * Xn.x + (double)Xn.y * Xn.y);
+        // flags kept across pushes: a superset of the window's tiny nodes until mode 1 renews them
+        if (a.tiny && node_tiny(Xn)) a.tiny[e] = 1;
         if (a.W > 0 && t >= a.W) {
             const float2 Xo = a.ring[((size_t)((t - a.W) % a.slots) * a.B + f) * a.n + i];
             s -= ((double)Xo.x * Xo.x + (double)Xo.y * Xo.y);
@@ -105,10 +107,6 @@ __device__ __forceinline__ float win_lt0(float x) {
 // keeps the error of a sum of K terms within about (WK + 1) K u^2 of their summed
 // magnitudes. Sign counts: exact FP32 tallies of positive and negative terms. The next
 // chunk's spectra are copied by cp.async while the current chunk is summed.
-// LIN = false: only the non-linear fields (sum Im, sum |Im|, sum Im^2, sign count) are summed
-// and stored (accumulator writes only; the re-sum of a mixed-precision streaming session,
-// whose linear sums come from the tensor cores).
-template <bool LIN>
 __global__ void __launch_bounds__(WIN_THREADS, 2) k_window(PairArgs a, int bins_metric, float* bins_out) {
     const FcCtrl* c = a.ctrl;
     if (c->bad) return;
@@ -121,8 +119,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window(PairArgs a, int bins_
     WinBand& sb = *reinterpret_cast<WinBand*>(win_smem_raw + sizeof(WinSmem));
     const bool band_out = a.finalize && !bins_out;
 
-    // (tile-pair lists are used by the non-linear re-sum only)
-    const int tp = (!LIN && a.tp_list) ? a.tp_list[a.tp0 + blockIdx.x] : a.tp0 + blockIdx.x;
+    const int tp = a.tp0 + blockIdx.x;
     const int g = blockIdx.y;
     const int f0 = g * a.group_bins;
     const int f1 = min(a.B, f0 + a.group_bins);
@@ -189,19 +186,17 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window(PairArgs a, int bins_
                 float2 X = make_float2(0.f, 0.f);
                 if (kk < kn && node_ok) X = sm.raw[kk][l_node];
                 if (sc != 0.f) X = make_float2(__fmul_rn(X.x, sc), __fmul_rn(X.y, sc));
-                const float2 u = LIN ? phasor_of(X) : make_float2(0.f, 0.f);
+                const float2 u = phasor_of(X);
                 if (l_node < FC_T) {
                     sm.row[kk][l_node][0] = make_float4(X.x, X.x, X.y, X.y);
                     sm.row[kk][l_node][1] = make_float4(-X.x, -X.x, u.x, u.x);
-                    if (LIN) sm.row[kk][l_node][2] = make_float4(u.y, u.y, -u.x, -u.x);
+                    sm.row[kk][l_node][2] = make_float4(u.y, u.y, -u.x, -u.x);
                 } else {
                     const int l = l_node - FC_T;
                     reinterpret_cast<float*>(sm.ca[kk])[l] = X.x;
                     reinterpret_cast<float*>(sm.cb[kk])[l] = X.y;
-                    if (LIN) {
-                        reinterpret_cast<float*>(sm.cua[kk])[l] = u.x;
-                        reinterpret_cast<float*>(sm.cub[kk])[l] = u.y;
-                    }
+                    reinterpret_cast<float*>(sm.cua[kk])[l] = u.x;
+                    reinterpret_cast<float*>(sm.cub[kk])[l] = u.y;
                 }
                 const bool tn = node_tiny(X);
                 sm.tiny[kk][l_node] = tn ? 1 : 0;
@@ -219,9 +214,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window(PairArgs a, int bins_
                 constexpr bool TINY = decltype(tiny_c)::value;
 #pragma unroll 2
                 for (int kk = 0; kk < kn; ++kk) {
-                    const float4 r0 = sm.row[kk][li][0], r1 = sm.row[kk][li][1];
-                    float4 r2 = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if constexpr (LIN) r2 = sm.row[kk][li][2];
+                    const float4 r0 = sm.row[kk][li][0], r1 = sm.row[kk][li][1], r2 = sm.row[kk][li][2];
                     RowConst rc;
                     rc.a = make_float2(r0.x, r0.y);
                     rc.b = make_float2(r0.z, r0.w);
@@ -232,12 +225,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window(PairArgs a, int bins_
                     rc.as = r0.x;
                     rc.bs = r0.z;
                     rc.tiny = TINY && sm.tiny[kk][li] != 0;
-                    const float4 xa = sm.ca[kk][cg], xb = sm.cb[kk][cg];
-                    float4 xua = xa, xub = xb;
-                    if constexpr (LIN) {
-                        xua = sm.cua[kk][cg];
-                        xub = sm.cub[kk][cg];
-                    }
+                    const float4 xa = sm.ca[kk][cg], xb = sm.cb[kk][cg], xua = sm.cua[kk][cg], xub = sm.cub[kk][cg];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const float2 aj = h ? make_float2(xa.z, xa.w) : make_float2(xa.x, xa.y);
@@ -245,39 +233,12 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window(PairArgs a, int bins_
                         const float2 uaj = h ? make_float2(xua.z, xua.w) : make_float2(xua.x, xua.y);
                         const float2 ubj = h ? make_float2(xub.z, xub.w) : make_float2(xub.x, xub.y);
                         const int j = FC_T + lj0 + 2 * h;
-                        auto terms = [&]() {
-                            if constexpr (LIN) {
-                                return pair_terms2<TINY>(rc, aj, bj, uaj, ubj, TINY && sm.tiny[kk][j] != 0,
-                                                         TINY && sm.tiny[kk][j + 1] != 0);
-                            } else {
-                                // Im and its sign exactly as pair_terms2 computes them
-                                PairTerms2 t;
-                                t.im = kahan_im2(rc.b, rc.a, rc.na, aj, bj);
-                                t.s0 = sign_of(t.im.x);
-                                t.s1 = sign_of(t.im.y);
-                                if (TINY && (rc.tiny || sm.tiny[kk][j] != 0)) {
-                                    const ImSign v = im_sign_fp64_call(rc.as, rc.bs, aj.x, bj.x);
-                                    t.im.x = v.im;
-                                    t.s0 = v.s;
-                                }
-                                if (TINY && (rc.tiny || sm.tiny[kk][j + 1] != 0)) {
-                                    const ImSign v = im_sign_fp64_call(rc.as, rc.bs, aj.y, bj.y);
-                                    t.im.y = v.im;
-                                    t.s1 = v.s;
-                                }
-                                t.re = t.ure = t.uim = make_float2(0.f, 0.f);
-                                return t;
-                            }
-                        };
-                        const PairTerms2 t = terms();
-                        if constexpr (LIN) {
-                            acc2_f_lazy(vh[h][0], vl[h][0], t.re);
-                            acc2_f_lazy(vh[h][1], vl[h][1], t.im);
-                            acc2_f_lazy(vh[h][2], vl[h][2], t.ure);
-                            acc2_f_lazy(vh[h][3], vl[h][3], t.uim);
-                        } else {
-                            acc2_f_lazy(vh[h][1], vl[h][1], t.im);
-                        }
+                        const PairTerms2 t = pair_terms2<TINY>(rc, aj, bj, uaj, ubj, TINY && sm.tiny[kk][j] != 0,
+                                                               TINY && sm.tiny[kk][j + 1] != 0);
+                        acc2_f_lazy(vh[h][0], vl[h][0], t.re);
+                        acc2_f_lazy(vh[h][1], vl[h][1], t.im);
+                        acc2_f_lazy(vh[h][2], vl[h][2], t.ure);
+                        acc2_f_lazy(vh[h][3], vl[h][3], t.uim);
                         acc2_f_lazy(vh[h][4], vl[h][4], make_float2(fabsf(t.im.x), fabsf(t.im.y)));
                         // im^2 as an exact two-product, scalar: the product feeds additions
                         float2 p2, e2;
@@ -320,7 +281,6 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window(PairArgs a, int bins_
                 const int w0 = li * FC_T + lj0;
 #pragma unroll
                 for (int k = 0; k < FC_NFIELD; ++k) {
-                    if (!LIN && (k == 0 || k == 2 || k == 3)) continue;  // linear fields: the tensor cores' part
                     float4 hq = make_float4(v[0][k].hi, v[1][k].hi, v[2][k].hi, v[3][k].hi);
                     float4 lq = make_float4(v[0][k].lo, v[1][k].lo, v[2][k].lo, v[3][k].lo);
                     __stcs(reinterpret_cast<float4*>(blk + (2 * k) * FC_TT + w0), hq);
@@ -328,7 +288,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window(PairArgs a, int bins_
                 }
                 __stcs(reinterpret_cast<int4*>(blk + 12 * FC_TT + w0), make_int4(sgn[0], sgn[1], sgn[2], sgn[3]));
             }
-            if (LIN && (a.finalize || bins_out)) {
+            if (a.finalize || bins_out) {
                 const float inv_i = sm.sinv[par][0][li];
                 const bool in_band = band_out && f >= a.fsel0 && f < a.fsel1;
 #pragma unroll
@@ -454,24 +414,10 @@ cudaError_t launch_node_batch(const PreBatch& b, cudaStream_t st) {
 
 static cudaError_t launch_window_kernel(const PairArgs& a, dim3 grid, int metric_index, float* out, cudaStream_t st) {
     const size_t smem = window_smem_bytes(a.finalize && !out);
-    cudaError_t e = cudaFuncSetAttribute(k_window<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_window, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)window_smem_bytes(true));
     if (e != cudaSuccess) return e;
-    k_window<true><<<grid, WIN_THREADS, smem, st>>>(a, metric_index, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_window_nonlinear_acc(const PairArgs& a, cudaStream_t st) {
-    PairArgs b = a;
-    b.finalize = 0;
-    b.write_acc = 1;
-    const int count = b.tp_count;
-    if (count <= 0) return cudaSuccess;
-    dim3 grid(count, b.groups);
-    const size_t smem = window_smem_bytes(false);
-    cudaError_t e = cudaFuncSetAttribute(k_window<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_window<false><<<grid, WIN_THREADS, smem, st>>>(b, 0, nullptr);
+    k_window<<<grid, WIN_THREADS, smem, st>>>(a, metric_index, out);
     return cudaGetLastError();
 }
 

@@ -4,9 +4,10 @@ A stream-mode session with a tensor-core precision keeps the exact add/subtract 
 every accumulator (FP32 terms, double-float sums); its drift re-sum, one slice of 128-node
 tile pairs per push, takes the linear sums (CSD real part, phasor sums) from tcgen05
 products over an operand ring of the window and the non-linear sums (sum Im, sum |Im|,
-sum Im^2, sign counts) from the exact window kernel. After a slice, COH and PLV carry the
-operand rounding of the tensor cores; IMAGCOHY (from sum Im), PLI, USPLI, WPLI and DSWPLI
-stay exact-term sums. Against the oracle on the window's GPU spectra (Supplementary
+sum Im^2, sign counts) from the non-linear sums kernel of the full-window mixed path (FP32
+partial sums of at most 36 trials added into double words; exact signs). After a slice, COH
+and PLV carry the operand rounding of the tensor cores; IMAGCOHY (from sum Im), PLI, USPLI,
+WPLI and DSWPLI are sums of the exact FP32 terms. Against the oracle on the window's GPU spectra (Supplementary
 Information 1): COH and PLV within 5e-3 absolute, the other metrics within 1e-5 with exact
 sign sums, through bulk fills, single pushes and more than two re-sum periods; served
 sessions give the same networks alone and in the mix.
@@ -15,6 +16,7 @@ sessions give the same networks alone and in the mix.
 import numpy as np
 import pytest
 
+import oracle as O
 from synth import white_trials
 from _fc_helpers import assert_close, oracle_spectral, window_spectra
 
@@ -145,3 +147,36 @@ def test_served_mixed_precision_sessions():
             for m in SPECTRAL:  # the standalone session runs the same kernels in the same order
                 assert np.array_equal(s.network(m, packed=True)[0], mixed[k][m], equal_nan=True), (k, m)
         _check(mixed[k], X, W, B, f"served cfg {k}")
+
+
+def test_mixed_stream_tiny_nodes_exact_signs():
+    """Sign sums of the re-sum where Im(X_i X_j*) sits at the rounding level and some nodes
+    have spectral components below 2^-50 (there an FMA residual of the exact determinant
+    can round, and the FP64 evaluation takes over): nodes 16-31 are real multiples of nodes
+    0-15, nodes 32-47 copies of 16-31 scaled by 2^-60 in trials 3, 9 and 10 only, so a node's
+    tiny flag comes from a single push. The sign accumulators equal the FP64 signs of the
+    window's GPU spectra (exact arithmetic on the same FP32 values) through three re-sum
+    periods, with and without a tiny trial in the window."""
+    n, N, W, T = 64, 200, 5, 16
+    x = white_trials(73, T, n, N)
+    rng = np.random.default_rng(9)
+    c = rng.uniform(0.3, 3.0, 16) * rng.choice([-1.0, 1.0], 16)
+    x[:, 16:32] = (x[:, :16].astype(np.float64) * c[None, :, None]).astype(np.float32)
+    x[:, 32:48] = x[:, 16:32]
+    for t in (3, 9, 10):
+        x[t, 32:48] *= np.float32(2.0 ** -60)
+    iu = np.triu_indices(n, 1)
+    with fc.Session(n, N, 200.0, (1.0, 60.0, 256), "hann", fc.FC_SPECTRAL_METRICS, W,
+                    mode=fc.FC_MODE_STREAM, precision=fc.FC_PREC_BF16) as s:
+        checked = 0
+        for t in range(T):
+            s.push(x[t])
+            if t in (W - 1, 9, 11, 14, T - 1):
+                X = window_spectra(s, W)
+                sums = O.pair_sums_pairs(X, *iu)
+                sg = s.accumulators("sign").reshape(s.B, -1)
+                assert np.array_equal(sg.astype(np.int64), sums["sign"].T), t
+                checked += 1
+        tiny = np.abs(X[:, 32:48]).max()
+        assert checked == 5 and np.any(sums["sign"] != 0)
+    assert tiny > 0

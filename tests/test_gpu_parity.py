@@ -314,7 +314,7 @@ def test_zero_and_identical_channels():
         _check_against_gpu_spectra(s, 5)
 
 
-@pytest.mark.parametrize("mode,prec", [("stream", "fp32"), ("full", "fp32"), ("full", "bf16")])
+@pytest.mark.parametrize("mode,prec", [("stream", "fp32"), ("stream", "bf16"), ("full", "fp32"), ("full", "bf16")])
 def test_sign_exact_where_im_is_within_rounding_of_zero(mode, prec):
     """Channels that are real multiples of others: Im(X_i X_j*) of their FP32 spectra is a
     few ulps from zero (or exactly zero) with either sign, the hardest input for the exact

@@ -491,6 +491,8 @@ def run_project_case(args):
 
 def run_case(args):
     """One small named case (the profiler captures' workloads); prints its timing per push."""
+    if args.case == "spectrum_methods":
+        return run_spectrum_case(args)
     if args.case == "project_5124":
         return run_project_case(args)
     import torch
@@ -521,6 +523,53 @@ def run_case(args):
         kt = fc.fc_kernel_times(s.handle, reset=True)
     print(json.dumps({"case": args.case, "description": c["desc"], "ms_per_push": dt if c["pushes"] else None,
                       "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in kt.items() if v[0]}}))
+    return 0
+
+
+def run_spectrum_case(args):
+    """Band spectra by the band DFT and by the real FFT (Methods 2.4: per-trial spectra),
+    device time of the spectrum kernel per trial, for sensor-, source- and wide-band shapes
+    (bulk pushes of 8 white-noise trials into full-window sessions, three pushes per method)."""
+    import torch
+    from paper_2303_03279_gb300 import fc
+    from synth import white_trials
+
+    fc.load()
+    shapes = [  # n, N, fs, (f_lo, f_hi, nfft)
+        (60, 500, 1000.0, (1.0, 50.0, 512)),
+        (60, 600, 600.0, (8.0, 12.0, 600)),
+        (5124, 500, 1000.0, (4.0, 44.0, 1000)),
+        (306, 1000, 1000.0, (1.0, 100.0, 1024)),
+        (5124, 500, 1000.0, (4.0, 44.0, 512)),
+        (5124, 1000, 1000.0, (1.0, 100.0, 1024)),
+        (2000, 1000, 1000.0, (0.0, 501.0, 1024)),
+        (1000, 4000, 1000.0, (1.0, 100.0, 4096)),
+    ]
+    K, reps = 8, 3
+    rows = []
+    for n, N, fs, band in shapes:
+        x = torch.from_numpy(white_trials(n + N, K, n, N)).cuda()
+        row = {"n": n, "N": N, "nfft": band[2], "band_hz": [band[0], band[1]]}
+        for name, sp in (("dft", fc.FC_SPECTRUM_DFT), ("fft", fc.FC_SPECTRUM_FFT), ("auto", fc.FC_SPECTRUM_AUTO)):
+            with fc.Session(n, N, fs, band, "hann", fc.FC_COH, K, mode=fc.FC_MODE_FULL, spectrum=sp) as s:
+                row["bins"] = s.B
+                fc.fc_push_trials(s.handle, x, K)
+                fc.fc_sync(s.handle)
+                fc.fc_set_profiling(s.handle, True)
+                fc.fc_kernel_times(s.handle, reset=True)
+                for _ in range(reps):
+                    fc.fc_push_trials(s.handle, x, K)
+                fc.fc_sync(s.handle)
+                kt = fc.fc_kernel_times(s.handle, reset=True)
+                if name == "auto":
+                    row["auto_picks"] = "fft" if s.info().spectrum == fc.FC_SPECTRUM_FFT else "dft"
+                else:
+                    row[f"{name}_us_per_trial"] = round(kt["spectrum"][1] * 1000.0 / (reps * K), 3)
+        rows.append(row)
+        del x
+        torch.cuda.empty_cache()
+    print(json.dumps({"case": "spectrum_methods", "description": run_spectrum_case.__doc__.split("\n\n")[0]
+                      .replace("\n    ", " "), "rows": rows}))
     return 0
 
 
@@ -880,7 +929,7 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="skip the EEG, MEG and source-space legs")
     ap.add_argument("--no-cpu-all-core", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="print the paper-style performance sweep instead")
-    ap.add_argument("--case", choices=sorted(CASES) + ["project_5124"],
+    ap.add_argument("--case", choices=sorted(CASES) + ["project_5124", "spectrum_methods"],
                     help="run one small named case (profiler captures)")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     args = ap.parse_args()

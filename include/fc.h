@@ -102,6 +102,18 @@ typedef enum {
                            spectra (the storage-off comparison of Results 3.1) */
 } fc_mode;
 
+/* How the band spectrum of a trial is computed (Methods 2.4: the per-trial spectrum of each
+ * node); both give the same bins to FP32 rounding. */
+typedef enum {
+    FC_SPECTRUM_AUTO = 0, /* the cheaper of the two for the session's sizes */
+    FC_SPECTRUM_DFT = 1,  /* band DFT: the trial times an [n_samples x n_bins] factor table
+                             (taper folded in, angles reduced exactly in FP64 on the host); any nfft */
+    FC_SPECTRUM_FFT = 2   /* real FFT of the tapered trial zero-padded to nfft (a mixed-radix
+                             complex FFT of nfft/2 points and the even/odd split), then the band
+                             bins selected; nfft even, 16 <= nfft <= 16384, nfft/2 with no prime
+                             factor above 5 (e.g. 512, 600, 1000, 1024) */
+} fc_spectrum;
+
 typedef struct {
     fc_precision precision;
     fc_mode mode;
@@ -114,6 +126,7 @@ typedef struct {
     void* (*dev_alloc)(size_t bytes, void* ctx);
     void (*dev_free)(void* ptr, void* ctx);
     void* alloc_ctx;
+    fc_spectrum spectrum; /* FC_SPECTRUM_AUTO by default */
 } fc_config;
 
 typedef struct {
@@ -127,9 +140,11 @@ typedef struct {
     uint32_t metric_mask;
     fc_mode mode;
     fc_precision precision;
+    fc_spectrum spectrum; /* the method in use (FC_SPECTRUM_DFT or FC_SPECTRUM_FFT) */
 } fc_info;
 
-/* Fill *cfg with the defaults: FP32, stream mode, library stream, resum_period 0, cudaMalloc. */
+/* Fill *cfg with the defaults: FP32, stream mode, library stream, resum_period 0, cudaMalloc,
+ * spectrum method chosen by the library. */
 fc_status fc_config_default(fc_config* cfg);
 
 /* Create a session (Methods 2.4/2.5 settings: nodes, samples, sampling rate, band, taper,
@@ -143,7 +158,8 @@ fc_status fc_config_default(fc_config* cfg);
  *   window: W >= 0 trials (0 = cumulative; FC_MODE_FULL needs W >= 1);
  *   cfg: NULL for defaults. *out receives the handle; on failure *out is NULL and nothing
  *   stays allocated. Errors: FC_ERR_INVALID_ARG, FC_ERR_UNSUPPORTED (XCOR above 8192
- *   samples), FC_ERR_OUT_OF_MEMORY, FC_ERR_CUDA. */
+ *   samples; FC_SPECTRUM_FFT with an nfft it does not take, see fc_spectrum),
+ *   FC_ERR_OUT_OF_MEMORY, FC_ERR_CUDA. */
 fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band, fc_taper taper,
                             uint32_t metric_mask, int window, const fc_config* cfg,
                             fc_session** out);

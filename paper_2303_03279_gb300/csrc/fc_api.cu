@@ -182,6 +182,12 @@ SpectrumArgs spectrum_args(fc_session* s, const float* x, int count, int write_f
     a.count = count;
     a.write_from = write_from;
     a.twiddle = s->twiddle;
+    a.fft = s->use_fft ? 1 : 0;
+    a.nfft = s->nfft;
+    a.first_bin = s->first_bin;
+    a.taper = s->taper_tab;
+    a.fft_tw = s->fft_tw;
+    a.fft_stages = fc_fft_radices(s->nfft / 2, &a.fft_radices);
     a.ring = s->ring;
     a.slots = s->slots;
     a.n = s->n;
@@ -754,7 +760,8 @@ fc_status fc_push_batch_pre(fc_session* const* ss, const float* const* x, int co
         b.nd[i] = NodeArgs{s->ring, s->psd, s->inv_psd, s->slots, s->n, s->B, s->W, push_node_mode(s), s->ctrl, 1};
         if (s->mixed_stream) b.nd[i].tiny = s->tiny_flags;
         b.val_prefix[i + 1] = b.val_prefix[i] + (long long)s->n * s->N;
-        b.spec_prefix[i + 1] = b.spec_prefix[i] + ((s->n + 31) / 32) * ((s->B + 31) / 32);
+        // (sessions on the FFT method are launched on their own: no CTA of the batched kernel)
+        b.spec_prefix[i + 1] = b.spec_prefix[i] + (s->use_fft ? 0 : ((s->n + 31) / 32) * ((s->B + 31) / 32));
         b.node_prefix[i + 1] = b.node_prefix[i] + s->B * s->n;
     }
     fc_session* s = ss[0];  // launches are counted (and timed) on the first session
@@ -787,13 +794,57 @@ fc_status fc_push_batch_post(fc_session* const* ss, FcCtrl* const* snap, int cou
 void fc_count_launch(fc_session* s) { s->launches++; }
 
 // Device bytes fc_session_create would allocate for these settings (mirrors its allocations).
-size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode mode, fc_precision prec) {
+int fc_fft_radices(int m, unsigned long long* packed) {
+    unsigned long long p = 0;
+    int n = 0;
+    auto take = [&](int r) {
+        while (m % r == 0 && n < 16) {
+            p |= (unsigned long long)r << (4 * n++);
+            m /= r;
+        }
+    };
+    take(4);
+    take(2);
+    take(3);
+    take(5);
+    if (packed) *packed = p;
+    return m == 1 ? n : -1;
+}
+
+bool fc_fft_size_ok(int nfft) {
+    return nfft >= 16 && nfft <= 16384 && nfft % 2 == 0 && fc_fft_radices(nfft / 2, nullptr) >= 0;
+}
+
+// Spectrum method. Cost per (trial, node): the band DFT kernel does N x (B rounded up to its
+// 32-bin tiles) complex multiply-adds; the warp FFT does per pass and point about one (radix
+// 2, 4), two (radix 3) or three (radix 5) such operations' worth of work, times kFftCost for
+// its shared-memory round trips.
+bool fc_spectrum_uses_fft(int N, int B, int nfft, fc_spectrum method) {
+    if (method == FC_SPECTRUM_DFT || !fc_fft_size_ok(nfft)) return false;
+    if (method == FC_SPECTRUM_FFT) return true;
+    constexpr double kFftCost = 2.0;
+    unsigned long long p = 0;
+    const int ns = fc_fft_radices(nfft / 2, &p);
+    double per_point = 0.0;
+    for (int i = 0; i < ns; ++i) {
+        const int r = (int)((p >> (4 * i)) & 15u);
+        per_point += r == 5 ? 3.0 : (r == 3 ? 2.0 : 1.0);
+    }
+    const double dft = (double)N * ((B + 31) / 32 * 32);
+    const double fft = kFftCost * (double)nfft * per_point;
+    return fft < dft;
+}
+
+size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode mode, fc_precision prec, int nfft) {
     const size_t nt = (n + FC_T - 1) / FC_T, ntp = nt * (nt + 1) / 2;
     const size_t P = (size_t)n * (n - 1) / 2;
     const size_t slots = mode == FC_MODE_FULL ? W : (W > 0 ? W + 1 : 1);
     size_t b = 256 + 9 * P * 4 + (size_t)n * N * 4;  // control block, network planes, trial staging
     if (mask & FC_SPECTRAL_METRICS) {
-        b += (size_t)N * B * 8 + slots * B * n * 8 + (size_t)B * n * 12 + ntp * 4;
+        // spectrum tables: DFT factors [N][B], or the FFT's taper [N] and twiddles [nfft/2]
+        b += (nfft > 0 && fc_spectrum_uses_fft(N, B, nfft, FC_SPECTRUM_AUTO)) ? (size_t)N * 4 + (size_t)nfft / 2 * 8
+                                                                               : (size_t)N * B * 8;
+        b += slots * B * n * 8 + (size_t)B * n * 12 + ntp * 4;
         if (mode == FC_MODE_STREAM) b += ntp * B * FC_BLOCK_WORDS * 4;
         if (mode == FC_MODE_STREAM && prec != FC_PREC_FP32) {
             // operand ring, 128-node tile lists, the 32-in-128 tile-pair list, tiny-node flags
@@ -865,6 +916,11 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
     if (cfg.mode != FC_MODE_STREAM && cfg.mode != FC_MODE_FULL) return fail(FC_ERR_INVALID_ARG, "bad mode");
     if (cfg.mode == FC_MODE_FULL && window < 1) return fail(FC_ERR_INVALID_ARG, "full mode needs window >= 1");
     if (cfg.precision < FC_PREC_FP32 || cfg.precision > FC_PREC_FP16) return fail(FC_ERR_INVALID_ARG, "bad precision");
+    if (cfg.spectrum < FC_SPECTRUM_AUTO || cfg.spectrum > FC_SPECTRUM_FFT) return fail(FC_ERR_INVALID_ARG, "bad spectrum method");
+    if (cfg.spectrum == FC_SPECTRUM_FFT && !fc_fft_size_ok(band.nfft))
+        return fail(FC_ERR_UNSUPPORTED,
+                    "the FFT spectrum needs an even nfft in 16 .. 16384 whose half has no prime factor above 5 "
+                    "(nfft %d)", band.nfft);
     if (cfg.precision != FC_PREC_FP32 && cfg.mode == FC_MODE_STREAM && (window < 1 || cfg.resum_period < 0))
         return fail(FC_ERR_UNSUPPORTED,
                     "a tensor-core precision in stream mode applies to the drift re-sum of a sliding window "
@@ -908,6 +964,7 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
     s->ntp = s->nt * (s->nt + 1) / 2;
     s->P = (long long)n_nodes * (n_nodes - 1) / 2;
     s->slots = cfg.mode == FC_MODE_FULL ? window : (window > 0 ? window + 1 : 1);
+    s->use_fft = fc_spectrum_uses_fft(n_samples, B, band.nfft, cfg.spectrum);
     cudaGetDevice(&s->device);
     s->num_sms = fc_device_sms(s->device);
 
@@ -940,13 +997,30 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
     TRY(alloc_zero(s, 1, &s->ctrl));
     // spectral state only when the session has spectral metrics (a COR / XCOR session holds none)
     if (s->spectral) {
-        // taper-folded DFT factors, FP64 on the host with exact angle reduction
-        {
+        auto taper_at = [&](int t) {
+            double w = 1.0;
+            if (taper == FC_TAPER_HANN) w = 0.5 - 0.5 * std::cos(2.0 * kPi * t / n_samples);
+            if (taper == FC_TAPER_HANN_SYM) w = n_samples > 1 ? 0.5 - 0.5 * std::cos(2.0 * kPi * t / (n_samples - 1)) : 1.0;
+            return w;
+        };
+        if (s->use_fft) {
+            // real FFT: the taper and the twiddles e^{-2 pi i k / nfft}, FP64 on the host
+            std::vector<float> wt(n_samples);
+            for (int t = 0; t < n_samples; ++t) wt[t] = (float)taper_at(t);
+            std::vector<float2> ft(band.nfft / 2);
+            for (int k = 0; k < band.nfft / 2; ++k) {
+                const double ang = 2.0 * kPi * (double)k / band.nfft;
+                ft[k] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
+            }
+            TRY(alloc_zero(s, wt.size(), &s->taper_tab));
+            TRY(alloc_zero(s, ft.size(), &s->fft_tw));
+            TRY(upload(s, s->taper_tab, wt.data(), wt.size() * sizeof(float)));
+            TRY(upload(s, s->fft_tw, ft.data(), ft.size() * sizeof(float2)));
+        } else {
+            // taper-folded DFT factors, FP64 on the host with exact angle reduction
             std::vector<float2> tw((size_t)n_samples * B);
             for (int t = 0; t < n_samples; ++t) {
-                double w = 1.0;
-                if (taper == FC_TAPER_HANN) w = 0.5 - 0.5 * std::cos(2.0 * kPi * t / n_samples);
-                if (taper == FC_TAPER_HANN_SYM) w = n_samples > 1 ? 0.5 - 0.5 * std::cos(2.0 * kPi * t / (n_samples - 1)) : 1.0;
+                const double w = taper_at(t);
                 for (int b = 0; b < B; ++b) {
                     const long long m = ((long long)(first + b) * t) % band.nfft;
                     const double ang = 2.0 * kPi * (double)m / band.nfft;
@@ -1596,6 +1670,7 @@ fc_status fc_session_info(fc_session* s, fc_info* info) {
     info->metric_mask = s->mask;
     info->mode = s->cfg.mode;
     info->precision = s->cfg.precision;
+    info->spectrum = s->use_fft ? FC_SPECTRUM_FFT : FC_SPECTRUM_DFT;
     if (h.bad_latched) return check_latched(s, &h);
     return FC_OK;
 }

@@ -106,7 +106,10 @@ struct fc_session {
     FcCtrl* ctrl;
     float* x_stage;         // [stage_trials][n][N]
     int stage_trials;
-    float2* twiddle;        // [N][B] taper-folded DFT factors
+    float2* twiddle;        // [N][B] taper-folded DFT factors (DFT spectrum method)
+    bool use_fft;           // spectrum by real FFT instead of the band DFT
+    float* taper_tab;       // FFT method: [N] taper
+    float2* fft_tw;         // FFT method: [nfft/2] twiddles e^{-2 pi i k / nfft}
     float2* ring;           // [slots][B][n]
     double* psd;            // [B][n]
     float* inv_psd;         // [B][n]
@@ -179,6 +182,12 @@ struct SpectrumArgs {
     int slots, n, N, B;
     FcCtrl* ctrl;
     int direct;            // 1: trial write_from + t into slot t of `ring`, unscaled (sensor spectra)
+    // real-FFT method (fft = 1): taper [N], twiddles [nfft/2], band bins first_bin .. + B - 1;
+    // the radices of nfft/2, four bits per pass, first pass in the low bits
+    int fft, nfft, first_bin, fft_stages;
+    unsigned long long fft_radices;
+    const float* taper;
+    const float2* fft_tw;
 };
 cudaError_t launch_validate(const float* x, long long count, FcCtrl* ctrl, cudaStream_t st);
 cudaError_t launch_spectrum(const SpectrumArgs& a, cudaStream_t st);
@@ -423,7 +432,14 @@ fc_status fc_push_batch_pre(fc_session* const* ss, const float* const* x, int co
 fc_status fc_push_batch_post(fc_session* const* ss, FcCtrl* const* snap, int count, cudaStream_t st);
 void fc_count_launch(fc_session* s);
 size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode mode,
-                             fc_precision prec = FC_PREC_FP32);
+                             fc_precision prec = FC_PREC_FP32, int nfft = 0);
+// Whether a session with these sizes computes its spectra by real FFT (method as configured;
+// FC_SPECTRUM_AUTO: the cheaper one); 0 for an FFT request the sizes do not allow.
+bool fc_spectrum_uses_fft(int N, int B, int nfft, fc_spectrum method);
+bool fc_fft_size_ok(int nfft);
+// Radices (4 first, then 2, 3, 5) of m = nfft/2, four bits each; returns the pass count, or
+// -1 when m has a prime factor above 5.
+int fc_fft_radices(int m, unsigned long long* packed);
 int fc_band_bins(double fs, fc_band band, int* first);
 
 cudaError_t launch_expand_dense(const float* packed, float* dense, int n, int antisym,

@@ -386,7 +386,8 @@ fc_status fc_server_session_bytes(int n_nodes, int n_samples, double fs, fc_band
     if (!bytes || n_nodes < 2 || n_samples < 1 || window < 1) return sfail(FC_ERR_INVALID_ARG, "bad session settings");
     const int B = fc_band_bins(fs, band, nullptr);
     if (B <= 0) return sfail(FC_ERR_INVALID_ARG, "the band selects no bin");
-    *bytes = fc_plan_session_bytes(n_nodes, n_samples, B, window, metric_mask, plain ? FC_MODE_FULL : FC_MODE_STREAM);
+    *bytes = fc_plan_session_bytes(n_nodes, n_samples, B, window, metric_mask, plain ? FC_MODE_FULL : FC_MODE_STREAM,
+                                    FC_PREC_FP32, band.nfft);
     return FC_OK;
 }
 
@@ -428,7 +429,8 @@ fc_status fc_server_open(fc_server* sv, int n_nodes, int n_samples, double fs, f
     if (st != FC_OK) return st;
     if (!sv->cfg.plain && sv->cfg.precision != FC_PREC_FP32) {  // the operand ring of a mixed-precision session
         const int B = fc_band_bins(fs, band, nullptr);
-        need = fc_plan_session_bytes(n_nodes, n_samples, B, window, metric_mask, FC_MODE_STREAM, sv->cfg.precision);
+        need = fc_plan_session_bytes(n_nodes, n_samples, B, window, metric_mask, FC_MODE_STREAM, sv->cfg.precision,
+                                      band.nfft);
     }
     {
         std::lock_guard<std::mutex> lk(sv->mu);

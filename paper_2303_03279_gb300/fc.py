@@ -37,6 +37,7 @@ FC_TAPER_NONE, FC_TAPER_HANN, FC_TAPER_HANN_SYM = 0, 1, 2
 TAPERS = {"none": 0, "hann": 1, "hann_sym": 2}
 FC_PREC_FP32, FC_PREC_TF32, FC_PREC_BF16, FC_PREC_FP16 = 0, 1, 2, 3
 FC_MODE_STREAM, FC_MODE_FULL = 0, 1
+FC_SPECTRUM_AUTO, FC_SPECTRUM_DFT, FC_SPECTRUM_FFT = 0, 1, 2
 
 FC_K_NAMES = ("spectrum", "calibrate", "node", "stream", "window", "herk_tc", "band_reduce",
               "cor", "xcor", "project", "other")
@@ -55,7 +56,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 class fc_config(C.Structure):
     _fields_ = [("precision", C.c_int), ("mode", C.c_int), ("stream", C.c_void_p),
                 ("resum_period", C.c_int), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
-                ("alloc_ctx", C.c_void_p)]
+                ("alloc_ctx", C.c_void_p), ("spectrum", C.c_int)]
 
 
 class fc_info(C.Structure):
@@ -63,7 +64,7 @@ class fc_info(C.Structure):
                 ("first_bin", C.c_int), ("nfft", C.c_int), ("window", C.c_int), ("k_used", C.c_int),
                 ("pushes", C.c_longlong), ("rejected", C.c_longlong), ("pairs", C.c_longlong),
                 ("device_bytes", C.c_size_t), ("metric_mask", C.c_uint32), ("mode", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("spectrum", C.c_int)]
 
 
 class fc_kernel_time(C.Structure):
@@ -501,11 +502,13 @@ class Session:
     """Owning wrapper: ``Session(n, N, fs, band, taper, mask, window, mode=..., ...)``."""
 
     def __init__(self, n_nodes, n_samples, fs, band, taper="hann", metric_mask=FC_ALL_METRICS,
-                 window=0, mode=FC_MODE_STREAM, precision=FC_PREC_FP32, stream=None, resum_period=0):
+                 window=0, mode=FC_MODE_STREAM, precision=FC_PREC_FP32, stream=None, resum_period=0,
+                 spectrum=FC_SPECTRUM_AUTO):
         cfg = fc_config_default()
         cfg.mode = mode
         cfg.precision = precision
         cfg.resum_period = resum_period
+        cfg.spectrum = spectrum
         if stream is not None:
             cfg.stream = C.c_void_p(int(stream))
         self.n, self.N = int(n_nodes), int(n_samples)

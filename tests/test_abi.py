@@ -73,3 +73,15 @@ def test_argument_errors_are_reported_before_device_use():
     with pytest.raises(fc.FcError) as e:
         fc.fc_session_create(8, 16, 100.0, (1.0, 20.0, 16), "hann", 1 << 12, 4)
     assert e.value.status == fc.FC_ERR_INVALID_ARG
+    # the real-FFT spectrum needs an even nfft in 16 .. 16384 with nfft/2 5-smooth
+    for nfft in (1001, 14, 8, 32768, 2 * 7 * 64):
+        cfg = fc.fc_config_default()
+        cfg.spectrum = fc.FC_SPECTRUM_FFT
+        with pytest.raises(fc.FcError) as e:
+            fc.fc_session_create(8, 4, 1000.0, (1.0, 200.0, nfft), "hann", fc.FC_COH, 4, cfg)
+        assert e.value.status == fc.FC_ERR_UNSUPPORTED, nfft
+    cfg = fc.fc_config_default()
+    cfg.spectrum = 3
+    with pytest.raises(fc.FcError) as e:
+        fc.fc_session_create(8, 16, 100.0, (1.0, 20.0, 16), "hann", fc.FC_COH, 4, cfg)
+    assert e.value.status == fc.FC_ERR_INVALID_ARG

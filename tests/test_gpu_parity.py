@@ -50,15 +50,29 @@ def _sign_sum_from_network(pli_net, K, B):
 # ----------------------------------------------------------------------- spectra
 
 
-@pytest.mark.parametrize("n,N,nfft,band,taper", [
+SPECTRUM_CASES = [
     (70, 500, 512, (1.0, 50.0), "hann"),
     (33, 1000, 1024, (1.0, 100.0), "hann_sym"),
-    (5, 37, 64, (0.0, 501.0), "none"),
-])
-def test_spectrum_kernel_matches_fp64_dft(n, N, nfft, band, taper):
+    (5, 37, 64, (0.0, 501.0), "none"),          # every bin 0 .. nfft/2, N < nfft
+    (40, 2000, 4096, (0.0, 501.0), "hann"),     # wide band: 2049 bins
+    (3, 10000, 16384, (10.0, 60.0), "hann"),    # largest transform (one warp per CTA)
+    (50, 500, 1000, (4.0, 44.0), "hann"),       # nfft/2 = 500: radix 4, 5, 5, 5
+    (20, 600, 600, (8.0, 12.0), "hann_sym"),    # nfft/2 = 300: radix 4, 3, 5, 5
+    (7, 100, 240, (0.0, 501.0), "none"),        # nfft/2 = 120: radix 4, 2, 3, 5; every bin
+]
+
+
+@pytest.mark.parametrize("method", ["dft", "fft"])
+@pytest.mark.parametrize("n,N,nfft,band,taper", SPECTRUM_CASES)
+def test_spectrum_kernel_matches_fp64_dft(n, N, nfft, band, taper, method):
+    """Band spectra of both methods (band DFT against a factor table; mixed-radix real FFT of
+    the zero-padded trial with the even/odd split, including the bins 0 and nfft/2) against
+    the FP64 DFT of the tapered trial, within 1e-5 of sum_t |x(t) w(t)|."""
     fs = 1000.0
     x = white_trials(1, 1, n, N)
-    with _session(n, N, fs, (band[0], band[1], nfft), 1, fc.FC_COH, taper=taper) as s:
+    sp = fc.FC_SPECTRUM_FFT if method == "fft" else fc.FC_SPECTRUM_DFT
+    with _session(n, N, fs, (band[0], band[1], nfft), 1, fc.FC_COH, taper=taper, spectrum=sp) as s:
+        assert s.info().spectrum == sp
         s.push(x[0])
         scale = fc.fc_debug_get_scale(s.handle)
         Xg = s.spectra(0).T.astype(np.complex128) / scale  # [n][B]
@@ -67,6 +81,31 @@ def test_spectrum_kernel_matches_fp64_dft(n, N, nfft, band, taper):
     # FP32 dot product error bound scale: sum_t |x(t) w(t)|
     bound = np.sum(np.abs(x[0].astype(np.float64) * O.taper(N, taper)), axis=1)[:, None]
     assert np.all(np.abs(Xg - Xr) <= 1e-5 * bound), np.max(np.abs(Xg - Xr) / bound)
+
+
+@pytest.mark.parametrize("mode", ["stream", "full"])
+def test_fft_spectra_sessions_against_oracle(mode):
+    """Sessions on the real-FFT method over a wide band (0 - 250 Hz at nfft 512: all 257
+    bins, including DC and the Nyquist bin of fs = 500 Hz): every spectral metric against the
+    oracle on the window's GPU spectra (1e-5, exact sign sums), the spectra themselves
+    against the FP64 DFT, through a bulk fill and single pushes that slide the window."""
+    n, N, W, T = 72, 400, 6, 10
+    fs = 500.0
+    x = white_trials(31, T, n, N)
+    x[:, 3] = 0.8 * x[:, 40] + 0.2 * x[:, 3]
+    md = fc.FC_MODE_STREAM if mode == "stream" else fc.FC_MODE_FULL
+    with _session(n, N, fs, (0.0, 251.0, 512), W, fc.FC_SPECTRAL_METRICS, mode=md,
+                  spectrum=fc.FC_SPECTRUM_FFT) as s:
+        assert s.info().spectrum == fc.FC_SPECTRUM_FFT and s.B == 257
+        s.push(x[:W])
+        for t in range(W, T):
+            s.push(x[t])
+        _check_against_gpu_spectra(s, W)
+        scale = fc.fc_debug_get_scale(s.handle)
+        Xg = s.spectra(0).T.astype(np.complex128) / scale
+    Xr = O.spectra(x[T - 1], O.band_bins(fs, 512, 0.0, 251.0), 512, "hann")
+    bound = np.sum(np.abs(x[T - 1].astype(np.float64) * O.taper(N, "hann")), axis=1)[:, None]
+    assert np.all(np.abs(Xg - Xr) <= 1e-5 * bound)
 
 
 def test_prescale_is_a_power_of_two_and_invariant():

@@ -389,8 +389,9 @@ def config_legs(fc, torch, stream):
 
     Full-window legs: one bulk fill, then ``reps`` single-trial pushes, each recomputing the
     whole window (the EEG leg instead repeats its one evaluation of all 20 trials). Streaming
-    leg: one bulk fill of the window, then ``pushes`` single-trial pushes; beside it the same
-    pushes through the mixed-precision full window (BF16, TF32 tensor-core linear sums).
+    leg: one bulk fill of the window, then ``pushes`` single-trial pushes, exact and in the
+    mixed-precision streaming form (BF16, TF32 drift re-sum); beside it pushes through the
+    mixed-precision full window (BF16, TF32 tensor-core linear sums).
     """
     from synth import ar2_source_model, ar2_source_trials, eeg_sinusoid_trials, meg_pink_trials
 
@@ -419,10 +420,13 @@ def config_legs(fc, torch, stream):
             x = ar2_source_trials(ar2_source_model(23, n, fs=c["fs"]), 0, W + 16, N)
         dev = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
         leg = {"description": c["desc"]}
-        precs = [("fp32", fc.FC_PREC_FP32)] + ([("bf16", fc.FC_PREC_BF16), ("tf32", fc.FC_PREC_TF32)]
-                                               if c["gen"] != "eeg" else [("bf16", fc.FC_PREC_BF16)])
-        for pname, prec in precs:
-            mode = fc.FC_MODE_STREAM if (c["mode"] == "stream" and prec == fc.FC_PREC_FP32) else fc.FC_MODE_FULL
+        precs = [("fp32", fc.FC_PREC_FP32, c["mode"])] + (
+            [("bf16", fc.FC_PREC_BF16, "full"), ("tf32", fc.FC_PREC_TF32, "full")] if c["gen"] != "eeg"
+            else [("bf16", fc.FC_PREC_BF16, "full")])
+        if c["mode"] == "stream":  # the mixed-precision streaming form (tensor-core drift re-sum)
+            precs += [("bf16_stream", fc.FC_PREC_BF16, "stream"), ("tf32_stream", fc.FC_PREC_TF32, "stream")]
+        for pname, prec, pmode in precs:
+            mode = fc.FC_MODE_STREAM if pmode == "stream" else fc.FC_MODE_FULL
             mask = fc.FC_ALL_METRICS if (c["mode"] == "full" and prec == fc.FC_PREC_FP32) else fc.FC_SPECTRAL_METRICS
             with fc.Session(n, N, c["fs"], c["band"], "hann", mask, W, mode=mode, precision=prec,
                             stream=stream.cuda_stream) as s:
@@ -441,7 +445,9 @@ def config_legs(fc, torch, stream):
             ms = sum(ts) / len(ts)
             ts_sorted = sorted(ts)
             leg[pname] = {
-                "path": ("streaming add/subtract update" if mode == fc.FC_MODE_STREAM else
+                "path": (("streaming add/subtract update" + ("" if prec == fc.FC_PREC_FP32 else
+                          f", drift re-sum with tcgen05 {pname[:4].upper()} linear sums"))
+                         if mode == fc.FC_MODE_STREAM else
                          ("full-window recompute, CUDA cores" if prec == fc.FC_PREC_FP32 else
                           f"full-window recompute, tcgen05 {pname.upper()} linear sums + CUDA-core non-linear sums")),
                 "metrics": "all 9" if mask == fc.FC_ALL_METRICS else "7 spectral",

@@ -133,7 +133,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
     if (warp == EPI_WARPS) {
         // ---------------------------------------------------------- loads + MMAs
         if ((tid & 31) == 0) {
-            const uint32_t idesc = make_idesc(KIND == 1 ? 2u : (a.ab_format == 1 ? 1u : 0u), TILE, TILE);
+            // N = 256: the row tile's two kinds (XR_a then XI_a, or UR_a then UI_a) are adjacent
+            // in shared memory with the 8-row-group stride, so one MMA takes both as a
+            // 256-row operand and writes both accumulators (TMEM columns 0-127 and 128-255)
+            const uint32_t idesc = make_idesc(KIND == 1 ? 2u : (a.ab_format == 1 ? 1u : 0u), TILE, 2 * TILE);
             const long long nchunk_total = (long long)nphase * a.nchunks;
             uint32_t full_ph[NSTAGE], free_ph[NSTAGE];
             for (int s = 0; s < NSTAGE; ++s) full_ph[s] = free_ph[s] = 0;
@@ -190,10 +193,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
                         const uint32_t acc = (ch > 0 || ks > 0) ? 1u : 0u;
                         const uint32_t off = ks * 256;
                         const uint64_t d_b = smem_desc(base + 0 * CHUNK_BYTES + off);   // XR_b or UR_b
-                        const uint64_t d_ar = smem_desc(base + 1 * CHUNK_BYTES + off);  // XR_a or UR_a
-                        const uint64_t d_ai = smem_desc(base + 2 * CHUNK_BYTES + off);  // XI_a or UI_a
-                        mma<KIND>(d, d_b, d_ar, idesc, acc);
-                        mma<KIND>(d + TILE, d_b, d_ai, idesc, acc);
+                        const uint64_t d_a2 = smem_desc(base + 1 * CHUNK_BYTES + off);  // [XR_a; XI_a] or [UR_a; UI_a]
+                        mma<KIND>(d, d_b, d_a2, idesc, acc);
                     }
                     mma_commit(&freeb[st]);  // the stage may be refilled once these MMAs have read it
                     ++consumed;
@@ -520,7 +521,10 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_herk_res(HerkArgs a) {
     } else if (warp == EPI + 1) {
         // ---------------------------------------------------------- MMAs
         if ((tid & 31) == 0) {
-            const uint32_t idesc = make_idesc(KIND == 1 ? 2u : (a.ab_format == 1 ? 1u : 0u), TILE, TILE);
+            // N = 256: the row tile's two kinds (XR_a then XI_a, or UR_a then UI_a) are adjacent
+            // in shared memory with the 8-row-group stride, so one MMA takes both as a
+            // 256-row operand and writes both accumulators (TMEM columns 0-127 and 128-255)
+            const uint32_t idesc = make_idesc(KIND == 1 ? 2u : (a.ab_format == 1 ? 1u : 0u), TILE, 2 * TILE);
             uint32_t rfull_ph[RC_MAX] = {0, 0, 0, 0}, sfull_ph[NST] = {0, 0, 0, 0, 0}, acce_ph[2] = {0, 0};
             long long sused = 0, u = 0;
             for (int it = (int)blockIdx.x; it < items && !failed; it += (int)gridDim.x) {
@@ -550,10 +554,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_herk_res(HerkArgs a) {
                                 const uint32_t acc = (q > 0 || ks > 0) ? 1u : 0u;
                                 const uint32_t off = ks * 256;
                                 const uint64_t d_b = smem_desc(sb + off);                   // XR_b or UR_b
-                                const uint64_t d_ar = smem_desc(r0 + off);                  // XR_a or UR_a
-                                const uint64_t d_ai = smem_desc(r0 + CHUNK_BYTES + off);    // XI_a or UI_a
-                                mma<KIND>(d, d_b, d_ar, idesc, acc);
-                                mma<KIND>(d + TILE, d_b, d_ai, idesc, acc);
+                                const uint64_t d_a2 = smem_desc(r0 + off);                  // [XR_a; XI_a] or [UR_a; UI_a]
+                                mma<KIND>(d, d_b, d_a2, idesc, acc);
                             }
                             mma_commit(&sfree[st]);                 // the stage may be refilled
                             if (b == I.b1 - 1) mma_commit(&rfree[q]);  // last tile of the bin: slot free
@@ -765,21 +767,24 @@ __global__ void k_pack_operands(PackArgs a) {
     const long long end = c->pushed + a.count;
     const long long start = (a.W > 0 && end > a.W) ? end - a.W : 0;
     const int K = (int)(end - start);
+    const int slot0 = (int)(start % a.slots);  // ring slot of the window's first trial
     const int esize = a.ab_format == 2 ? 4 : 2;
     const int per16 = 16 / esize;                 // elements per 16-byte unit
-    const long long units_per_block = (long long)TILE * 8;  // 128 rows x 8 units of 16 bytes
-    const long long total = (long long)a.ntiles * a.B * a.nchunks * units_per_block;
+    // unit e = (block index (tile, bin, chunk)) * 1024 + (m8 * 8 + kc) * 8 + r: the low ten
+    // bits give the place in the block, the block index is split with 32-bit arithmetic
+    const long long total = (long long)a.ntiles * a.B * a.nchunks * 1024;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        long long rest = e;
-        const int r = (int)(rest % 8); rest /= 8;       // row within core matrix
-        const int kc = (int)(rest % 8); rest /= 8;      // core matrix along K within the chunk
-        const int m8 = (int)(rest % 16); rest /= 16;    // 8-row group
-        const int ch = (int)(rest % a.nchunks); rest /= a.nchunks;
-        const int f = (int)(rest % a.B); rest /= a.B;
-        const int tile = (int)rest;
+        const unsigned low = (unsigned)e & 1023u;
+        const int r = (int)(low & 7u), kc = (int)((low >> 3) & 7u), m8 = (int)(low >> 6);
+        const unsigned blk = (unsigned)(e >> 10);
+        const int ch = (int)(blk % (unsigned)a.nchunks);
+        const unsigned tf = blk / (unsigned)a.nchunks;
+        const int f = (int)(tf % (unsigned)a.B), tile = (int)(tf / (unsigned)a.B);
         const int m = m8 * 8 + r;
         const int node = tile * TILE + m;
         const int k0 = (ch * 8 + kc) * per16;           // first inner index of this 16-byte unit
+        const float2* col = a.ring + (size_t)f * a.n + node;
+        const size_t slot_stride = (size_t)a.B * a.n;
         float v[4][8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -787,8 +792,9 @@ __global__ void k_pack_operands(PackArgs a) {
             v[0][q] = v[1][q] = v[2][q] = v[3][q] = 0.f;  // padding: +0 exactly
             if (q < per16 && node < a.n && k < 2 * K) {
                 const int part = k >= K;
-                const long long trial = start + (part ? k - K : k);
-                const float2 X = a.ring[((size_t)(trial % a.slots) * a.B + f) * a.n + node];
+                int slot = slot0 + (part ? k - K : k);
+                if (slot >= a.slots) slot -= a.slots;
+                const float2 X = col[(size_t)slot * slot_stride];
                 const float2 u = phasor_of_x(X);
                 v[0][q] = part ? X.y : X.x;   // XR
                 v[1][q] = part ? -X.x : X.y;  // XI
@@ -799,7 +805,7 @@ __global__ void k_pack_operands(PackArgs a) {
 #pragma unroll
         for (int kind = 0; kind < 4; ++kind) {
             unsigned char* dst = a.ops + ((((size_t)tile * a.B + f) * 4 + kind) * a.nchunks + ch) * (size_t)CHUNK_BYTES +
-                                 (size_t)(m8 * 8 + kc) * 128 + r * 16;
+                                 (size_t)low * 16;
             *reinterpret_cast<uint4*>(dst) = pack_chunk(v[kind], per16, a.ab_format);
         }
     }

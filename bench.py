@@ -354,6 +354,10 @@ CASES = {
     "window_5124_bf16": dict(n=5124, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=100, prec="bf16", pushes=1,
                              desc="5124 nodes, W = 100, 40 bins, BF16 tensor-core full window (about 1.5 GB on the "
                                   "device): bulk fill + 1 push"),
+    "xcor_meg_window": dict(n=306, N=1000, fs=1000.0, band=(1.0, 100.0, 1024), W=100, prec="fp32", pushes=2,
+                            metrics="XCOR",
+                            desc="XCOR only, 306 MEG-sized channels, W = 100 trials x 1000 samples (2048-point "
+                                 "transforms), full-window recompute: bulk fill + 2 pushes"),
     "xcor_306_window": dict(n=306, N=500, fs=600.0, band=(8.0, 12.0, 600), W=20, prec="fp32", pushes=2,
                             metrics="XCOR",
                             desc="XCOR only, 306 nodes, W = 20 trials x 500 samples (1024-point transforms), "

@@ -123,8 +123,10 @@ __global__ void k_xcor_pairs(XcorArgs a, long long n_items, long long first_tria
     float2* buf = smem + (size_t)wib * M;
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
     if (item >= n_items) return;
-    const long long p = item / n_trials;
-    const long long trial = c->pushed + first_trial + item % n_trials;
+    // trial-major: the warps of a CTA take consecutive pairs of one trial (pairs of one row
+    // share its spectrum in L1; one trial's spectra stay in L2 while all pairs read them)
+    const long long p = item % a.P;
+    const long long trial = c->pushed + first_trial + item / a.P;
     if (trial < 0) return;  // window not yet full
     int i, j;
     unpack_pair(p, a.n, i, j);
@@ -240,8 +242,10 @@ __device__ __forceinline__ void xcor_pairs_reg(const XcorArgs& a, long long n_it
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long item = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
     if (item >= n_items) return;
-    const long long p = item / n_trials;
-    const long long trial = c->pushed + first_trial + item % n_trials;
+    // trial-major: the warps of a CTA take consecutive pairs of one trial (pairs of one row
+    // share its spectrum in L1; one trial's spectra stay in L2 while all pairs read them)
+    const long long p = item % a.P;
+    const long long trial = c->pushed + first_trial + item / a.P;
     if (trial < 0) return;  // window not yet full
     int i, j;
     unpack_pair(p, a.n, i, j);

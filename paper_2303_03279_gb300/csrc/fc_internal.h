@@ -159,6 +159,14 @@ struct fc_session {
     // in_stream into alternating buffers; async network reads leave on out_stream from a
     // device snapshot of the plane
     cudaStream_t in_stream = nullptr, out_stream = nullptr;
+    // exact drift re-sum overlapped with the streaming update (FP32 stream sessions): the
+    // slice of a single-trial push runs on side_stream (lowest priority) into resum_scratch
+    // (resum_scratch_tp tile pairs x all bins) beside k_stream; the scratch is copied over
+    // the slice's accumulator blocks once both are done
+    float* resum_scratch = nullptr;
+    int resum_scratch_tp = 0;
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     float* x_in[2] = {nullptr, nullptr};
     cudaEvent_t ev_in[2] = {nullptr, nullptr};    // the copy into x_in[b] has landed
     cudaEvent_t ev_used[2] = {nullptr, nullptr};  // the push that read x_in[b] is done
@@ -222,6 +230,7 @@ struct PairArgs {
     int update;        // stream kernel: 1 = add/subtract the trials, 0 = finalize only
     int write_acc;     // window kernel: store accumulators (re-sum)
     int tp0, tp_count; // window kernel: tile pairs tp0 .. tp0 + tp_count - 1 (tp_count 0: all)
+    int acc_tp_base;   // window kernel: the accumulator block of tile pair tp is acc[tp - acc_tp_base]
     int u0;            // stream kernel: first unit of this launch (a push may span launches)
     int fsel0, fsel1;  // bins fsel0 .. fsel1 - 1 enter the band average (a sub-band of the B)
     int count;         // trials pushed by this call (window end = pushed + count)
@@ -247,6 +256,8 @@ struct StreamBatch {
 };
 cudaError_t launch_stream_batch(const StreamBatch& b, int grid_ctas, cudaStream_t st);
 cudaError_t launch_window_sums(const PairArgs& a, cudaStream_t st);
+// nfloats (a multiple of 4) from src to dst, skipped when ctrl->bad (a rejected push)
+cudaError_t launch_copy_blocks(const float* src, float* dst, long long nfloats, const FcCtrl* ctrl, cudaStream_t st);
 cudaError_t launch_band_reduce(const PairArgs& a, cudaStream_t st);
 cudaError_t launch_bins_from_acc(const PairArgs& a, int metric_index, float* out, cudaStream_t st);
 cudaError_t launch_bins_window(const PairArgs& a, int metric_index, float* out, cudaStream_t st);

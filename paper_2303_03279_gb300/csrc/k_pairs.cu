@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window(PairArgs a, int bins_
                 sgn[q] = (q & 1) ? (int)pos[q >> 1].y - (int)neg[q >> 1].y : (int)pos[q >> 1].x - (int)neg[q >> 1].x;
             }
             if (a.write_acc) {
-                float* blk = a.acc + ((size_t)tp * a.B + f) * FC_BLOCK_WORDS;
+                float* blk = a.acc + ((size_t)(tp - a.acc_tp_base) * a.B + f) * FC_BLOCK_WORDS;
                 const int w0 = li * FC_T + lj0;
 #pragma unroll
                 for (int k = 0; k < FC_NFIELD; ++k) {
@@ -418,6 +418,28 @@ static cudaError_t launch_window_kernel(const PairArgs& a, dim3 grid, int metric
                                          (int)window_smem_bytes(true));
     if (e != cudaSuccess) return e;
     k_window<<<grid, WIN_THREADS, smem, st>>>(a, metric_index, out);
+    return cudaGetLastError();
+}
+
+namespace {
+// Re-summed accumulator blocks from the scratch into the state, unless the push was
+// rejected (then the window, and with it every block, stays as it was).
+__global__ void k_copy_blocks(const float4* __restrict__ src, float4* __restrict__ dst, long long n4,
+                              const FcCtrl* ctrl) {
+    if (ctrl->bad) return;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x)
+        __stcs(dst + i, __ldcs(src + i));
+}
+}  // namespace
+
+cudaError_t launch_copy_blocks(const float* src, float* dst, long long nfloats, const FcCtrl* ctrl, cudaStream_t st) {
+    const long long n4 = nfloats / 4;
+    if (n4 <= 0) return cudaSuccess;
+    long long blocks = (n4 + 255) / 256;
+    const long long cap = 4LL * fc_device_sms();
+    if (blocks > cap) blocks = cap;
+    k_copy_blocks<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<const float4*>(src), reinterpret_cast<float4*>(dst),
+                                                  n4, ctrl);
     return cudaGetLastError();
 }
 

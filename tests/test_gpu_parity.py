@@ -393,6 +393,7 @@ def test_nonfinite_trial_is_rejected_and_state_kept():
         for t in range(3):
             s.push(x[t])
         before = _nets(s, SPECTRAL + ("COR", "XCOR"))
+        acc_before = {f: s.accumulators(f) for f in ("csd_re", "csd_im", "u_re", "abs", "sq", "sign")}
         bad = x[3].copy()
         bad[5, 7] = np.nan
         s.push(bad)
@@ -403,6 +404,10 @@ def test_nonfinite_trial_is_rejected_and_state_kept():
         after = _nets(s, SPECTRAL + ("COR", "XCOR"))
         for m in before:
             assert np.array_equal(before[m], after[m], equal_nan=True), m
+        # the rejected push's drift re-sum slice (a third of the tile pairs at W = 3) left the
+        # accumulators as they were
+        for f, v in acc_before.items():
+            assert np.array_equal(v, s.accumulators(f)), f
         info = s.info()
         assert info.pushes == 3 and info.rejected == 1
         s.push(x[3])

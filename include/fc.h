@@ -111,7 +111,7 @@ typedef enum {
     FC_SPECTRUM_FFT = 2   /* real FFT of the tapered trial zero-padded to nfft (a mixed-radix
                              complex FFT of nfft/2 points and the even/odd split), then the band
                              bins selected; nfft even, 16 <= nfft <= 16384, nfft/2 with no prime
-                             factor above 5 (e.g. 512, 600, 1000, 1024) */
+                             factor above 7 (e.g. 512, 600, 1000, 1024, 4200) */
 } fc_spectrum;
 
 typedef struct {

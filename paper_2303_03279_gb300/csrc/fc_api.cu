@@ -872,6 +872,7 @@ int fc_fft_radices(int m, unsigned long long* packed) {
     take(2);
     take(3);
     take(5);
+    take(7);
     if (packed) *packed = p;
     return m == 1 ? n : -1;
 }
@@ -882,8 +883,8 @@ bool fc_fft_size_ok(int nfft) {
 
 // Spectrum method. Cost per (trial, node): the band DFT kernel does N x (B rounded up to its
 // 32-bin tiles) complex multiply-adds; the warp FFT does per pass and point about one (radix
-// 2, 4), two (radix 3) or three (radix 5) such operations' worth of work, times kFftCost for
-// its shared-memory round trips.
+// 2, 4), two (radix 3), three (radix 5) or four (radix 7) such operations' worth of work,
+// times kFftCost for its shared-memory round trips.
 bool fc_spectrum_uses_fft(int N, int B, int nfft, fc_spectrum method) {
     if (method == FC_SPECTRUM_DFT || !fc_fft_size_ok(nfft)) return false;
     if (method == FC_SPECTRUM_FFT) return true;
@@ -893,7 +894,7 @@ bool fc_spectrum_uses_fft(int N, int B, int nfft, fc_spectrum method) {
     double per_point = 0.0;
     for (int i = 0; i < ns; ++i) {
         const int r = (int)((p >> (4 * i)) & 15u);
-        per_point += r == 5 ? 3.0 : (r == 3 ? 2.0 : 1.0);
+        per_point += r == 7 ? 4.0 : (r == 5 ? 3.0 : (r == 3 ? 2.0 : 1.0));
     }
     const double dft = (double)N * ((B + 31) / 32 * 32);
     const double fft = kFftCost * (double)nfft * per_point;
@@ -986,7 +987,7 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
     if (cfg.spectrum < FC_SPECTRUM_AUTO || cfg.spectrum > FC_SPECTRUM_FFT) return fail(FC_ERR_INVALID_ARG, "bad spectrum method");
     if (cfg.spectrum == FC_SPECTRUM_FFT && !fc_fft_size_ok(band.nfft))
         return fail(FC_ERR_UNSUPPORTED,
-                    "the FFT spectrum needs an even nfft in 16 .. 16384 whose half has no prime factor above 5 "
+                    "the FFT spectrum needs an even nfft in 16 .. 16384 whose half has no prime factor above 7 "
                     "(nfft %d)", band.nfft);
     if (cfg.precision != FC_PREC_FP32 && cfg.mode == FC_MODE_STREAM && (window < 1 || cfg.resum_period < 0))
         return fail(FC_ERR_UNSUPPORTED,

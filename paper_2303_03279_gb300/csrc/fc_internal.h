@@ -448,8 +448,8 @@ size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode 
 // FC_SPECTRUM_AUTO: the cheaper one); 0 for an FFT request the sizes do not allow.
 bool fc_spectrum_uses_fft(int N, int B, int nfft, fc_spectrum method);
 bool fc_fft_size_ok(int nfft);
-// Radices (4 first, then 2, 3, 5) of m = nfft/2, four bits each; returns the pass count, or
-// -1 when m has a prime factor above 5.
+// Radices (4 first, then 2, 3, 5, 7) of m = nfft/2, four bits each; returns the pass count,
+// or -1 when m has a prime factor above 7.
 int fc_fft_radices(int m, unsigned long long* packed);
 int fc_band_bins(double fs, fc_band band, int* first);
 

@@ -10,9 +10,9 @@
 // put a 1e-3 relative error into every spectrum and hence into every metric.
 //
 // Wide bands (and any band, where it is cheaper) take the real-FFT method instead when nfft/2
-// has no prime factor above 5: one warp per (trial, node) transforms the tapered trial,
+// has no prime factor above 7: one warp per (trial, node) transforms the tapered trial,
 // zero-padded to nfft, as the complex sequence z[m] = y[2m] + i y[2m+1] of M = nfft/2 points
-// (mixed-radix 4/2/3/5 Stockham passes between two shared-memory buffers), and takes only the
+// (mixed-radix 4/2/3/5/7 Stockham passes between two shared-memory buffers), and takes only the
 // band bins from the even/odd split X[k] = E[k] + e^{-2 pi i k / nfft} O[k] with
 // E[k] = (Z[k] + conj Z[M-k]) / 2 and O[k] = (Z[k] - conj Z[M-k]) / 2i. Its FP32 rounding grows
 // with the number of passes instead of N.
@@ -178,7 +178,7 @@ __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int
             V[1] = f_add(d02, d13);
             V[2] = f_sub(s02, s13);
             V[3] = f_sub(d02, d13);
-        } else {  // R = 3, 5: the R-point DFT by its definition, roots from the table
+        } else {  // R = 3, 5, 7: the R-point DFT by its definition, roots from the table
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 float2 acc = v[0];
@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(256) k_spectrum_fft(SpectrumArgs a) {
         if (R == 4) stockham_pass<4>(cur, nxt, M, Ns, a.fft_tw, lane);
         else if (R == 2) stockham_pass<2>(cur, nxt, M, Ns, a.fft_tw, lane);
         else if (R == 3) stockham_pass<3>(cur, nxt, M, Ns, a.fft_tw, lane);
-        else stockham_pass<5>(cur, nxt, M, Ns, a.fft_tw, lane);
+        else if (R == 5) stockham_pass<5>(cur, nxt, M, Ns, a.fft_tw, lane);
+        else stockham_pass<7>(cur, nxt, M, Ns, a.fft_tw, lane);
         __syncwarp();
         float2* t = cur;
         cur = nxt;

@@ -73,8 +73,8 @@ def test_argument_errors_are_reported_before_device_use():
     with pytest.raises(fc.FcError) as e:
         fc.fc_session_create(8, 16, 100.0, (1.0, 20.0, 16), "hann", 1 << 12, 4)
     assert e.value.status == fc.FC_ERR_INVALID_ARG
-    # the real-FFT spectrum needs an even nfft in 16 .. 16384 with nfft/2 5-smooth
-    for nfft in (1001, 14, 8, 32768, 2 * 7 * 64):
+    # the real-FFT spectrum needs an even nfft in 16 .. 16384 with nfft/2 7-smooth
+    for nfft in (1001, 22, 8, 32768, 2 * 11 * 64):
         cfg = fc.fc_config_default()
         cfg.spectrum = fc.FC_SPECTRUM_FFT
         with pytest.raises(fc.FcError) as e:

@@ -59,6 +59,8 @@ SPECTRUM_CASES = [
     (50, 500, 1000, (4.0, 44.0), "hann"),       # nfft/2 = 500: radix 4, 5, 5, 5
     (20, 600, 600, (8.0, 12.0), "hann_sym"),    # nfft/2 = 300: radix 4, 3, 5, 5
     (7, 100, 240, (0.0, 501.0), "none"),        # nfft/2 = 120: radix 4, 2, 3, 5; every bin
+    (9, 300, 448, (0.0, 501.0), "hann"),        # nfft/2 = 224: radix 4, 4, 2, 7; every bin
+    (4, 4000, 4200, (8.0, 12.0), "hann"),       # nfft/2 = 2100: radix 4, 3, 5, 5, 7
 ]
 
 

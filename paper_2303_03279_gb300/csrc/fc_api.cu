@@ -603,15 +603,9 @@ fc_status stage_resum_slice(fc_session* s) {
 // networks come from the streaming state and the state ends as the slice's sums: the same
 // arithmetic and order of effects as the update followed by the slice.
 
-fc_status push_stream_overlapped(fc_session* s, PairArgs pa) {
-    long long r, R;
-    next_resum_phase(s, r, R);
-    const int tp0 = (int)(s->ntp * r / R), tp1 = (int)(s->ntp * (r + 1) / R);
-    if (tp1 <= tp0) {  // no tile pair in this phase: the update alone
-        LAUNCH(FC_K_STREAM, launch_stream_update(pa, s->stream));
-        if (pa.finalize && pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
-        return FC_OK;
-    }
+// Marks the point of the session stream after which the slice may start (the push's
+// spectra and per-node sums are in), creating the side stream on first use.
+fc_status resum_fork_point(fc_session* s) {
     if (!s->side_stream) {
         int least = 0, greatest = 0;
         CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
@@ -619,8 +613,12 @@ fc_status push_stream_overlapped(fc_session* s, PairArgs pa) {
         CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
     }
-    CK(cudaEventRecord(s->ev_fork, s->stream));  // spectra and per-node sums of the trial are in
-    LAUNCH(FC_K_STREAM, launch_stream_update(pa, s->stream));
+    CK(cudaEventRecord(s->ev_fork, s->stream));
+    return FC_OK;
+}
+
+// The slice of tile pairs tp0 .. tp1 - 1 on the side stream, into the scratch.
+fc_status resum_fork(fc_session* s, int tp0, int tp1) {
     CK(cudaStreamWaitEvent(s->side_stream, s->ev_fork, 0));
     PairArgs ps = pair_args(s, false, 1);
     ps.write_acc = 1;
@@ -633,10 +631,29 @@ fc_status push_stream_overlapped(fc_session* s, PairArgs pa) {
     ps.acc_tp_base = tp0;
     LAUNCH_ON(FC_K_WINDOW, s->side_stream, launch_window_sums(ps, s->side_stream));
     CK(cudaEventRecord(s->ev_join, s->side_stream));
+    return FC_OK;
+}
+
+// After the update: the scratch over the slice's blocks (skipped for a rejected push).
+fc_status resum_join(fc_session* s, int tp0, int tp1) {
     CK(cudaStreamWaitEvent(s->stream, s->ev_join, 0));
     const long long words = (long long)(tp1 - tp0) * s->B * FC_BLOCK_WORDS;
     LAUNCH(FC_K_OTHER, launch_copy_blocks(s->resum_scratch, s->acc + (size_t)tp0 * s->B * FC_BLOCK_WORDS, words,
                                           s->ctrl, s->stream));
+    return FC_OK;
+}
+
+fc_status push_stream_overlapped(fc_session* s, PairArgs pa) {
+    long long r, R;
+    next_resum_phase(s, r, R);
+    const int tp0 = (int)(s->ntp * r / R), tp1 = (int)(s->ntp * (r + 1) / R);
+    fc_status st;
+    if (tp1 > tp0 && (st = resum_fork_point(s)) != FC_OK) return st;
+    LAUNCH(FC_K_STREAM, launch_stream_update(pa, s->stream));
+    if (tp1 > tp0) {
+        if ((st = resum_fork(s, tp0, tp1)) != FC_OK) return st;
+        if ((st = resum_join(s, tp0, tp1)) != FC_OK) return st;
+    }
     if (pa.finalize && pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
     return FC_OK;
 }
@@ -833,6 +850,32 @@ fc_status fc_push_batch_pre(fc_session* const* ss, const float* const* x, int co
     LAUNCH(FC_K_OTHER, launch_validate_batch(b, st));
     LAUNCH(FC_K_SPECTRUM, launch_spectrum_batch(b, st));
     LAUNCH(FC_K_NODE, launch_node_batch(b, st));
+    // drift re-sum slices of FP32 sessions: set up here (their inputs are in), launched by
+    // fc_push_batch_fork beside the update, copied in by fc_push_batch_post
+    for (int i = 0; i < count; ++i) {
+        fc_session* si = ss[i];
+        if (!si->resum_scratch || !resum_on(si) || si->resum_pending) continue;
+        long long r, R;
+        next_resum_phase(si, r, R);
+        si->resum_tp0 = (int)(si->ntp * r / R);
+        si->resum_tp1 = (int)(si->ntp * (r + 1) / R);
+        if (si->resum_tp1 <= si->resum_tp0) continue;
+        fc_status fst = resum_fork_point(si);
+        if (fst != FC_OK) return fst;
+        si->resum_pending = true;
+        si->resum_forked = false;
+    }
+    return FC_OK;
+}
+
+fc_status fc_push_batch_fork(fc_session* const* ss, int count) {
+    for (int i = 0; i < count; ++i) {
+        fc_session* s = ss[i];
+        if (!s->resum_pending || s->resum_forked) continue;
+        fc_status st = resum_fork(s, s->resum_tp0, s->resum_tp1);
+        if (st != FC_OK) return st;
+        s->resum_forked = true;
+    }
     return FC_OK;
 }
 
@@ -845,8 +888,14 @@ fc_status fc_push_batch_post(fc_session* const* ss, FcCtrl* const* snap, int cou
         fc_session* s = ss[i];
         PairArgs pa = fc_push_stream_args(s);
         if (pa.finalize && pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
-        fc_status r = stage_resum_slice(s);
-        if (r != FC_OK) return r;
+        fc_status r;
+        if (s->resum_pending) {  // the slice forked at the push's first share
+            if (!s->resum_forked && (r = resum_fork(s, s->resum_tp0, s->resum_tp1)) != FC_OK) return r;
+            if ((r = resum_join(s, s->resum_tp0, s->resum_tp1)) != FC_OK) return r;
+            s->resum_pending = s->resum_forked = false;
+        } else if (!s->resum_scratch && (r = stage_resum_slice(s)) != FC_OK) {
+            return r;
+        }
         b.ctrl[i] = s->ctrl;
         b.snap[i] = snap ? snap[i] : nullptr;
     }

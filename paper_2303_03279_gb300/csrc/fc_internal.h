@@ -167,6 +167,10 @@ struct fc_session {
     int resum_scratch_tp = 0;
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // a batched (served) push's slice: tile pairs resum_tp0 .. resum_tp1 - 1, forked after the
+    // push's per-node sums, copied in when its last share of the update is done
+    int resum_tp0 = 0, resum_tp1 = 0;
+    bool resum_pending = false, resum_forked = false;
     float* x_in[2] = {nullptr, nullptr};
     cudaEvent_t ev_in[2] = {nullptr, nullptr};    // the copy into x_in[b] has landed
     cudaEvent_t ev_used[2] = {nullptr, nullptr};  // the push that read x_in[b] is done
@@ -441,6 +445,9 @@ fc_status fc_push_single(fc_session* s, const float* xdev);
 PairArgs fc_push_stream_args(fc_session* s);
 fc_status fc_push_batch_pre(fc_session* const* ss, const float* const* x, int count, cudaStream_t st);
 fc_status fc_push_batch_post(fc_session* const* ss, FcCtrl* const* snap, int count, cudaStream_t st);
+// Launch, on each session's side stream, the drift re-sum slices that fc_push_batch_pre set
+// up (call after the batched update launch, so the update's CTAs are dispatched first).
+fc_status fc_push_batch_fork(fc_session* const* ss, int count);
 void fc_count_launch(fc_session* s);
 size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode mode,
                              fc_precision prec = FC_PREC_FP32, int nfft = 0);

@@ -241,6 +241,9 @@ fc_status enqueue_tick(fc_server* sv, const std::vector<Part>& plan, InFlight& f
         cudaError_t e = launch_stream_batch(b, 2 * sv->num_sms, sv->stream);
         if (e != cudaSuccess) return sfail(FC_ERR_CUDA, cudaGetErrorString(e));
     }
+    // the drift re-sum slices of the pushes that started in this tick, beside the update
+    pst = fc_push_batch_fork(pre_s, npre);
+    if (pst != FC_OK) return pst;
     // drift re-sum slices, then one commit of every push that finishes; the commit also
     // writes each control block (prescale, rejection count) to the session's pinned slot
     fc_session* post_s[FC_MAX_BATCH];

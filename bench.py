@@ -707,6 +707,9 @@ def run_ours(args, w, wname):
                     "algorithmic_bytes_per_launch": alg_bytes,
                     "traffic": ncu_traffic(stream_kernel_hash(), wname)}
     kernel_share = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in ktimes.items() if v[0]}
+    if "window" in kernel_share:  # the exact re-sum slice runs on a side stream beside the update
+        kernel_share["window"]["note"] = ("drift re-sum slice on the session's side stream, timed from its "
+                                          "fork: includes waiting for the SMs the update holds")
 
     # e2e: host trial in (pinned), one metric's network out, through the public API. Each
     # step pushes its trial from pinned host memory and reads its COH network back into
@@ -839,7 +842,12 @@ def run_ours(args, w, wname):
                                 "signs; FP32 partial sums of <= 36 trials into double words)",
                         "kernels_ms_per_push": {k: round(v, 4) for k, v in kms.items()},
                         "tensor_core_share_of_push": kms.get("herk_tc", 0.0) / sms_,
-                        "resum_slice_ms_per_push": kms.get("herk_tc", 0.0) + kms.get("window", 0.0)}
+                        # the slice's non-linear sums run beside the update on a side stream: their
+                        # event times include waiting for SMs, so the push time beyond the update is
+                        # what the re-sum costs
+                        "push_beyond_update_ms": sms_ - kms.get("stream", 0.0),
+                        "side_stream_note": "window: the slice's non-linear sums, timed on the side "
+                                            "stream from the fork (includes waiting for the update's SMs)"}
         ss.close()
         del ss
 

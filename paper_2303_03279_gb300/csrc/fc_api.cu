@@ -522,13 +522,10 @@ PackArgs ring_pack_args(fc_session* s, int count) {
 // Mixed-precision streaming: push r of a period re-sums the 128-node tile pairs
 // [ntp128 r / R, ntp128 (r + 1) / R): their linear sums (CSD re, phasor re and im) from the
 // tensor cores over the operand ring, their non-linear sums (sum Im, sum |Im|, sum Im^2,
-// signs) from the exact window kernel on the 32-node tile pairs inside them. The ring takes
-// this push's trial first (and drops the one leaving the window).
-fc_status stage_resum_slice_mixed(fc_session* s, long long r, long long R) {
-    PackArgs pk = ring_pack_args(s, 1);
-    LAUNCH(FC_K_HERK_TC, launch_pack_ring(pk, 0, s->stream));
-    const int p0 = (int)(s->ntp128 * r / R), p1 = (int)(s->ntp128 * (r + 1) / R);
-    if (p1 <= p0) return FC_OK;
+// signs) from the non-linear sums kernel on the 32-node tile pairs inside them. The ring
+// takes this push's trial first (and drops the one leaving the window).
+// The tensor-core part: linear sums of 128-node tile pairs p0 .. p1 - 1 into the state.
+fc_status resum_mixed_linear(fc_session* s, int p0, int p1) {
     HerkArgs ha{};
     ha.ops = s->ops;
     ha.tile_a = s->tile_a128;
@@ -553,7 +550,13 @@ fc_status stage_resum_slice_mixed(fc_session* s, long long r, long long R) {
     ha.acc_out = s->acc;
     ha.nt32 = s->nt;
     LAUNCH(FC_K_HERK_TC, launch_herk_tc(ha, s->stream));
-    // the non-linear sums of the same 32-node tile pairs, every bin (accumulators, not the band)
+    return FC_OK;
+}
+
+// The non-linear sums (sum Im, sum |Im|, sum Im^2, signs) of the 32-node tile pairs inside
+// 128-node tile pairs p0 .. p1 - 1: into the state, or (scratch) into the session's scratch
+// by list position, on stream st.
+fc_status resum_mixed_nonlinear(fc_session* s, int p0, int p1, bool scratch, cudaStream_t st) {
     PairArgs pa = pair_args(s, false, 1);
     pa.tp_list = s->list32;
     pa.tp0 = s->list32_off[p0];
@@ -565,8 +568,22 @@ fc_status stage_resum_slice_mixed(fc_session* s, long long r, long long R) {
     const long long waves = 8LL * s->num_sms * nonlinear_ctas_per_sm();
     pa.group_bins = (int)std::max(1LL, std::min<long long>(s->B, (long long)pa.tp_count * s->B / std::max(1LL, waves)));
     pa.groups = (s->B + pa.group_bins - 1) / pa.group_bins;
-    LAUNCH(FC_K_WINDOW, launch_nonlinear_acc(pa, s->stream));
+    if (scratch) {
+        pa.acc = s->resum_scratch;
+        pa.acc_by_pos = 1;
+    }
+    LAUNCH_ON(FC_K_WINDOW, st, launch_nonlinear_acc(pa, st));
     return FC_OK;
+}
+
+fc_status stage_resum_slice_mixed(fc_session* s, long long r, long long R) {
+    PackArgs pk = ring_pack_args(s, 1);
+    LAUNCH(FC_K_HERK_TC, launch_pack_ring(pk, 0, s->stream));
+    const int p0 = (int)(s->ntp128 * r / R), p1 = (int)(s->ntp128 * (r + 1) / R);
+    if (p1 <= p0) return FC_OK;
+    fc_status st = resum_mixed_linear(s, p0, p1);
+    if (st != FC_OK) return st;
+    return resum_mixed_nonlinear(s, p0, p1, false, s->stream);
 }
 
 // The slice phase of this push (r of R), advancing the session's phase.
@@ -617,9 +634,30 @@ fc_status resum_fork_point(fc_session* s) {
     return FC_OK;
 }
 
-// The slice of tile pairs tp0 .. tp1 - 1 on the side stream, into the scratch.
-fc_status resum_fork(fc_session* s, int tp0, int tp1) {
+// This push's slice: 32-node tile pairs [t0, t1) of an FP32 session, 128-node tile pairs of
+// a mixed-precision one (advances the session's re-sum phase); false when it is empty.
+bool resum_range(fc_session* s, int& t0, int& t1) {
+    long long r, R;
+    next_resum_phase(s, r, R);
+    const long long nt = s->mixed_stream ? s->ntp128 : s->ntp;
+    t0 = (int)(nt * r / R);
+    t1 = (int)(nt * (r + 1) / R);
+    return t1 > t0;
+}
+
+// The slice [t0, t1) on the side stream, into the scratch: the whole exact re-sum of an FP32
+// session; the operand-ring update and the non-linear sums of a mixed-precision one.
+fc_status resum_fork(fc_session* s, int t0, int t1) {
     CK(cudaStreamWaitEvent(s->side_stream, s->ev_fork, 0));
+    if (s->mixed_stream) {
+        PackArgs pk = ring_pack_args(s, 1);
+        LAUNCH_ON(FC_K_OTHER, s->side_stream, launch_pack_ring(pk, 0, s->side_stream));
+        fc_status st = resum_mixed_nonlinear(s, t0, t1, true, s->side_stream);
+        if (st != FC_OK) return st;
+        CK(cudaEventRecord(s->ev_join, s->side_stream));
+        return FC_OK;
+    }
+    const int tp0 = t0, tp1 = t1;
     PairArgs ps = pair_args(s, false, 1);
     ps.write_acc = 1;
     ps.finalize = 0;
@@ -634,9 +672,20 @@ fc_status resum_fork(fc_session* s, int tp0, int tp1) {
     return FC_OK;
 }
 
-// After the update: the scratch over the slice's blocks (skipped for a rejected push).
-fc_status resum_join(fc_session* s, int tp0, int tp1) {
+// After the update: the scratch over the slice's blocks (skipped for a rejected push); for a
+// mixed-precision session first the tensor-core linear sums straight into the state, then
+// the non-linear planes from the scratch.
+fc_status resum_join(fc_session* s, int t0, int t1) {
     CK(cudaStreamWaitEvent(s->stream, s->ev_join, 0));
+    if (s->mixed_stream) {
+        fc_status st = resum_mixed_linear(s, t0, t1);
+        if (st != FC_OK) return st;
+        const int off = s->list32_off[t0], cnt = s->list32_off[t1] - off;
+        LAUNCH(FC_K_OTHER, launch_gather_nonlinear(s->resum_scratch, s->acc, s->list32 + off, cnt, s->B, s->ctrl,
+                                                   s->stream));
+        return FC_OK;
+    }
+    const int tp0 = t0, tp1 = t1;
     const long long words = (long long)(tp1 - tp0) * s->B * FC_BLOCK_WORDS;
     LAUNCH(FC_K_OTHER, launch_copy_blocks(s->resum_scratch, s->acc + (size_t)tp0 * s->B * FC_BLOCK_WORDS, words,
                                           s->ctrl, s->stream));
@@ -644,15 +693,17 @@ fc_status resum_join(fc_session* s, int tp0, int tp1) {
 }
 
 fc_status push_stream_overlapped(fc_session* s, PairArgs pa) {
-    long long r, R;
-    next_resum_phase(s, r, R);
-    const int tp0 = (int)(s->ntp * r / R), tp1 = (int)(s->ntp * (r + 1) / R);
+    int t0, t1;
+    const bool slice = resum_range(s, t0, t1);
     fc_status st;
-    if (tp1 > tp0 && (st = resum_fork_point(s)) != FC_OK) return st;
+    if (slice && (st = resum_fork_point(s)) != FC_OK) return st;
     LAUNCH(FC_K_STREAM, launch_stream_update(pa, s->stream));
-    if (tp1 > tp0) {
-        if ((st = resum_fork(s, tp0, tp1)) != FC_OK) return st;
-        if ((st = resum_join(s, tp0, tp1)) != FC_OK) return st;
+    if (slice) {
+        if ((st = resum_fork(s, t0, t1)) != FC_OK) return st;
+        if ((st = resum_join(s, t0, t1)) != FC_OK) return st;
+    } else if (s->mixed_stream) {  // the operand ring takes the trial every push
+        PackArgs pk = ring_pack_args(s, 1);
+        LAUNCH(FC_K_HERK_TC, launch_pack_ring(pk, 0, s->stream));
     }
     if (pa.finalize && pa.groups > 1) LAUNCH(FC_K_BAND_REDUCE, launch_band_reduce(pa, s->stream));
     return FC_OK;
@@ -855,11 +906,10 @@ fc_status fc_push_batch_pre(fc_session* const* ss, const float* const* x, int co
     for (int i = 0; i < count; ++i) {
         fc_session* si = ss[i];
         if (!si->resum_scratch || !resum_on(si) || si->resum_pending) continue;
-        long long r, R;
-        next_resum_phase(si, r, R);
-        si->resum_tp0 = (int)(si->ntp * r / R);
-        si->resum_tp1 = (int)(si->ntp * (r + 1) / R);
-        if (si->resum_tp1 <= si->resum_tp0) continue;
+        if (!resum_range(si, si->resum_tp0, si->resum_tp1)) {
+            si->resum_tp0 = si->resum_tp1 = -1;  // empty phase (a mixed session's ring still takes the trial)
+            continue;
+        }
         fc_status fst = resum_fork_point(si);
         if (fst != FC_OK) return fst;
         si->resum_pending = true;
@@ -893,8 +943,11 @@ fc_status fc_push_batch_post(fc_session* const* ss, FcCtrl* const* snap, int cou
             if (!s->resum_forked && (r = resum_fork(s, s->resum_tp0, s->resum_tp1)) != FC_OK) return r;
             if ((r = resum_join(s, s->resum_tp0, s->resum_tp1)) != FC_OK) return r;
             s->resum_pending = s->resum_forked = false;
-        } else if (!s->resum_scratch && (r = stage_resum_slice(s)) != FC_OK) {
-            return r;
+        } else if (!s->resum_scratch) {
+            if ((r = stage_resum_slice(s)) != FC_OK) return r;
+        } else if (s->mixed_stream && resum_on(s)) {  // empty phase: the operand ring takes the trial
+            PackArgs pk = ring_pack_args(s, 1);
+            LAUNCH(FC_K_HERK_TC, launch_pack_ring(pk, 0, s->stream));
         }
         b.ctrl[i] = s->ctrl;
         b.snap[i] = snap ? snap[i] : nullptr;
@@ -969,6 +1022,8 @@ size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode 
             const size_t per_chunk = prec == FC_PREC_TF32 ? 32 : 64;
             const size_t nchunks = (2 * slots + per_chunk - 1) / per_chunk;
             b += nt128 * B * 4 * nchunks * herk_chunk_bytes() + ntp128 * 4 + ntp * 4 + (size_t)B * n;
+            // re-sum scratch: at most 16 32-node tile pairs per 128-node tile pair of a slice
+            b += (ntp128 + W - 1) / W * 16 * B * FC_BLOCK_WORDS * 4;
         }
         int wg, wgb;
         const int sms = fc_device_sms();
@@ -1203,6 +1258,16 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
             TRY(upload(s, s->list32, l32.data(), l32.size() * sizeof(int)));
             TRY(alloc_zero(s, (size_t)s->nt128 * B * 4 * s->nchunks * herk_chunk_bytes(), &s->ops));
             TRY(alloc_zero(s, (size_t)B * n_nodes, &s->tiny_flags));
+            // the non-linear re-sum of one push beside the update: its 32-node tile pairs (at
+            // most those inside one slice of 128-node tile pairs), all bins
+            const int R = cfg.resum_period > 0 ? cfg.resum_period : window;
+            int most = 0;
+            for (int r = 0; r < R; ++r) {
+                const int p0 = (int)((long long)s->ntp128 * r / R), p1 = (int)((long long)s->ntp128 * (r + 1) / R);
+                most = std::max(most, s->list32_off[p1] - s->list32_off[p0]);
+            }
+            s->resum_scratch_tp = std::max(1, most);
+            TRY(alloc_zero(s, (size_t)s->resum_scratch_tp * B * FC_BLOCK_WORDS, &s->resum_scratch));
         }
         if (cfg.precision != FC_PREC_FP32 && cfg.mode == FC_MODE_FULL) {
             s->ab_format = cfg.precision == FC_PREC_BF16 ? 1 : (cfg.precision == FC_PREC_FP16 ? 0 : 2);

@@ -235,6 +235,7 @@ struct PairArgs {
     int write_acc;     // window kernel: store accumulators (re-sum)
     int tp0, tp_count; // window kernel: tile pairs tp0 .. tp0 + tp_count - 1 (tp_count 0: all)
     int acc_tp_base;   // window kernel: the accumulator block of tile pair tp is acc[tp - acc_tp_base]
+    int acc_by_pos;    // non-linear re-sum: block i of the list goes to acc[i] (a scratch), not acc[tp]
     int u0;            // stream kernel: first unit of this launch (a push may span launches)
     int fsel0, fsel1;  // bins fsel0 .. fsel1 - 1 enter the band average (a sub-band of the B)
     int count;         // trials pushed by this call (window end = pushed + count)
@@ -262,6 +263,10 @@ cudaError_t launch_stream_batch(const StreamBatch& b, int grid_ctas, cudaStream_
 cudaError_t launch_window_sums(const PairArgs& a, cudaStream_t st);
 // nfloats (a multiple of 4) from src to dst, skipped when ctrl->bad (a rejected push)
 cudaError_t launch_copy_blocks(const float* src, float* dst, long long nfloats, const FcCtrl* ctrl, cudaStream_t st);
+// The non-linear planes (sum Im, sum |Im|, sum Im^2, sign count) of scratch block set i (B bins)
+// into the accumulator blocks of tile pair list[i], i < count; skipped when ctrl->bad.
+cudaError_t launch_gather_nonlinear(const float* scratch, float* acc, const int* list, int count, int B,
+                                    const FcCtrl* ctrl, cudaStream_t st);
 cudaError_t launch_band_reduce(const PairArgs& a, cudaStream_t st);
 cudaError_t launch_bins_from_acc(const PairArgs& a, int metric_index, float* out, cudaStream_t st);
 cudaError_t launch_bins_window(const PairArgs& a, int metric_index, float* out, cudaStream_t st);

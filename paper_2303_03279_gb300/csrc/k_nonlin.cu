@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
             if constexpr (ACC) {
                 // accumulator block of (tile pair, bin): planes 2k, 2k + 1 = hi, lo of field k
                 // (1 sum Im, 4 sum |Im|, 5 sum Im^2), plane 12 the sign count
-                float* blk = a.acc + ((size_t)tp * a.B + f) * FC_BLOCK_WORDS;
+                float* blk = a.acc + ((size_t)(a.acc_by_pos ? (int)blockIdx.x : tp) * a.B + f) * FC_BLOCK_WORDS;
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
                     const int w0 = (li0 + r) * FC_T + lj0, q0 = 2 * r, q1 = 2 * r + 1;

@@ -432,6 +432,39 @@ __global__ void k_copy_blocks(const float4* __restrict__ src, float4* __restrict
 }
 }  // namespace
 
+namespace {
+// planes 2, 3 (sum Im), 8 .. 11 (sum |Im|, sum Im^2) and 12 (sign count) of a block
+__global__ void k_gather_nonlinear(const float4* __restrict__ scratch, float4* __restrict__ acc,
+                                   const int* __restrict__ list, long long n4, int B, const FcCtrl* ctrl) {
+    if (ctrl->bad) return;
+    constexpr int P4 = FC_TT / 4;  // float4 per plane
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(e % P4);
+        long long rest = e / P4;
+        const int pi = (int)(rest % 7);
+        rest /= 7;
+        const int f = (int)(rest % B);
+        const long long i = rest / B;
+        const int plane = pi < 2 ? 2 + pi : 6 + pi;  // 2, 3, 8, 9, 10, 11, 12
+        const size_t off = (size_t)plane * P4 + w;
+        const float4 v = __ldcs(scratch + ((size_t)i * B + f) * (FC_BLOCK_WORDS / 4) + off);
+        __stcs(acc + ((size_t)list[i] * B + f) * (FC_BLOCK_WORDS / 4) + off, v);
+    }
+}
+}  // namespace
+
+cudaError_t launch_gather_nonlinear(const float* scratch, float* acc, const int* list, int count, int B,
+                                    const FcCtrl* ctrl, cudaStream_t st) {
+    const long long n4 = (long long)count * B * 7 * (FC_TT / 4);
+    if (n4 <= 0) return cudaSuccess;
+    long long blocks = (n4 + 255) / 256;
+    const long long cap = 4LL * fc_device_sms();
+    if (blocks > cap) blocks = cap;
+    k_gather_nonlinear<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<const float4*>(scratch),
+                                                       reinterpret_cast<float4*>(acc), list, n4, B, ctrl);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_copy_blocks(const float* src, float* dst, long long nfloats, const FcCtrl* ctrl, cudaStream_t st) {
     const long long n4 = nfloats / 4;
     if (n4 <= 0) return cudaSuccess;

@@ -191,6 +191,19 @@ std::vector<Part> plan_tick(fc_server* sv) {
             take(ss, can);
         }
     }
+    // whole waves: the persistent update grid takes units round-robin, so a share whose units
+    // are not a multiple of its CTAs leaves the launch as long as the CTAs with one unit more.
+    // The largest share that does not finish in this launch is trimmed to a multiple (its rest
+    // goes next tick); any contiguous run of such a length gives every CTA as many of its units.
+    const long long grid = 2LL * sv->num_sms;
+    Part* big = nullptr;
+    for (Part& p : plan)
+        if (!p.single && !p.finish && (!big || p.nu > big->nu)) big = &p;
+    if (big && big->nu > grid) {
+        const long long extra = big->nu % grid;
+        big->nu -= extra;
+        big->ss->next_unit -= extra;
+    }
     return plan;
 }
 

@@ -159,10 +159,11 @@ struct fc_session {
     // in_stream into alternating buffers; async network reads leave on out_stream from a
     // device snapshot of the plane
     cudaStream_t in_stream = nullptr, out_stream = nullptr;
-    // exact drift re-sum overlapped with the streaming update (FP32 stream sessions): the
-    // slice of a single-trial push runs on side_stream (lowest priority) into resum_scratch
-    // (resum_scratch_tp tile pairs x all bins) beside k_stream; the scratch is copied over
-    // the slice's accumulator blocks once both are done
+    // drift re-sum overlapped with the streaming update: the slice of a push (FP32 sessions:
+    // the whole exact re-sum; mixed-precision sessions: its non-linear sums) runs on
+    // side_stream (lowest priority) into resum_scratch (resum_scratch_tp 32-node tile pairs x
+    // all bins) beside k_stream; the scratch goes over the slice's accumulator blocks (their
+    // non-linear planes for mixed precision) once both are done
     float* resum_scratch = nullptr;
     int resum_scratch_tp = 0;
     cudaStream_t side_stream = nullptr;

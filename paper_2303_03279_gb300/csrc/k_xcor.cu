@@ -275,11 +275,39 @@ __device__ __forceinline__ void xcor_pairs_reg(const XcorArgs& a, long long n_it
 #pragma unroll 1
     for (int half = 0; half < (1 << S); ++half) {
         float2 x[E];
+        if (S == 0) {
+            // one pass: the products P[k] = Z_i[k] conj(Z_j[k]) of this lane's k into the warp's
+            // transpose buffer (free until the transpose), P[M] (the Nyquist bin) in lane 0's
+            // register; then the even/odd split with P[M - k] from the buffer, so each spectrum
+            // element is loaded from memory once
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int k = lane + 32 * r;
+                tb[k] = cmul(Zi[k], cconj(Zj[k]));
+            }
+            const float2 pnyq = lane == 0 ? cmul(Zi[M], cconj(Zj[M])) : make_float2(0.f, 0.f);
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int k = lane + 32 * r;
+                const float2 pk = tb[k];
+                const float2 pm = cconj(k == 0 ? pnyq : tb[M - k]);
+                const float2 e2 = make_float2(0.5f * __fadd_rn(pk.x, pm.x), 0.5f * __fadd_rn(pk.y, pm.y));
+                const float2 dd = csub(pk, pm);
+                float2 w;  // e^{+2 pi i k / L}
+                if (!NO_STW)
+                    w = cconj(stw[k]);
+                else
+                    w = cconj((k & 1) ? cmul(sth[M / 2 + (k >> 1)], tw1) : sth[M / 2 + (k >> 1)]);
+                const float2 o = cmul(make_float2(0.5f * dd.x, 0.5f * dd.y), w);
+                x[r] = make_float2(__fsub_rn(e2.x, o.y), __fadd_rn(e2.y, o.x));
+            }
+        }
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const int e = lane + 32 * r;
             if (S == 0) {
-                x[r] = prod(e);
+                // formed above
             } else if (S == 1) {  // first stage, span MS: top half u + v, bottom half (u - v) e^{+2 pi i e / M}
                 const float2 u = prod(e), v = prod(e + MS);
                 x[r] = half == 0 ? cadd(u, v) : cmul(csub(u, v), cconj(sth[MS + e]));

@@ -901,8 +901,9 @@ fc_status fc_push_batch_pre(fc_session* const* ss, const float* const* x, int co
     LAUNCH(FC_K_OTHER, launch_validate_batch(b, st));
     LAUNCH(FC_K_SPECTRUM, launch_spectrum_batch(b, st));
     LAUNCH(FC_K_NODE, launch_node_batch(b, st));
-    // drift re-sum slices of FP32 sessions: set up here (their inputs are in), launched by
-    // fc_push_batch_fork beside the update, copied in by fc_push_batch_post
+    // drift re-sum slices (FP32 sessions: the exact re-sum; mixed-precision sessions: its
+    // non-linear sums): set up here (their inputs are in), launched by fc_push_batch_fork
+    // beside the update, put into the state by fc_push_batch_post
     for (int i = 0; i < count; ++i) {
         fc_session* si = ss[i];
         if (!si->resum_scratch || !resum_on(si) || si->resum_pending) continue;
@@ -1360,11 +1361,11 @@ fc_status fc_session_destroy(fc_session* s) {
     cudaStreamSynchronize(s->stream);
     if (s->in_stream) cudaStreamSynchronize(s->in_stream);
     if (s->out_stream) cudaStreamSynchronize(s->out_stream);
+    if (s->side_stream) cudaStreamSynchronize(s->side_stream);  // a re-sum slice may still write the scratch
     drain_timings(s);
     free_all(s);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     if (s->side_stream) {
-        cudaStreamSynchronize(s->side_stream);
         cudaStreamDestroy(s->side_stream);
         cudaEventDestroy(s->ev_fork);
         cudaEventDestroy(s->ev_join);

@@ -199,20 +199,21 @@ __global__ void k_xcor_pairs(XcorArgs a, long long n_items, long long first_tria
 // so the remaining spans (below E and below 32) pair registers of the same lane again, with
 // twiddles that are the same for every lane. The output lands in bit-reversed order, which
 // the scan over lags reads through the bit reversal of each position.
-// CTAs per SM to keep registers for: at 512- and 1024-point transforms one more than the
-// register use alone would allow (shared memory holds four and three; the kernel is
-// issue-bound and gains from warps)
+// CTAs per SM to keep registers for: at 512-point transforms one more than the register use
+// alone would allow (shared memory holds four; the kernel is issue-bound and gains from
+// warps); at 1024 points two, with the product-step twiddle table (three CTAs without the
+// table and with 80 registers spilled and took 3 % longer once the products are staged
+// in shared memory)
 // 0: no minimum (the plain bound). The explicit minimum of one at 2048 points lets ptxas
 // keep 240 registers instead of 188 (15 % faster); at 4096 points it made ptxas spill
 // 564 bytes (22 % slower), so that form keeps the plain bound.
 template <int E, int S> struct XcorMinBlocks { static constexpr int v = 0; };
 template <> struct XcorMinBlocks<16, 0> { static constexpr int v = 4; };
-template <> struct XcorMinBlocks<32, 0> { static constexpr int v = 3; };
+template <> struct XcorMinBlocks<32, 0> { static constexpr int v = 2; };
 template <> struct XcorMinBlocks<64, 0> { static constexpr int v = 1; };
 // Forms without the product-step twiddle table stw (its odd entries come from the stage
-// table): 8192 points, where it does not fit, and 1024 points, where leaving it out lets a
-// third CTA onto the SM
-template <int E, int S> struct XcorNoStw { static constexpr bool v = S == 2 || (E == 32 && S == 0); };
+// table): 8192 points, where it does not fit
+template <int E, int S> struct XcorNoStw { static constexpr bool v = S == 2; };
 
 template <int E, int S>
 __device__ __forceinline__ void xcor_pairs_reg(const XcorArgs& a, long long n_items, long long first_trial,

@@ -438,6 +438,7 @@ fc_status stage_window(fc_session* s, int count, bool write_acc) {
         pk.count = count;
         pk.ab_format = s->ab_format;
         pk.ctrl = s->ctrl;
+        pk.ring_order = 1;  // operands by ring slot: a single push rewrites one slot only
         HerkArgs ha{};
         ha.ops = s->ops;
         ha.tile_a = s->tile_a128;
@@ -470,7 +471,10 @@ fc_status stage_window(fc_session* s, int count, bool write_acc) {
             else
                 herk_groups(s->ntp128, s->sel1 - s->sel0, s->num_sms, (long long)s->P, s->herk_gcap, ha.groups,
                             ha.group_bins);
-            LAUNCH(FC_K_HERK_TC, launch_pack_operands(pk, s->stream));
+            if (count == 1)  // the new trial's slot (it held the trial that left)
+                LAUNCH(FC_K_HERK_TC, launch_pack_ring(pk, 2, s->stream));
+            else if (count > 1)  // the whole window (a band change, count 0, keeps the operands)
+                LAUNCH(FC_K_HERK_TC, launch_pack_operands(pk, s->stream));
             LAUNCH(FC_K_HERK_TC, launch_herk_tc(ha, s->stream));
             LAUNCH(FC_K_BAND_REDUCE, launch_herk_band(ha, s->stream));
         }

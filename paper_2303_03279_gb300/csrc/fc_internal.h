@@ -279,6 +279,8 @@ struct PackArgs {
     int n, B, W, slots, ntiles, nchunks, count;
     int ab_format;        // 0 = FP16, 1 = BF16, 2 = TF32
     const FcCtrl* ctrl;
+    int ring_order;       // full pack: inner positions by ring slot (s, slots + s) instead of by
+                          // window order (k, K + k); slots outside the window hold zeros
 };
 struct HerkArgs {
     const unsigned char* ops;

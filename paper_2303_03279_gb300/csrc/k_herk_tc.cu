@@ -790,10 +790,22 @@ __global__ void k_pack_operands(PackArgs a) {
         for (int q = 0; q < 8; ++q) {
             const int k = k0 + q;
             v[0][q] = v[1][q] = v[2][q] = v[3][q] = 0.f;  // padding: +0 exactly
-            if (q < per16 && node < a.n && k < 2 * K) {
-                const int part = k >= K;
-                int slot = slot0 + (part ? k - K : k);
+            bool take = false;
+            int slot = 0, part = 0;
+            if (a.ring_order) {  // position k: slot k (first half) or k - slots (second half)
+                part = k >= a.slots;
+                slot = part ? k - a.slots : k;
+                if (slot < a.slots) {  // the window's trial in this slot, if any
+                    const long long t = end - 1 - (((end - 1 - slot) % a.slots) + a.slots) % a.slots;
+                    take = t >= start && t >= 0;
+                }
+            } else if (k < 2 * K) {
+                part = k >= K;
+                slot = slot0 + (part ? k - K : k);
                 if (slot >= a.slots) slot -= a.slots;
+                take = true;
+            }
+            if (q < per16 && node < a.n && take) {
                 const float2 X = col[(size_t)slot * slot_stride];
                 const float2 u = phasor_of_x(X);
                 v[0][q] = part ? X.y : X.x;   // XR
@@ -838,16 +850,19 @@ __global__ void k_pack_ring(PackArgs a, int mode) {
     if (c->bad) return;
     const long long end = c->pushed + a.count;  // window after this call: [end - W, end)
     const long long start = end > a.W ? end - a.W : 0;
-    const int nslot = mode == 0 ? 2 : a.slots;
+    // mode 0: the newest slot written, the next one (whose trial left) cleared; mode 1: every
+    // slot from the window; mode 2: the newest slot only (full mode: W slots, so the newest
+    // trial's slot is the one whose trial left)
+    const int nslot = mode == 0 ? 2 : (mode == 2 ? 1 : a.slots);
     const long long total = (long long)nslot * a.B * a.n;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         const int node = (int)(e % a.n);
         const int f = (int)((e / a.n) % a.B);
         const int q = (int)(e / ((long long)a.n * a.B));
         // mode 0: q = 0 the newest trial's slot, q = 1 the slot of the trial that left
-        const int s = mode == 0 ? (int)((q == 0 ? end - 1 : end) % a.slots) : q;
+        const int s = mode != 1 ? (int)((q == 0 ? end - 1 : end) % a.slots) : q;
         bool in_window = false;
-        if (mode == 0) {
+        if (mode != 1) {
             in_window = q == 0;
         } else {
             // the window's trial in slot s, if any: t = s (mod slots), start <= t < end
@@ -920,7 +935,7 @@ cudaError_t launch_herk_tc(const HerkArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_pack_ring(const PackArgs& a, int mode, cudaStream_t st) {
-    const long long total = (long long)(mode == 0 ? 2 : a.slots) * a.B * a.n;
+    const long long total = (long long)(mode == 0 ? 2 : (mode == 2 ? 1 : a.slots)) * a.B * a.n;
     long long blocks = (total + 255) / 256;
     const long long cap = 8LL * fc_device_sms();
     if (blocks > cap) blocks = cap;

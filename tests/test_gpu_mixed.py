@@ -148,6 +148,37 @@ def test_mixed_window_fill_and_slide():
                 _check(s, min(t + 1, W))
 
 
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_mixed_bulk_then_single_pushes_and_band_change(prec):
+    """The full-window operands are kept by ring slot: a bulk fill packs the whole window,
+    each single push rewrites only its own trial's slot (the slot of the trial that left), a
+    band change reuses the operands as they are. Against the oracle on the window's GPU
+    spectra after the fill, after single pushes that slide the window past every slot, and
+    after a band change (oracle on the selected bins) and one more push."""
+    n, N, W = 140, 128, 5
+    x = white_trials(23, W + 8, n, N)
+    with fc.Session(n, N, 256.0, (4.0, 60.0, 128), "hann", fc.FC_SPECTRAL_METRICS, W,
+                    mode=fc.FC_MODE_FULL, precision=PRECISIONS[prec]) as s:
+        s.push(x[:W])
+        _check(s, W, prec=prec)
+        for t in range(W, W + 7):
+            s.push(x[t])
+        _check(s, W, prec=prec)
+        fc.fc_set_band(s.handle, 10.0, 30.0)  # bins 5 .. 14 of the computed 2 .. 29
+        sel = slice(5 - 2, 15 - 2)
+        for step in range(2):
+            X = window_spectra(s, W)[:, :, sel]
+            I, J = np.triu_indices(n, 1)
+            ref = O.spectral_networks_pairs(X, I, J)
+            for m in LINEAR:
+                got = s.network(m, packed=True)[0].astype(np.float64)
+                assert np.abs(got - ref[m]).max() <= TOL_TC[prec], (m, step)
+            for m in NONLINEAR:
+                assert_close(s.network(m, packed=True)[0], ref[m], what=f"{m} after the band change")
+            if step == 0:
+                s.push(x[W + 7])
+
+
 def test_streaming_tensor_core_precision_needs_a_sliding_window_with_resum():
     """In stream mode a tensor-core precision applies to the drift re-sum of a sliding window:
     a cumulative window (0) or a session without re-sums is refused."""

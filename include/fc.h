@@ -171,7 +171,11 @@ fc_status fc_session_destroy(fc_session* s);
  * copied; a pageable host buffer may be reused on return, a page-locked one or a device
  * buffer once the session's stream has passed this call (fc_sync). A trial holding NaN or
  * Inf is rejected on the device and leaves the state unchanged; the next synchronizing
- * call (fc_sync, fc_get_network, fc_session_info) then reports FC_ERR_NONFINITE once. */
+ * call (fc_sync, fc_get_network, fc_session_info) then reports FC_ERR_NONFINITE once.
+ * In stream mode with a drift re-sum, the push's re-sum slice runs on a second stream the
+ * session owns (created on first use, lowest priority), beside the update on the session's
+ * stream; events order it after the push's spectra and before the push's end on the
+ * session's stream, so callers see one ordered stream as before. */
 fc_status fc_push_trial(fc_session* s, const float* x, int x_on_device);
 
 /* Push `count` trials x[count][n_nodes][n_samples] (host or device) and update the network

@@ -41,13 +41,28 @@ __device__ __forceinline__ void node_elem(const NodeArgs& a, int e) {
         const long long end = c->pushed + a.count;
         const long long start = (a.W > 0 && end > a.W) ? end - a.W : 0;
         const float sc = c->in_scale;  // 0 for sessions (their ring holds prescaled spectra)
-        s = 0.0;
+        // |X|^2 summed as a double word on the FP32 pipes: both squares are exact two-products
+        // while every nonzero component is at least 2^-50 (no underflow); a node with a tiny
+        // component takes the FP64 sum instead
+        df32 acc = df_make(0.f, 0.f);
         bool tiny = false;
         for (long long k = start; k < end; ++k) {
             float2 X = a.ring[((size_t)(k % a.slots) * a.B + f) * a.n + i];
             if (sc != 0.f) X = make_float2(__fmul_rn(X.x, sc), __fmul_rn(X.y, sc));
-            s += (double)X.x * X.x + (double)X.y * X.y;
+            float p1, e1, p2, e2;
+            two_prod(X.x, X.x, p1, e1);
+            two_prod(X.y, X.y, p2, e2);
+            acc = df_add_df(acc, df_add_df(df_make(p1, e1), df_make(p2, e2)));
             tiny |= node_tiny(X);
+        }
+        s = (double)acc.hi + (double)acc.lo;
+        if (tiny) {
+            s = 0.0;
+            for (long long k = start; k < end; ++k) {
+                float2 X = a.ring[((size_t)(k % a.slots) * a.B + f) * a.n + i];
+                if (sc != 0.f) X = make_float2(__fmul_rn(X.x, sc), __fmul_rn(X.y, sc));
+                s += (double)X.x * X.x + (double)X.y * X.y;
+            }
         }
         if (a.tiny) a.tiny[e] = tiny ? 1 : 0;
     }

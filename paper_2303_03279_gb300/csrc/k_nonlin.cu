@@ -28,7 +28,12 @@
 // (a, a, b, b) and (-a, -a) so that they load straight into packed FP32x2 operands; column
 // spectra as planes of a and b. Per pair and trial the loop issues the determinant (two
 // packed FMAs, a packed multiply and FMA for two pairs), two compare-to-float tallies, one
-// absolute add and a packed add and FMA for two pairs.
+// absolute add and a packed add and FMA for two pairs; it is unrolled four trials deep so
+// that the shared-memory loads of later trials cover the latency of earlier ones. The next
+// chunk of trials is copied by cp.async while the current one is computed, two adjacent
+// nodes (16 bytes) per copy when the node count is even. Each bin's metrics are formed for
+// two pairs per packed operation (CUDA's built-in FP32x2 operations, which round each lane
+// like the scalar operation and are never contracted), bit for bit as the scalar finalize.
 #include "df32.cuh"
 #include "fc_internal.h"
 #include "pair_common.cuh"
@@ -59,11 +64,29 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) 
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// x^2 - s for two lanes of double words x = xh + xl, s = sh + sl: the same correctly rounded
+// steps as df_sq_minus per lane (exact square of the leading word by FMA, the cross term
+// 2 xh xl, the two differences and their sum), on the packed FP32 pipe. The built-in packed
+// operations round like their scalar counterparts and are never contracted.
+__device__ __forceinline__ float2 sq_minus2(float2 xh, float2 xl, float2 sh, float2 sl) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 nph = __fmul2_rn(__fmul2_rn(xh, m1), xh);        // -fl(xh^2)
+    float2 pl = __ffma2_rn(xh, xh, nph);                          // xh^2 - fl(xh^2), exact
+    pl = __ffma2_rn(__fadd2_rn(xh, xh), xl, pl);                  // + 2 xh xl
+    const float2 d1 = __fadd2_rn(nph, sh);                        // -(fl(xh^2) - sh)
+    const float2 d2 = __ffma2_rn(sl, m1, pl);                     // pl - sl
+    return __ffma2_rn(d1, m1, d2);                                // (fl(xh^2) - sh) + (pl - sl)
+}
+
 struct NlSmem {
-    float2 raw[NK][2 * FC_T];   // the next chunk's spectra as copied (row tile, column tile)
+    alignas(16) float2 raw[NK][2 * FC_T];  // the next chunk's spectra as copied (row tile, column tile)
     float4 rowv[NK][FC_T];  // row node i: (a, a, b, b)
     float2 rown[NK][FC_T];  // row node i: (-a, -a)
     float4 cola[NK][FC_T / 4];  // column nodes: a, four per vector
@@ -100,12 +123,16 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
         }
     for (int e = tid; e < 4 * FC_TT; e += NL_THREADS) (&sm.band[0][0][0])[e] = 0.f;
 
-    // Chunks of NK trials of the bins fa .. fb - 1 in order. Thread tid always copies and
-    // converts node l = tid % 64 of the two tiles, trials kk = tid / 64 + 2 q of a chunk: the
-    // copy of chunk c + 1 (cp.async, asynchronous) runs while chunk c is computed.
-    const int l_node = tid & 63, kk0 = tid >> 6;
+    // Chunks of NK trials of the bins fa .. fb - 1 in order; the copy of chunk c + 1
+    // (cp.async, asynchronous) runs while chunk c is computed. For an even node count a
+    // thread copies and converts node pairs (16 bytes per copy): pair lp of the two tiles'
+    // 32, trials kp0 + 4 q, each warp on one tile. For an odd node count: node l = tid % 64,
+    // trials tid / 64 + 2 q.
+    const bool pairs = (a.n & 1) == 0;
+    const int lp = ((tid >> 5) & 1) * (FC_T / 2) + (tid & 15), kp0 = ((tid >> 6) << 1) | ((tid >> 4) & 1);
+    const int l_node = pairs ? 2 * lp : tid & 63, kk0 = pairs ? kp0 : tid >> 6;
     const int node = l_node < FC_T ? ta * FC_T + l_node : tb * FC_T + l_node - FC_T;
-    const bool node_ok = node < a.n;
+    const bool node_ok = node < a.n;  // even count: node + 1 < n as well
     const int nchunk = (K + NK - 1) / NK;
     const int csize = (K + nchunk - 1) / nchunk;  // balanced chunks of at most NK trials
     const int slot_start = (int)(start % a.slots);
@@ -116,12 +143,22 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
         while (slot >= a.slots) slot -= a.slots;
         const float2* src = a.ring + (size_t)f * a.n + node;
         const size_t slot_stride = (size_t)a.B * a.n;
+        if (pairs) {
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int kk = kk0 + 2 * q;
-            if (kk < kn && node_ok) cp_async8(&sm.raw[kk][l_node], src + (size_t)slot * slot_stride);
-            slot += 2;
-            if (slot >= a.slots) slot -= a.slots;
+            for (int q = 0; q < PER / 2; ++q) {
+                const int kk = kk0 + 4 * q;
+                if (kk < kn && node_ok) cp_async16(&sm.raw[kk][l_node], src + (size_t)slot * slot_stride);
+                slot += 4;
+                if (slot >= a.slots) slot -= a.slots;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int kk = kk0 + 2 * q;
+                if (kk < kn && node_ok) cp_async8(&sm.raw[kk][l_node], src + (size_t)slot * slot_stride);
+                slot += 2;
+                if (slot >= a.slots) slot -= a.slots;
+            }
         }
         cp_async_commit();
     };
@@ -149,17 +186,34 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
             const int kn = min(csize, K - k0);
             cp_async_wait_all();
             __syncthreads();  // the chunk has landed; every thread is done with the previous one
+            if (pairs) {
 #pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                const int kk = kk0 + 2 * q;
-                float2 X = make_float2(0.f, 0.f);
-                if (kk < kn && node_ok) X = sm.raw[kk][l_node];
-                if (l_node < FC_T) {
-                    sm.rowv[kk][l_node] = make_float4(X.x, X.x, X.y, X.y);
-                    sm.rown[kk][l_node] = make_float2(-X.x, -X.x);
-                } else {
-                    reinterpret_cast<float*>(sm.cola[kk])[l_node - FC_T] = X.x;
-                    reinterpret_cast<float*>(sm.colb[kk])[l_node - FC_T] = X.y;
+                for (int q = 0; q < PER / 2; ++q) {
+                    const int kk = kk0 + 4 * q;
+                    float4 X = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (kk < kn && node_ok) X = *reinterpret_cast<const float4*>(&sm.raw[kk][l_node]);
+                    if (l_node < FC_T) {
+                        sm.rowv[kk][l_node] = make_float4(X.x, X.x, X.y, X.y);
+                        sm.rowv[kk][l_node + 1] = make_float4(X.z, X.z, X.w, X.w);
+                        *reinterpret_cast<float4*>(&sm.rown[kk][l_node]) = make_float4(-X.x, -X.x, -X.z, -X.z);
+                    } else {
+                        *reinterpret_cast<float2*>(reinterpret_cast<float*>(sm.cola[kk]) + l_node - FC_T) = make_float2(X.x, X.z);
+                        *reinterpret_cast<float2*>(reinterpret_cast<float*>(sm.colb[kk]) + l_node - FC_T) = make_float2(X.y, X.w);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < PER; ++q) {
+                    const int kk = kk0 + 2 * q;
+                    float2 X = make_float2(0.f, 0.f);
+                    if (kk < kn && node_ok) X = sm.raw[kk][l_node];
+                    if (l_node < FC_T) {
+                        sm.rowv[kk][l_node] = make_float4(X.x, X.x, X.y, X.y);
+                        sm.rown[kk][l_node] = make_float2(-X.x, -X.x);
+                    } else {
+                        reinterpret_cast<float*>(sm.cola[kk])[l_node - FC_T] = X.x;
+                        reinterpret_cast<float*>(sm.colb[kk])[l_node - FC_T] = X.y;
+                    }
                 }
             }
             __syncthreads();  // converted; the raw buffer is free again
@@ -174,7 +228,7 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
             for (int q = 0; q < 4; ++q) pim[q] = pab[q] = psq[q] = make_float2(0.f, 0.f);
             auto chunk = [&](auto tiny_c) {
                 constexpr bool TINY = decltype(tiny_c)::value;
-#pragma unroll 2
+#pragma unroll 4
                 for (int kk = 0; kk < kn; ++kk) {
                     const float4 ca = sm.cola[kk][cg], cb = sm.colb[kk][cg];
                     const float2 aj[2] = {make_float2(ca.x, ca.y), make_float2(ca.z, ca.w)};
@@ -245,49 +299,65 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
                            make_int4((int)pos[q0].x - (int)neg[q0].x, (int)pos[q0].y - (int)neg[q0].y,
                                      (int)pos[q1].x - (int)neg[q1].x, (int)pos[q1].y - (int)neg[q1].y));
                 }
-                continue;
-            }
+            } else {
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                float4 acc[4];
+                for (int r = 0; r < 2; ++r) {
+                    float4 acc[4];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) acc[m] = *reinterpret_cast<float4*>(&sm.band[m][li0 + r][lj0]);
+                    for (int m = 0; m < 4; ++m) acc[m] = *reinterpret_cast<float4*>(&sm.band[m][li0 + r][lj0]);
 #pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                    const int q = 2 * r + (c4 >> 1);
-                    const bool y = c4 & 1;
-                    const float fp = y ? pos[q].y : pos[q].x, fn = y ? neg[q].y : neg[q].x;
-                    const int np = (int)fp, nn = (int)fn;
-                    const int sg = np - nn;
-                    const df32 sim = y ? df_make(imh[q].y, iml[q].y) : df_make(imh[q].x, iml[q].x);
-                    const df32 sab = y ? df_make(abh[q].y, abl[q].y) : df_make(abh[q].x, abl[q].x);
-                    const df32 ssq = y ? df_make(sqh[q].y, sql[q].y) : df_make(sqh[q].x, sql[q].x);
-                    // |S| and S^2 - K as floats, exactly, as in the session finalize
-                    float pli_n, usn;
-                    if (K <= 2048) {
-                        pli_n = small_int_to_float(abs(sg));
-                        usn = small_int_to_float(sg * sg - K);
-                    } else {
-                        pli_n = (float)abs(sg);
-                        usn = K <= 46340 ? (float)(sg * sg - K) : (float)((long long)sg * sg - K);
+                    for (int h = 0; h < 2; ++h) {
+                        // two pairs (columns lj0 + 2h, + 1) per packed operation; every lane takes
+                        // the same correctly rounded steps as the scalar finalize of a session
+                        const int q = 2 * r + h;
+                        const float2 m1 = make_float2(-1.f, -1.f);
+                        const float2 nz = __fadd2_rn(pos[q], neg[q]);  // nonzero terms (exact)
+                        float2 pli, uspli;
+                        if (K <= 4096) {
+                            // S = pos - neg and S^2 - K are exact in FP32 while |S| <= K <= 4096
+                            const float2 sg = __ffma2_rn(neg[q], m1, pos[q]);
+                            pli = make_float2(__fmul_rn(fabsf(sg.x), kc.inv_K), __fmul_rn(fabsf(sg.y), kc.inv_K));
+                            uspli = __fmul2_rn(__ffma2_rn(sg, sg, f2(-(float)K)), f2(kc.inv_KK1));
+                        } else {
+                            float* pl = &pli.x;
+                            float* us = &uspli.x;
+#pragma unroll
+                            for (int y = 0; y < 2; ++y) {
+                                const int sg = (int)(y ? pos[q].y : pos[q].x) - (int)(y ? neg[q].y : neg[q].x);
+                                const float usn = K <= 46340 ? (float)(sg * sg - K) : (float)((long long)sg * sg - K);
+                                pl[y] = __fmul_rn((float)abs(sg), kc.inv_K);
+                                us[y] = __fmul_rn(usn, kc.inv_KK1);
+                            }
+                        }
+                        const float2 fsab = __fadd2_rn(abh[q], abl[q]);  // double words to float
+                        const float2 fsim = __fadd2_rn(imh[q], iml[q]);
+                        const float2 wpli = make_float2(fsab.x > 0.f ? __fdividef(fabsf(fsim.x), fsab.x) : 0.f,
+                                                        fsab.y > 0.f ? __fdividef(fabsf(fsim.y), fsab.y) : 0.f);
+                        // (sum Im)^2 - sum Im^2 and (sum |Im|)^2 - sum Im^2 from the double words
+                        const float2 num = sq_minus2(imh[q], iml[q], sqh[q], sql[q]);
+                        const float2 den = sq_minus2(abh[q], abl[q], sqh[q], sql[q]);
+                        // two or more nonzero terms, else 0 (the definition's zero denominator)
+                        const float2 dsw = make_float2(nz.x > 1.f && den.x != 0.f ? __fdividef(num.x, den.x) : 0.f,
+                                                       nz.y > 1.f && den.y != 0.f ? __fdividef(num.y, den.y) : 0.f);
+                        auto add_lanes = [&](float4& v, float2 t) {
+                            if (h == 0) {
+                                const float2 u = __fadd2_rn(make_float2(v.x, v.y), t);
+                                v.x = u.x;
+                                v.y = u.y;
+                            } else {
+                                const float2 u = __fadd2_rn(make_float2(v.z, v.w), t);
+                                v.z = u.x;
+                                v.w = u.y;
+                            }
+                        };
+                        add_lanes(acc[0], pli);
+                        add_lanes(acc[1], uspli);
+                        add_lanes(acc[2], wpli);
+                        add_lanes(acc[3], dsw);
                     }
-                    const float pli = __fmul_rn(pli_n, kc.inv_K);
-                    const float uspli = __fmul_rn(usn, kc.inv_KK1);
-                    const float fsab = df_to_f(sab);
-                    const float wpli = fsab > 0.f ? __fdividef(fabsf(df_to_f(sim)), fsab) : 0.f;
-                    float dswpli = 0.f;
-                    if (np + nn > 1) {  // two or more nonzero terms
-                        const float num = df_sq_minus(sim, ssq);
-                        const float den = df_sq_minus(sab, ssq);
-                        dswpli = den != 0.f ? __fdividef(num, den) : 0.f;
-                    }
-                    set4(acc[0], c4, __fadd_rn(get4(acc[0], c4), pli));
-                    set4(acc[1], c4, __fadd_rn(get4(acc[1], c4), uspli));
-                    set4(acc[2], c4, __fadd_rn(get4(acc[2], c4), wpli));
-                    set4(acc[3], c4, __fadd_rn(get4(acc[3], c4), dswpli));
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) *reinterpret_cast<float4*>(&sm.band[m][li0 + r][lj0]) = acc[m];
                 }
-#pragma unroll
-                for (int m = 0; m < 4; ++m) *reinterpret_cast<float4*>(&sm.band[m][li0 + r][lj0]) = acc[m];
             }
         }
     }

@@ -148,6 +148,20 @@ def test_mixed_window_fill_and_slide():
                 _check(s, min(t + 1, W))
 
 
+@pytest.mark.parametrize("n", [97, 98])
+def test_mixed_window_odd_and_even_node_counts(n):
+    """The non-linear sums stage the spectra one node per copy for an odd node count and two
+    nodes per copy for an even one; both, with a ragged last 32-node tile, a window of two
+    chunks of trials (K = 40) and a ring that has wrapped, against the oracle."""
+    N, W = 128, 40
+    x = white_trials(29, W + 3, n, N)
+    with fc.Session(n, N, 256.0, (4.0, 60.0, 128), "hann", fc.FC_SPECTRAL_METRICS, W,
+                    mode=fc.FC_MODE_FULL, precision=fc.FC_PREC_BF16) as s:
+        s.push(x[:W + 2])
+        s.push(x[W + 2])
+        _check(s, W)
+
+
 @pytest.mark.parametrize("prec", ["bf16", "tf32"])
 def test_mixed_bulk_then_single_pushes_and_band_change(prec):
     """The full-window operands are kept by ring slot: a bulk fill packs the whole window,

@@ -796,9 +796,10 @@ def run_ours(args, w, wname):
         if tc_launches:
             # algorithmic tensor work: 16 flop per pair-bin-trial (the CSD and phasor complex
             # multiply-adds); the launched GEMMs (4 real 128 x 128 x Kp per 128-node tile pair and
-            # bin, Kp = 2W padded to 64, full diagonal tiles) are larger
+            # bin, Kp = 2W padded to the 16-element K-step of the resident-operand products,
+            # full diagonal tiles) are larger
             nt128 = (n + 127) // 128
-            kp = ((2 * W + 63) // 64) * 64
+            kp = ((2 * W + 15) // 16) * 16
             flops_alg = 16 * P * B * W
             flops_padded = 4 * 2 * 128 * 128 * kp * (nt128 * (nt128 + 1) // 2) * B
             herk_ms = tc_ms / tc_launches * 2

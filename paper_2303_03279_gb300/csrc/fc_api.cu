@@ -439,6 +439,7 @@ fc_status stage_window(fc_session* s, int count, bool write_acc) {
         pk.ab_format = s->ab_format;
         pk.ctrl = s->ctrl;
         pk.ring_order = 1;  // operands by ring slot: a single push rewrites one slot only
+        pk.last_kc = s->last_kc;
         HerkArgs ha{};
         ha.ops = s->ops;
         ha.tile_a = s->tile_a128;
@@ -464,6 +465,7 @@ fc_status stage_window(fc_session* s, int count, bool write_acc) {
         ha.seg_b1 = s->seg_b1;
         ha.nseg = s->nseg;
         ha.seg_max = s->seg_max;
+        ha.last_kc = s->last_kc;
         if (s->mask & (FC_COH | FC_IMAGCOHY | FC_PLV)) {
             if (s->seg_a)
                 herk_res_groups(s->nseg, s->seg_max, s->sel1 - s->sel0, s->num_sms, (long long)s->P, s->herk_gcap,
@@ -520,6 +522,7 @@ PackArgs ring_pack_args(fc_session* s, int count) {
     pk.count = count;
     pk.ab_format = s->ab_format;
     pk.ctrl = s->ctrl;
+    pk.last_kc = s->last_kc;
     return pk;
 }
 
@@ -553,6 +556,7 @@ fc_status resum_mixed_linear(fc_session* s, int p0, int p1) {
     ha.ctrl = s->ctrl;
     ha.acc_out = s->acc;
     ha.nt32 = s->nt;
+    ha.last_kc = s->last_kc;
     LAUNCH(FC_K_HERK_TC, launch_herk_tc(ha, s->stream));
     return FC_OK;
 }
@@ -1295,7 +1299,13 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
             int gb;
             if (s->nchunks <= herk_resident_max_chunks()) {
                 // resident-operand form: each row tile a with its column tiles b >= a in balanced
-                // segments of at most kHerkSegTiles tiles
+                // segments of at most kHerkSegTiles tiles. Its operands keep, in the last
+                // K-chunk, only the 16-byte columns up to the last K-step that holds inner
+                // positions (2 W of them; the rest would be zero padding)
+                const int per16 = per_chunk / 8;
+                const int units16 = (2 * window + per16 - 1) / per16;
+                const int last = units16 - 8 * (s->nchunks - 1);
+                s->last_kc = std::min(8, last + (last & 1));
                 std::vector<unsigned short> sa, sb0, sb1;
                 for (int ta = 0; ta < s->nt128; ++ta) {
                     const int len = s->nt128 - ta, parts = (len + kHerkSegTiles - 1) / kHerkSegTiles;

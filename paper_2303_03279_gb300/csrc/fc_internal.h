@@ -130,6 +130,7 @@ struct fc_session {
     int xcor_spec_trials;
     // tensor-core full-window path (precision BF16 / FP16 / TF32)
     int nt128, ntp128, nchunks, ab_format;
+    int last_kc = 8;        // core-matrix columns of the last operand K-chunk (see PackArgs)
     unsigned short* tile_a128;
     unsigned short* tile_b128;
     unsigned char* ops;     // packed operands [nt128][B][4][nchunks][16 KB]
@@ -281,6 +282,8 @@ struct PackArgs {
     const FcCtrl* ctrl;
     int ring_order;       // full pack: inner positions by ring slot (s, slots + s) instead of by
                           // window order (k, K + k); slots outside the window hold zeros
+    int last_kc;          // 16-byte core-matrix columns stored in the last K-chunk (2 .. 7: the
+                          // short layout read by the resident-operand products; else all 8)
 };
 struct HerkArgs {
     const unsigned char* ops;
@@ -301,6 +304,7 @@ struct HerkArgs {
     const unsigned short* seg_b0;
     const unsigned short* seg_b1;
     int nseg, seg_max;
+    int last_kc;          // as PackArgs::last_kc (the resident-operand form only)
     // accumulator mode (drift re-sum of a mixed-precision streaming session): the products of
     // 128-node tile pairs tp0 .. tp0 + ntp - 1 are written as the linear sums (CSD re, phasor
     // re and im) of the streaming accumulators acc (nt32 node tiles of 32), not as metrics

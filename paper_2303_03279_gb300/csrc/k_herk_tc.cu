@@ -21,7 +21,12 @@
 // K-major, no-swizzle canonical layout of core matrices (8 rows x 16 bytes):
 //   byte offset = ((m / 8) * 8 + kc) * 128 + (m % 8) * 16 + (byte within the 16-byte row chunk)
 // i.e. leading (K-direction) core-matrix stride 128 B, stride (M/N-direction) 1024 B.
-// One cp.async.bulk moves a block into shared memory as is.
+// One cp.async.bulk moves a block into shared memory as is. Short last chunk (operands of
+// the resident-operand form, last_kc < 8): the last K-chunk keeps only its first last_kc
+// core-matrix columns, those up to the last K-step that holds inner positions (the others
+// hold zero padding only), as (m / 8) * last_kc + kc core matrices, 8-row groups last_kc x
+// 128 B apart, at the start of its 16 KB block; its copies move 2 KB per column and its
+// MMAs take last_kc / 2 K-steps.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -53,6 +58,12 @@ __device__ __forceinline__ long long packed_index(int i, int j, int n) {
 
 __device__ __forceinline__ const unsigned char* op_block(const HerkArgs& a, int tile, int f, int kind, int chunk) {
     return a.ops + ((((size_t)tile * a.B + f) * 4 + kind) * a.nchunks + chunk) * (size_t)CHUNK_BYTES;
+}
+
+// Core-matrix columns stored in K-chunk ch of a pack with last_kc (the short layout of the
+// last chunk when 2 <= last_kc < 8, else all 8).
+__device__ __forceinline__ int chunk_cols(int last_kc, int ch, int nchunks) {
+    return (ch == nchunks - 1 && last_kc >= 2 && last_kc < 8) ? last_kc : 8;
 }
 
 // Work of one CTA: units u = blockIdx.x + k gridDim.x of ntp x groups (tile pair u / groups,
@@ -491,10 +502,13 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_herk_res(HerkArgs a) {
                             if (!mbar_wait_bounded(&rfree[q], rfree_ph[q])) { failed = true; break; }
                             rfree_ph[q] ^= 1;
                         }
+                        // the two kinds back to back, so that the second continues the first's
+                        // 8-row groups (a 256-row operand); a short last chunk moves less
+                        const uint32_t qb = (uint32_t)chunk_cols(a.last_kc, q, nch) * 2048u;
                         unsigned char* dst = res + (size_t)q * 2 * CHUNK_BYTES;
-                        mbar_expect_tx(&rfull[q], 2 * CHUNK_BYTES);
-                        bulk_g2s(dst, op_block(a, I.a, f, kr, q), CHUNK_BYTES, &rfull[q]);
-                        bulk_g2s(dst + CHUNK_BYTES, op_block(a, I.a, f, kr + 1, q), CHUNK_BYTES, &rfull[q]);
+                        mbar_expect_tx(&rfull[q], 2 * qb);
+                        bulk_g2s(dst, op_block(a, I.a, f, kr, q), qb, &rfull[q]);
+                        bulk_g2s(dst + qb, op_block(a, I.a, f, kr + 1, q), qb, &rfull[q]);
                     }
                     if (failed) break;
                     ++rloads;
@@ -505,8 +519,9 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_herk_res(HerkArgs a) {
                                 if (!mbar_wait_bounded(&sfree[st], sfree_ph[st])) { failed = true; break; }
                                 sfree_ph[st] ^= 1;
                             }
-                            mbar_expect_tx(&sfull[st], CHUNK_BYTES);
-                            bulk_g2s(stg + (size_t)st * CHUNK_BYTES, op_block(a, b, f, kr, q), CHUNK_BYTES, &sfull[st]);
+                            const uint32_t qb = (uint32_t)chunk_cols(a.last_kc, q, nch) * 2048u;
+                            mbar_expect_tx(&sfull[st], qb);
+                            bulk_g2s(stg + (size_t)st * CHUNK_BYTES, op_block(a, b, f, kr, q), qb, &sfull[st]);
                             ++scount[st];
                             ++sloads;
                         }
@@ -549,12 +564,15 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_herk_res(HerkArgs a) {
                             fence_after();
                             const uint32_t sb = smem_u32(stg + (size_t)st * CHUNK_BYTES);
                             const uint32_t r0 = smem_u32(res + (size_t)q * 2 * CHUNK_BYTES);
+                            const int cols = chunk_cols(a.last_kc, q, nch);  // 2 per K-step
+                            const uint32_t sbo = (uint32_t)cols * 128u;
 #pragma unroll
                             for (int ks = 0; ks < 4; ++ks) {
+                                if (2 * ks >= cols) break;
                                 const uint32_t acc = (q > 0 || ks > 0) ? 1u : 0u;
                                 const uint32_t off = ks * 256;
-                                const uint64_t d_b = smem_desc(sb + off);                   // XR_b or UR_b
-                                const uint64_t d_a2 = smem_desc(r0 + off);                  // [XR_a; XI_a] or [UR_a; UI_a]
+                                const uint64_t d_b = smem_desc_sbo(sb + off, sbo);          // XR_b or UR_b
+                                const uint64_t d_a2 = smem_desc_sbo(r0 + off, sbo);         // [XR_a; XI_a] or [UR_a; UI_a]
                                 mma<KIND>(d, d_b, d_a2, idesc, acc);
                             }
                             mma_commit(&sfree[st]);                 // the stage may be refilled
@@ -780,6 +798,8 @@ __global__ void k_pack_operands(PackArgs a) {
         const int ch = (int)(blk % (unsigned)a.nchunks);
         const unsigned tf = blk / (unsigned)a.nchunks;
         const int f = (int)(tf % (unsigned)a.B), tile = (int)(tf / (unsigned)a.B);
+        const int cols = chunk_cols(a.last_kc, ch, a.nchunks);
+        if (kc >= cols) continue;  // not stored (zero padding of a short last chunk)
         const int m = m8 * 8 + r;
         const int node = tile * TILE + m;
         const int k0 = (ch * 8 + kc) * per16;           // first inner index of this 16-byte unit
@@ -817,7 +837,7 @@ __global__ void k_pack_operands(PackArgs a) {
 #pragma unroll
         for (int kind = 0; kind < 4; ++kind) {
             unsigned char* dst = a.ops + ((((size_t)tile * a.B + f) * 4 + kind) * a.nchunks + ch) * (size_t)CHUNK_BYTES +
-                                 (size_t)low * 16;
+                                 (size_t)((m8 * cols + kc) * 8 + r) * 16;
             *reinterpret_cast<uint4*>(dst) = pack_chunk(v[kind], per16, a.ab_format);
         }
     }
@@ -832,8 +852,9 @@ __device__ __forceinline__ void put_elem(unsigned char* ops, const PackArgs& a, 
     const int esize = a.ab_format == 2 ? 4 : 2;
     const int per16 = 16 / esize;
     const int chunk = k / (8 * per16), kc = (k / per16) % 8, e16 = k % per16;
+    const int cols = chunk_cols(a.last_kc, chunk, a.nchunks);  // kc < cols for every stored k
     unsigned char* dst = ops + ((((size_t)tile * a.B + f) * 4 + kind) * a.nchunks + chunk) * (size_t)CHUNK_BYTES +
-                         (size_t)((m / 8) * 8 + kc) * 128 + (m % 8) * 16 + e16 * esize;
+                         (size_t)((m / 8) * cols + kc) * 128 + (m % 8) * 16 + e16 * esize;
     if (a.ab_format == 2) {
         uint32_t t;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
@@ -920,6 +941,8 @@ cudaError_t launch_herk_tc(const HerkArgs& a, cudaStream_t st) {
         }
         return cudaGetLastError();
     }
+    // the streaming-operand form reads full chunks only
+    if (a.last_kc >= 2 && a.last_kc < 8) return cudaErrorInvalidValue;
     const int units = a.ntp * a.groups;
     const int ctas = units < a.grid_ctas ? units : a.grid_ctas;
     if (a.ab_format == 2) {

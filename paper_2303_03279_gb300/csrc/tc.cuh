@@ -14,15 +14,18 @@ namespace fctc {
 using fcmbar::smem_u32;
 
 // Shared-memory matrix descriptor: K-major, no swizzle; LBO = 128 B (next core matrix
-// along K), SBO = 1024 B (next 8-row group), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+// along K), SBO = the stride between 8-row groups (1024 B for a full 128-byte K-chunk; a
+// shorter chunk of c core-matrix columns stores its 8-row groups c x 128 B apart),
+// descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sbo(uint32_t saddr, uint32_t sbo) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) { return smem_desc_sbo(saddr, 1024u); }
 
 // Instruction descriptor: D = F32, A/B format (F16 = 0, BF16 = 1, TF32 = 2), both K-major,
 // N >> 3 at bit 17, M >> 4 at bit 24.

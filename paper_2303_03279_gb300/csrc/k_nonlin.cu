@@ -126,8 +126,10 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
     // Chunks of NK trials of the bins fa .. fb - 1 in order; the copy of chunk c + 1
     // (cp.async, asynchronous) runs while chunk c is computed. For an even node count a
     // thread copies and converts node pairs (16 bytes per copy): pair lp of the two tiles'
-    // 32, trials kp0 + 4 q, each warp on one tile. For an odd node count: node l = tid % 64,
-    // trials tid / 64 + 2 q.
+    // 32, trials kp0 + 4 q, each warp on one tile; the ring is the session's own device
+    // allocation (256-byte aligned) and every (slot, bin) row starts at an even node offset,
+    // so each pair starts on 16 bytes. For an odd node count: node l = tid % 64, trials
+    // tid / 64 + 2 q.
     const bool pairs = (a.n & 1) == 0;
     const int lp = ((tid >> 5) & 1) * (FC_T / 2) + (tid & 15), kp0 = ((tid >> 6) << 1) | ((tid >> 4) & 1);
     const int l_node = pairs ? 2 * lp : tid & 63, kk0 = pairs ? kp0 : tid >> 6;

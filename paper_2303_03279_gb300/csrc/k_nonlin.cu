@@ -192,8 +192,10 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
 #pragma unroll
                 for (int q = 0; q < PER / 2; ++q) {
                     const int kk = kk0 + 4 * q;
-                    float4 X = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (kk < kn && node_ok) X = *reinterpret_cast<const float4*>(&sm.raw[kk][l_node]);
+                    if (kk >= kn) break;  // trials past the chunk are never read
+                    // a node past n is converted from whatever the buffer holds: its pairs are
+                    // masked out and never stored
+                    const float4 X = *reinterpret_cast<const float4*>(&sm.raw[kk][l_node]);
                     if (l_node < FC_T) {
                         sm.rowv[kk][l_node] = make_float4(X.x, X.x, X.y, X.y);
                         sm.rowv[kk][l_node + 1] = make_float4(X.z, X.z, X.w, X.w);

@@ -162,6 +162,18 @@ def test_mixed_window_odd_and_even_node_counts(n):
         _check(s, W)
 
 
+def test_mixed_window_longer_than_4096_trials():
+    """K = 4200 trials: beyond K = 4096 the non-linear sums form S and S^2 - K of PLI and USPLI
+    through integers instead of exactly in FP32 (the packed finalize's other branch), and the
+    products take the streaming-operand form (132 K-chunks). Against the oracle, signs exact."""
+    n, N, W = 40, 64, 4200
+    x = white_trials(31, W, n, N)
+    with fc.Session(n, N, 128.0, (8.0, 40.0, 64), "hann", fc.FC_SPECTRAL_METRICS, W,
+                    mode=fc.FC_MODE_FULL, precision=fc.FC_PREC_BF16) as s:
+        s.push(x)
+        _check(s, W)
+
+
 @pytest.mark.parametrize("prec", ["bf16", "tf32"])
 def test_mixed_bulk_then_single_pushes_and_band_change(prec):
     """The full-window operands are kept by ring slot: a bulk fill packs the whole window,

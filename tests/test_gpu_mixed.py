@@ -162,6 +162,37 @@ def test_mixed_window_odd_and_even_node_counts(n):
         _check(s, W)
 
 
+def test_mixed_degenerate_channels_and_single_trial():
+    """Degenerate inputs on the mixed path, against the oracle's conventions: a zero channel
+    (every metric 0 with it), an identical pair (COH and PLV 1 within the operand rounding;
+    Im of the exact FP32 terms is exactly 0, so PLI, WPLI and DSWPLI are exactly 0), and a
+    window of one trial (COH and PLV 1, USPLI undefined: NaN, DSWPLI 0 with at most one
+    nonzero term)."""
+    n, N, K = 36, 100, 5
+    x = white_trials(7, K, n, N)
+    x[:, 3] = 0.0
+    x[:, 7] = x[:, 11]
+    with fc.Session(n, N, 100.0, (1.0, 40.0, 128), "hann", fc.FC_SPECTRAL_METRICS, K,
+                    mode=fc.FC_MODE_FULL, precision=fc.FC_PREC_BF16) as s:
+        s.push(x)
+        _check(s, K)
+        nets = {m: s.network(m, packed=True)[0] for m in LINEAR + NONLINEAR}
+        zero = packed_index(3, np.arange(4, n), n)
+        for m in LINEAR + ("PLI", "WPLI", "DSWPLI"):
+            assert np.all(nets[m][zero] == 0.0), m
+        p = packed_index(7, 11, n)
+        assert abs(nets["COH"][p] - 1) < TOL_TC["bf16"] and abs(nets["PLV"][p] - 1) < TOL_TC["bf16"]
+        assert nets["PLI"][p] == 0 and nets["WPLI"][p] == 0 and nets["DSWPLI"][p] == 0
+    x1 = white_trials(6, 1, 2, 64)
+    with fc.Session(2, 64, 128.0, (2.0, 30.0, 64), "hann", fc.FC_SPECTRAL_METRICS, 4,
+                    mode=fc.FC_MODE_FULL, precision=fc.FC_PREC_BF16) as s:
+        s.push(x1[0])
+        nets = {m: s.network(m, packed=True)[0] for m in LINEAR + NONLINEAR}
+        assert abs(nets["COH"][0] - 1) < TOL_TC["bf16"] and abs(nets["PLV"][0] - 1) < TOL_TC["bf16"]
+        assert np.isnan(nets["USPLI"][0]) and nets["DSWPLI"][0] == 0
+        _check(s, 1)
+
+
 def test_mixed_window_longer_than_4096_trials():
     """K = 4200 trials: beyond K = 4096 the non-linear sums form S and S^2 - K of PLI and USPLI
     through integers instead of exactly in FP32 (the packed finalize's other branch), and the

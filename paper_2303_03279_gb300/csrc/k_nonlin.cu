@@ -10,17 +10,23 @@
 //
 // Sums. The signs are tallied as counts of positive and of negative terms in FP32 (exact
 // integers below 2^24 trials). Im, |Im| and Im^2 are summed in FP32 over chunks of NK
-// trials and each chunk's partial sums are added to double-word window sums, so the
-// debiased differences x^2 - s are evaluated from FP64-class sums with the exact square
-// of their leading word (df_sq_minus). Where at most one term of the window is nonzero
-// both differences are exactly 0 (sum_{k != l} of products), and DSWPLI is 0, as the
-// definition's zero denominator gives; the counts decide this exactly.
+// trials and each chunk's partial sums are added to double-word window sums; the debiased
+// differences x^2 - s are then evaluated in double words with the exact square of their
+// leading word (df_sq_minus). The FP32 chunk sums leave each of (sum Im)^2, (sum |Im|)^2
+// and sum Im^2 off by up to ~m u (sum |Im|)^2 (m <= NK terms per chunk, u = 2^-24), so
+// DSWPLI is off by up to ~6 m u (sum |Im|)^2 / ((sum |Im|)^2 - sum Im^2): small except
+// where one term dominates a short window. Where at most one term of the window is
+// nonzero both differences are exactly 0 (sum_{k != l} of products), and DSWPLI is 0, as
+// the definition's zero denominator gives; the counts decide this exactly.
 //
 // Accumulator mode (ACC): the window sums of each bin are stored into the streaming
 // accumulators (sum Im, sum |Im|, sum Im^2 as double words, the sign count) of the tile pairs
 // of a list; this is the drift re-sum of a mixed-precision streaming session, whose linear
-// sums come from the tensor cores. Its sums carry the chunked FP32 rounding (NK terms per
-// partial sum), well inside the operand rounding of those linear sums.
+// sums come from the tensor cores. Here every term is added exactly as the streaming update
+// adds it (Im, |Im| and the exact two-product of Im^2 into double words, renormalized every
+// chunk): the update later subtracts a trial's terms from these sums, and sums rounded to
+// FP32 would keep that trial's rounding (a residue of the size of the largest trial of the
+// re-summed window) after it has left.
 //
 // Work split: a CTA of 128 threads takes one 32 x 32 tile pair and a group of bins; each
 // thread holds a 2 x 4 register tile of pairs (rows 2 rg, 2 rg + 1; columns 4 cg .. 4 cg + 3),
@@ -256,9 +262,20 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
                                 pos[q] = add2(pos[q], make_float2(gt0(im.x), gt0(im.y)));
                                 neg[q] = add2(neg[q], make_float2(lt0(im.x), lt0(im.y)));
                             }
-                            pab[q] = make_float2(__fadd_rn(pab[q].x, fabsf(im.x)), __fadd_rn(pab[q].y, fabsf(im.y)));
-                            pim[q] = add2(pim[q], im);
-                            psq[q] = fma2(im, im, psq[q]);
+                            if constexpr (ACC) {
+                                // the streaming update's own terms, exactly: Im, |Im| and the
+                                // exact two-product of Im^2 into the double-word window sums
+                                acc2_f_lazy(imh[q], iml[q], im);
+                                acc2_f_lazy(abh[q], abl[q], make_float2(fabsf(im.x), fabsf(im.y)));
+                                float2 p2, e2;
+                                two_prod(im.x, im.x, p2.x, e2.x);
+                                two_prod(im.y, im.y, p2.y, e2.y);
+                                acc2_d_lazy(sqh[q], sql[q], p2, e2);
+                            } else {
+                                pab[q] = make_float2(__fadd_rn(pab[q].x, fabsf(im.x)), __fadd_rn(pab[q].y, fabsf(im.y)));
+                                pim[q] = add2(pim[q], im);
+                                psq[q] = fma2(im, im, psq[q]);
+                            }
                         }
                     }
                 }
@@ -267,13 +284,23 @@ __global__ void __launch_bounds__(NL_THREADS, 3) k_nonlin(PairArgs a) {
                 chunk(std::true_type{});
             else
                 chunk(std::false_type{});
-            // the chunk's partial sums into the double-word window sums (lazy: renormalized
-            // once per bin)
+            if constexpr (ACC) {
+                // per-term lazy sums: renormalized every chunk (at most NK terms each)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                acc2_f_lazy(imh[q], iml[q], pim[q]);
-                acc2_f_lazy(abh[q], abl[q], pab[q]);
-                acc2_f_lazy(sqh[q], sql[q], psq[q]);
+                for (int q = 0; q < 4; ++q) {
+                    renorm2(imh[q], iml[q]);
+                    renorm2(abh[q], abl[q]);
+                    renorm2(sqh[q], sql[q]);
+                }
+            } else {
+                // the chunk's partial sums into the double-word window sums (lazy:
+                // renormalized once per bin)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc2_f_lazy(imh[q], iml[q], pim[q]);
+                    acc2_f_lazy(abh[q], abl[q], pab[q]);
+                    acc2_f_lazy(sqh[q], sql[q], psq[q]);
+                }
             }
         }
         if (vmask) {

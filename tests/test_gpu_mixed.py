@@ -3,7 +3,8 @@
 COH, IMAGCOHY and PLV come from the tensor-core Hermitian products (tcgen05, BF16 / FP16
 / TF32 operands, FP32 accumulation): |gpu - oracle| <= 5e-3 absolute. PLI, USPLI, WPLI and
 DSWPLI come from the CUDA-core non-linear sums on the exact FP32 terms: 1e-5 relative,
-with the sign sums recovered exactly. The oracle runs on the GPU's own FP32 spectra, so
+with the sign sums recovered exactly; DSWPLI within the bound its FP32 chunk sums give
+(1e-5 plus 6 m u times the conditioning of its debiased differences, see _fc_helpers). The oracle runs on the GPU's own FP32 spectra, so
 the differences isolate the operand rounding of the contraction.
 """
 
@@ -12,7 +13,7 @@ import pytest
 
 import oracle as O
 from synth import eeg_sinusoid_trials, meg_pink_trials, white_trials
-from _fc_helpers import assert_close, window_spectra, packed_index
+from _fc_helpers import assert_close, assert_close_bound, dswpli_mixed_tolerance, window_spectra, packed_index
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -45,9 +46,13 @@ def _check(s, K, I=None, J=None, prec="bf16"):
         err = np.abs(got - ref[m])
         errs[m] = float(err.max())
         assert err.max() <= TOL_TC[prec], (m, prec, err.max())
+    dsw_tol = dswpli_mixed_tolerance(X, I, J)
     for m in NONLINEAR:
         got = s.network(m, packed=True)[0].astype(np.float64)[p]
-        assert_close(got, ref[m], what=f"{m} ({prec})")
+        if m == "DSWPLI":  # FP32 chunk sums: the bound grows with the debiasing's conditioning
+            assert_close_bound(got, ref[m], dsw_tol, what=f"{m} ({prec})")
+        else:
+            assert_close(got, ref[m], what=f"{m} ({prec})")
         errs[m] = float(np.abs(got - ref[m]).max())
     pli = s.network("PLI", packed=True)[0].astype(np.float64)[p]
     assert np.array_equal(np.rint(pli * K * s.B), np.rint(ref["PLI"] * K * s.B))
@@ -191,6 +196,19 @@ def test_mixed_degenerate_channels_and_single_trial():
         assert abs(nets["COH"][0] - 1) < TOL_TC["bf16"] and abs(nets["PLV"][0] - 1) < TOL_TC["bf16"]
         assert np.isnan(nets["USPLI"][0]) and nets["DSWPLI"][0] == 0
         _check(s, 1)
+
+
+def test_mixed_window_of_two_trials():
+    """W = 2, the worst-conditioned debiasing: DSWPLI of a window of two trials is
+    2 Im_1 Im_2 / (2 |Im_1| |Im_2|), formed from sums of squares; held to the bound that the
+    FP32 chunk sums give (see dswpli_mixed_tolerance), the other metrics as elsewhere."""
+    n, N, W = 137, 128, 2
+    x = white_trials(75, 6, n, N)
+    with fc.Session(n, N, 256.0, (4.0, 60.0, 128), "hann", fc.FC_SPECTRAL_METRICS, W,
+                    mode=fc.FC_MODE_FULL, precision=fc.FC_PREC_BF16) as s:
+        for t in range(6):
+            s.push(x[t])
+            _check(s, min(t + 1, W))
 
 
 def test_mixed_window_longer_than_4096_trials():

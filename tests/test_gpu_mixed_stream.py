@@ -9,7 +9,8 @@ partial sums of at most 36 trials added into double words; exact signs). After a
 and PLV carry the operand rounding of the tensor cores; IMAGCOHY (from sum Im), PLI, USPLI,
 WPLI and DSWPLI are sums of the exact FP32 terms. Against the oracle on the window's GPU spectra (Supplementary
 Information 1): COH and PLV within 5e-3 absolute, the other metrics within 1e-5 with exact
-sign sums, through bulk fills, single pushes and more than two re-sum periods; served
+sign sums (the re-sum adds the non-linear terms exactly as the update does, so a trial that
+leaves the window leaves no rounding residue behind), through bulk fills, single pushes and more than two re-sum periods; served
 sessions give the same networks alone and in the mix.
 """
 
@@ -71,6 +72,25 @@ def test_mixed_stream_against_oracle(prec):
                 nets = {m: s.network(m, packed=True)[0] for m in SPECTRAL}
                 errs = _check(nets, window_spectra(s, W), W, B, f"{prec} push {t}")
         print(f"[{prec}] max |gpu - oracle| of the tensor-core metrics:", {k: f"{v:.1e}" for k, v in errs.items()})
+
+
+def test_mixed_stream_odd_nodes_shortest_window():
+    """137 nodes (odd: the non-linear re-sum stages one node per copy; a ragged last 32-node
+    and 128-node tile) with the shortest sliding window that re-sums, W = 2 (3 ring slots):
+    single pushes from the start, through 3 re-sum periods, against the oracle. With two
+    trials a window's debiased differences are as ill-conditioned as they get, so a re-sum
+    that rounded its sums would leave residues that the strict tolerance catches."""
+    n, N, W, T = 137, 128, 2, 9
+    x = white_trials(73, T, n, N)
+    with fc.Session(n, N, 256.0, (4.0, 60.0, 128), "hann", fc.FC_SPECTRAL_METRICS, W,
+                    mode=fc.FC_MODE_STREAM, precision=fc.FC_PREC_BF16) as s:
+        B = s.B
+        for t in range(T):
+            s.push(x[t])
+            if t in (0, 1, 4, T - 1):
+                K = min(t + 1, W)
+                nets = {m: s.network(m, packed=True)[0] for m in SPECTRAL}
+                _check(nets, window_spectra(s, K), K, B, f"push {t}")
 
 
 def test_mixed_stream_slice_covers_every_block():

@@ -750,6 +750,7 @@ def run_ours(args, w, wname):
     plain = None
     mixed = None
     mixed_stream = None
+    mixed_stream_split = None
     if not args.no_plain:
         ps = fc.Session(n, N, w["fs"], B_band, "hann", mask, W, mode=fc.FC_MODE_FULL, stream=stream.cuda_stream)
         fc.fc_push_trials(ps.handle, dev[:W].contiguous(), W)
@@ -815,42 +816,48 @@ def run_ours(args, w, wname):
         ms.close()
         del ms
         # mixed-precision streaming: the exact streaming update, drift re-sum slices with the
-        # linear sums on the tensor cores (BF16 operand ring)
-        torch.cuda.synchronize()
-        ss = fc.Session(n, N, w["fs"], B_band, "hann", mask, W, mode=fc.FC_MODE_STREAM, precision=fc.FC_PREC_BF16,
-                        stream=stream.cuda_stream)
-        fc.fc_push_trials(ss.handle, dev[:W].contiguous(), W)
-        for k in range(warmup):
-            fc.fc_push_trial(ss.handle, trial(W + k))
-        fc.fc_sync(ss.handle)
-        fc.fc_set_profiling(ss.handle, True)
-        fc.fc_kernel_times(ss.handle, reset=True)
-        sst = max(3, steps)
-        sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(sst)]
-        for k in range(sst):
-            sev[k][0].record(stream)
-            fc.fc_push_trial(ss.handle, trial(W + warmup + k))
-            sev[k][1].record(stream)
-        torch.cuda.synchronize()
-        skt = fc.fc_kernel_times(ss.handle, reset=True)
-        sl = sorted(a.elapsed_time(b) for a, b in sev)
-        sms_ = sum(sl) / len(sl)
-        kms = {k: v[1] / sst for k, v in skt.items() if v[0]}
-        mixed_stream = {"value": world * units / (sms_ / 1000.0), "unit": UNIT, "ms_per_step": sms_,
-                        "latency_ms": {"p50": sl[len(sl) // 2], "p99": sl[-1]}, "steps": sst,
-                        "path": "exact streaming update (FP32 terms, double-float sums); drift re-sum slice: "
-                                "tcgen05 BF16 linear sums over the operand ring + CUDA-core non-linear sums (exact "
-                                "signs; FP32 partial sums of <= 36 trials into double words)",
-                        "kernels_ms_per_push": {k: round(v, 4) for k, v in kms.items()},
-                        "tensor_core_share_of_push": kms.get("herk_tc", 0.0) / sms_,
-                        # the slice's non-linear sums run beside the update on a side stream: their
-                        # event times include waiting for SMs, so the push time beyond the update is
-                        # what the re-sum costs
-                        "push_beyond_update_ms": sms_ - kms.get("stream", 0.0),
-                        "side_stream_note": "window: the slice's non-linear sums, timed on the side "
-                                            "stream from the fork (includes waiting for the update's SMs)"}
-        ss.close()
-        del ss
+        # linear sums on the tensor cores (BF16 operand ring; split TF32: high and low parts)
+        for key, sprec, label in (("bf16", fc.FC_PREC_BF16, "BF16"),
+                                  ("tf32x3", fc.FC_PREC_TF32X3, "split-TF32 (hi hi + hi lo + lo hi)")):
+            torch.cuda.synchronize()
+            ss = fc.Session(n, N, w["fs"], B_band, "hann", mask, W, mode=fc.FC_MODE_STREAM, precision=sprec,
+                            stream=stream.cuda_stream)
+            fc.fc_push_trials(ss.handle, dev[:W].contiguous(), W)
+            for k in range(warmup):
+                fc.fc_push_trial(ss.handle, trial(W + k))
+            fc.fc_sync(ss.handle)
+            fc.fc_set_profiling(ss.handle, True)
+            fc.fc_kernel_times(ss.handle, reset=True)
+            sst = max(3, steps)
+            sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(sst)]
+            for k in range(sst):
+                sev[k][0].record(stream)
+                fc.fc_push_trial(ss.handle, trial(W + warmup + k))
+                sev[k][1].record(stream)
+            torch.cuda.synchronize()
+            skt = fc.fc_kernel_times(ss.handle, reset=True)
+            sl = sorted(a.elapsed_time(b) for a, b in sev)
+            sms_ = sum(sl) / len(sl)
+            kms = {k: v[1] / sst for k, v in skt.items() if v[0]}
+            leg = {"value": world * units / (sms_ / 1000.0), "unit": UNIT, "ms_per_step": sms_,
+                   "latency_ms": {"p50": sl[len(sl) // 2], "p99": sl[-1]}, "steps": sst,
+                   "path": f"exact streaming update (FP32 terms, double-float sums); drift re-sum slice: "
+                           f"tcgen05 {label} linear sums over the operand ring + CUDA-core non-linear sums "
+                           f"(exact signs; the update's own terms added exactly into double words)",
+                   "kernels_ms_per_push": {k: round(v, 4) for k, v in kms.items()},
+                   "tensor_core_share_of_push": kms.get("herk_tc", 0.0) / sms_,
+                   # the slice's non-linear sums run beside the update on a side stream: their
+                   # event times include waiting for SMs, so the push time beyond the update is
+                   # what the re-sum costs
+                   "push_beyond_update_ms": sms_ - kms.get("stream", 0.0),
+                   "side_stream_note": "window: the slice's non-linear sums, timed on the side "
+                                       "stream from the fork (includes waiting for the update's SMs)"}
+            if key == "bf16":
+                mixed_stream = leg
+            else:
+                mixed_stream_split = leg
+            ss.close()
+            del ss
 
     # serving: many concurrent sessions, continuous batching vs plain FP32 one trial at a time
     serving = None
@@ -920,6 +927,7 @@ def run_ours(args, w, wname):
                    "parallelism": f"{world} independent session(s), one per GPU"},
         "latency_ms": {"p50": p50, "p99": p99, "what": "device time from push enqueue to network ready"},
         "plain_fp32": plain, "mixed_bf16_full_window": mixed, "mixed_bf16_stream": mixed_stream,
+        "mixed_tf32x3_stream": mixed_stream_split,
         "serving": serving, "configs": configs,
         "roofline": roofline, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
         "clocks": clocks.summary(), "gpu_launches": launches,

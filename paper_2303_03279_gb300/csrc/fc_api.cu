@@ -1028,9 +1028,10 @@ size_t fc_plan_session_bytes(int n, int N, int B, int W, uint32_t mask, fc_mode 
         if (mode == FC_MODE_STREAM && prec != FC_PREC_FP32) {
             // operand ring, 128-node tile lists, the 32-in-128 tile-pair list, tiny-node flags
             const size_t nt128 = (n + 127) / 128, ntp128 = nt128 * (nt128 + 1) / 2;
-            const size_t per_chunk = prec == FC_PREC_TF32 ? 32 : 64;
+            const size_t per_chunk = (prec == FC_PREC_TF32 || prec == FC_PREC_TF32X3) ? 32 : 64;
             const size_t nchunks = (2 * slots + per_chunk - 1) / per_chunk;
-            b += nt128 * B * 4 * nchunks * herk_chunk_bytes() + ntp128 * 4 + ntp * 4 + (size_t)B * n;
+            const size_t kinds = prec == FC_PREC_TF32X3 ? 8 : 4;  // split TF32: high and low parts
+            b += nt128 * B * kinds * nchunks * herk_chunk_bytes() + ntp128 * 4 + ntp * 4 + (size_t)B * n;
             // re-sum scratch: at most 16 32-node tile pairs per 128-node tile pair of a slice
             b += (ntp128 + W - 1) / W * 16 * B * FC_BLOCK_WORDS * 4;
         }
@@ -1096,7 +1097,9 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
     if (window < 0) return fail(FC_ERR_INVALID_ARG, "window must be >= 0");
     if (cfg.mode != FC_MODE_STREAM && cfg.mode != FC_MODE_FULL) return fail(FC_ERR_INVALID_ARG, "bad mode");
     if (cfg.mode == FC_MODE_FULL && window < 1) return fail(FC_ERR_INVALID_ARG, "full mode needs window >= 1");
-    if (cfg.precision < FC_PREC_FP32 || cfg.precision > FC_PREC_FP16) return fail(FC_ERR_INVALID_ARG, "bad precision");
+    if (cfg.precision < FC_PREC_FP32 || cfg.precision > FC_PREC_TF32X3) return fail(FC_ERR_INVALID_ARG, "bad precision");
+    if (cfg.precision == FC_PREC_TF32X3 && cfg.mode == FC_MODE_FULL)
+        return fail(FC_ERR_UNSUPPORTED, "split TF32 applies to the drift re-sum of a streaming session");
     if (cfg.spectrum < FC_SPECTRUM_AUTO || cfg.spectrum > FC_SPECTRUM_FFT) return fail(FC_ERR_INVALID_ARG, "bad spectrum method");
     if (cfg.spectrum == FC_SPECTRUM_FFT && !fc_fft_size_ok(band.nfft))
         return fail(FC_ERR_UNSUPPORTED,
@@ -1241,8 +1244,10 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
             // mixed-precision streaming: the drift re-sum takes the linear sums from the tensor
             // cores over an operand ring of the window (inner dimension 2 (W + 1): ring slots)
             s->mixed_stream = true;
-            s->ab_format = cfg.precision == FC_PREC_BF16 ? 1 : (cfg.precision == FC_PREC_FP16 ? 0 : 2);
-            const int per_chunk = s->ab_format == 2 ? 32 : 64;
+            s->ab_format = cfg.precision == FC_PREC_BF16 ? 1
+                           : cfg.precision == FC_PREC_FP16 ? 0
+                           : cfg.precision == FC_PREC_TF32X3 ? 3 : 2;
+            const int per_chunk = s->ab_format >= 2 ? 32 : 64;
             s->nchunks = (2 * s->slots + per_chunk - 1) / per_chunk;
             s->nt128 = (n_nodes + 127) / 128;
             s->ntp128 = s->nt128 * (s->nt128 + 1) / 2;
@@ -1265,7 +1270,8 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
             TRY(upload(s, s->tile_b128, tb.data(), tb.size() * sizeof(unsigned short)));
             TRY(alloc_zero(s, l32.size(), &s->list32));
             TRY(upload(s, s->list32, l32.data(), l32.size() * sizeof(int)));
-            TRY(alloc_zero(s, (size_t)s->nt128 * B * 4 * s->nchunks * herk_chunk_bytes(), &s->ops));
+            const size_t kinds = s->ab_format == 3 ? 8 : 4;  // split TF32: high and low parts
+            TRY(alloc_zero(s, (size_t)s->nt128 * B * kinds * s->nchunks * herk_chunk_bytes(), &s->ops));
             TRY(alloc_zero(s, (size_t)B * n_nodes, &s->tiny_flags));
             // the non-linear re-sum of one push beside the update: its 32-node tile pairs (at
             // most those inside one slice of 128-node tile pairs), all bins

@@ -133,7 +133,7 @@ struct fc_session {
     int last_kc = 8;        // core-matrix columns of the last operand K-chunk (see PackArgs)
     unsigned short* tile_a128;
     unsigned short* tile_b128;
-    unsigned char* ops;     // packed operands [nt128][B][4][nchunks][16 KB]
+    unsigned char* ops;     // packed operands [nt128][B][4 kinds, 8 for split TF32][nchunks][16 KB]
     unsigned char* tiny_flags;  // [B][n] a trial of the window has a tiny component (mixed path)
     bool mixed_stream;      // streaming session whose re-sum takes the linear sums from the tensor cores
     int* list32;            // mixed streaming: 32-node tile pairs grouped by 128-node tile pair
@@ -276,9 +276,9 @@ cudaError_t launch_bins_window(const PairArgs& a, int metric_index, float* out, 
 // Tensor-core full-window linear sums (k_herk_tc.cu).
 struct PackArgs {
     const float2* ring;
-    unsigned char* ops;   // [tiles128][B][4 kinds][nchunks][16 KB]
+    unsigned char* ops;   // [tiles128][B][4 kinds, 8 for split TF32 (ab_format 3)][nchunks][16 KB]
     int n, B, W, slots, ntiles, nchunks, count;
-    int ab_format;        // 0 = FP16, 1 = BF16, 2 = TF32
+    int ab_format;        // 0 = FP16, 1 = BF16, 2 = TF32, 3 = split TF32 (high + low parts)
     const FcCtrl* ctrl;
     int ring_order;       // full pack: inner positions by ring slot (s, slots + s) instead of by
                           // window order (k, K + k); slots outside the window hold zeros

@@ -421,7 +421,7 @@ fc_status fc_server_create(const fc_server_config* cfg, fc_server** out) {
         delete sv;
         return sfail(FC_ERR_INVALID_ARG, "max_batch must be 0..32");
     }
-    if (sv->cfg.precision < FC_PREC_FP32 || sv->cfg.precision > FC_PREC_FP16) {
+    if (sv->cfg.precision < FC_PREC_FP32 || sv->cfg.precision > FC_PREC_TF32X3) {
         delete sv;
         return sfail(FC_ERR_INVALID_ARG, "bad precision");
     }

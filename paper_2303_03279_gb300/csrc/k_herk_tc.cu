@@ -56,8 +56,12 @@ __device__ __forceinline__ long long packed_index(int i, int j, int n) {
     return (long long)i * n - (long long)i * (i + 1) / 2 + (j - i - 1);
 }
 
+// Operand kinds per (tile, bin): XR, XI, UR, UI; split TF32 (ab_format 3) adds their
+// low parts as kinds 4 .. 7.
+__device__ __forceinline__ int op_kinds(int ab_format) { return ab_format == 3 ? 8 : 4; }
+
 __device__ __forceinline__ const unsigned char* op_block(const HerkArgs& a, int tile, int f, int kind, int chunk) {
-    return a.ops + ((((size_t)tile * a.B + f) * 4 + kind) * a.nchunks + chunk) * (size_t)CHUNK_BYTES;
+    return a.ops + ((((size_t)tile * a.B + f) * op_kinds(a.ab_format) + kind) * a.nchunks + chunk) * (size_t)CHUNK_BYTES;
 }
 
 // Core-matrix columns stored in K-chunk ch of a pack with last_kc (the short layout of the
@@ -91,20 +95,32 @@ __device__ __forceinline__ void seq_next_bin(const HerkArgs& a, HerkSeq& s) {
 // issues the MMAs; warps 0-7 drain TMEM, two per lane quarter, each over half of the row
 // nodes). Every wait is bounded; a timeout is recorded in
 // the control block.
-template <int KIND>
+// SPLIT (split TF32, KIND 1): each operand is a TF32 high part and a TF32 low part (the
+// rounding residue); a stage holds both (six blocks), and each K step issues three MMAs,
+// hi x hi + hi x lo + lo x hi, so the products keep FP32-class accuracy (the dropped lo x lo
+// term and the low part's own rounding are ~2^-22 of the product).
+template <bool SPLIT>
+struct HerkStages {
+    static constexpr int NST = SPLIT ? 2 : NSTAGE;                       // stages in flight
+    static constexpr int SB = (SPLIT ? 2 : 1) * STAGE_BYTES;             // bytes per stage
+    static constexpr int SMEM = NST * SB + 512 + EPI_WARPS * 512;
+};
+
+template <int KIND, bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
+    constexpr int NST = HerkStages<SPLIT>::NST, SB = HerkStages<SPLIT>::SB;
     extern __shared__ __align__(1024) unsigned char smem[];
     FcCtrl* c = const_cast<FcCtrl*>(a.ctrl);
     if (c->bad) return;
     const int units = a.ntp * a.groups;
     if ((int)blockIdx.x >= units) return;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);  // [NSTAGE]
-    uint64_t* freeb = full + NSTAGE;                                             // [NSTAGE]
-    uint64_t* accf = freeb + NSTAGE;                                             // [2] MMAs -> epilogue
-    uint64_t* acce = accf + 2;                                                   // [2] epilogue -> MMAs
-    uint64_t* drain = acce + 2;                                                  // [1]
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * SB);  // [NST]
+    uint64_t* freeb = full + NST;                                    // [NST]
+    uint64_t* accf = freeb + NST;                                    // [2] MMAs -> epilogue
+    uint64_t* acce = accf + 2;                                       // [2] epilogue -> MMAs
+    uint64_t* drain = acce + 2;                                      // [1]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
-    float* sinv_all = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES + 512);  // [EPI_WARPS][128]
+    float* sinv_all = reinterpret_cast<float*>(smem + NST * SB + 512);  // [EPI_WARPS][128]
     const int tid = threadIdx.x, warp = tid >> 5;
 
     if (warp == 0) {
@@ -114,7 +130,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int s = 0; s < NSTAGE; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&freeb[s], 1);
         }
@@ -149,17 +165,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
             // 256-row operand and writes both accumulators (TMEM columns 0-127 and 128-255)
             const uint32_t idesc = make_idesc(KIND == 1 ? 2u : (a.ab_format == 1 ? 1u : 0u), TILE, 2 * TILE);
             const long long nchunk_total = (long long)nphase * a.nchunks;
-            uint32_t full_ph[NSTAGE], free_ph[NSTAGE];
-            for (int s = 0; s < NSTAGE; ++s) full_ph[s] = free_ph[s] = 0;
+            uint32_t full_ph[NST], free_ph[NST];
+            for (int s = 0; s < NST; ++s) full_ph[s] = free_ph[s] = 0;
             uint32_t acce_ph[2] = {0, 0};
             long long loads = 0;
             HerkSeq ls;  // unit and bin of the phase being loaded
             seq_unit(a, ls, (int)blockIdx.x);
             long long lph = 0;
-            auto issue_load = [&]() {  // chunk `loads` of the sequence into stage loads % NSTAGE
+            auto issue_load = [&]() {  // chunk `loads` of the sequence into stage loads % NST
                 if (loads >= nchunk_total) return;
-                const int st = (int)(loads % NSTAGE);
-                if (loads >= NSTAGE) {  // the MMAs of the chunk that used this stage have read it
+                const int st = (int)(loads % NST);
+                if (loads >= NST) {  // the MMAs of the chunk that used this stage have read it
                     if (!mbar_wait_bounded(&freeb[st], free_ph[st])) failed = true;
                     free_ph[st] ^= 1;
                 }
@@ -170,14 +186,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
                 const int tp = a.tp0 + ls.u / a.groups, f = ls.f;
                 const int ta = a.tile_a[tp], tb = a.tile_b[tp];
                 const int k0 = (ph & 1) ? 2 : 0;  // phase A: X operands, phase B: U operands
-                unsigned char* dst = smem + st * STAGE_BYTES;
-                mbar_expect_tx(&full[st], STAGE_BYTES);
+                unsigned char* dst = smem + st * SB;
+                mbar_expect_tx(&full[st], SB);
                 bulk_g2s(dst + 0 * CHUNK_BYTES, op_block(a, tb, f, k0, ch), CHUNK_BYTES, &full[st]);
                 bulk_g2s(dst + 1 * CHUNK_BYTES, op_block(a, ta, f, k0, ch), CHUNK_BYTES, &full[st]);
                 bulk_g2s(dst + 2 * CHUNK_BYTES, op_block(a, ta, f, k0 + 1, ch), CHUNK_BYTES, &full[st]);
+                if constexpr (SPLIT) {  // the low parts, in the same order
+                    bulk_g2s(dst + 3 * CHUNK_BYTES, op_block(a, tb, f, k0 + 4, ch), CHUNK_BYTES, &full[st]);
+                    bulk_g2s(dst + 4 * CHUNK_BYTES, op_block(a, ta, f, k0 + 4, ch), CHUNK_BYTES, &full[st]);
+                    bulk_g2s(dst + 5 * CHUNK_BYTES, op_block(a, ta, f, k0 + 5, ch), CHUNK_BYTES, &full[st]);
+                }
                 ++loads;
             };
-            for (int s = 0; s < NSTAGE - 1; ++s) issue_load();
+            for (int s = 0; s < NST - 1; ++s) issue_load();
             long long consumed = 0;
             for (int ph = 0; ph < nphase && !failed; ++ph) {
                 const int b = ph & 1;
@@ -191,14 +212,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
                 }
                 const uint32_t d = tmem + (uint32_t)(b * 2 * TILE);
                 for (int ch = 0; ch < a.nchunks; ++ch) {
-                    const int st = (int)(consumed % NSTAGE);
+                    const int st = (int)(consumed % NST);
                     if (!mbar_wait_bounded(&full[st], full_ph[st])) {
                         failed = true;
                         break;
                     }
                     full_ph[st] ^= 1;
                     fence_after();
-                    const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
+                    const uint32_t base = smem_u32(smem + st * SB);
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
                         const uint32_t acc = (ch > 0 || ks > 0) ? 1u : 0u;
@@ -206,6 +227,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
                         const uint64_t d_b = smem_desc(base + 0 * CHUNK_BYTES + off);   // XR_b or UR_b
                         const uint64_t d_a2 = smem_desc(base + 1 * CHUNK_BYTES + off);  // [XR_a; XI_a] or [UR_a; UI_a]
                         mma<KIND>(d, d_b, d_a2, idesc, acc);
+                        if constexpr (SPLIT) {
+                            const uint64_t d_bl = smem_desc(base + 3 * CHUNK_BYTES + off);
+                            const uint64_t d_a2l = smem_desc(base + 4 * CHUNK_BYTES + off);
+                            mma<KIND>(d, d_b, d_a2l, idesc, 1u);   // hi x lo
+                            mma<KIND>(d, d_bl, d_a2, idesc, 1u);   // lo x hi
+                        }
                     }
                     mma_commit(&freeb[st]);  // the stage may be refilled once these MMAs have read it
                     ++consumed;
@@ -218,7 +245,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_herk_tc(HerkArgs a) {
             mma_commit(drain);
             mbar_wait_bounded(drain, 0);
             for (long long l = consumed; l < loads; ++l) {
-                const int st = (int)(l % NSTAGE);
+                const int st = (int)(l % NST);
                 mbar_wait_bounded(&full[st], full_ph[st]);
                 full_ph[st] ^= 1;
             }
@@ -759,10 +786,19 @@ __device__ __forceinline__ float2 phasor_of_x(float2 X) {
     return make_float2(__fmul_rn(X.x, r), __fmul_rn(X.y, r));
 }
 
-__device__ __forceinline__ uint4 pack_chunk(const float (&v)[8], int per16, int ab_format) {
-    if (ab_format == 2) {  // TF32: round to nearest (ties away), stored in 32-bit words
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t t;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
+    return t;
+}
+// Split TF32: x = hi + lo with hi = tf32(x) and lo = tf32(x - hi) (x - hi is exact in FP32).
+__device__ __forceinline__ float tf32_low(float x) { return __fsub_rn(x, __uint_as_float(tf32_bits(x))); }
+
+// low = true: the low parts of a split-TF32 operand (ab_format 3).
+__device__ __forceinline__ uint4 pack_chunk(const float (&v)[8], int per16, int ab_format, bool low = false) {
+    if (ab_format >= 2) {  // TF32: round to nearest (ties away), stored in 32-bit words
         uint32_t t[4];
-        for (int q = 0; q < 4; ++q) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t[q]) : "f"(v[q]));
+        for (int q = 0; q < 4; ++q) t[q] = tf32_bits(low ? tf32_low(v[q]) : v[q]);
         return make_uint4(t[0], t[1], t[2], t[3]);
     }
     unsigned short h[8];
@@ -786,7 +822,7 @@ __global__ void k_pack_operands(PackArgs a) {
     const long long start = (a.W > 0 && end > a.W) ? end - a.W : 0;
     const int K = (int)(end - start);
     const int slot0 = (int)(start % a.slots);  // ring slot of the window's first trial
-    const int esize = a.ab_format == 2 ? 4 : 2;
+    const int esize = a.ab_format >= 2 ? 4 : 2;
     const int per16 = 16 / esize;                 // elements per 16-byte unit
     // unit e = (block index (tile, bin, chunk)) * 1024 + (m8 * 8 + kc) * 8 + r: the low ten
     // bits give the place in the block, the block index is split with 32-bit arithmetic
@@ -834,11 +870,13 @@ __global__ void k_pack_operands(PackArgs a) {
                 v[3][q] = part ? -u.x : u.y;  // UI
             }
         }
+        const int nk = op_kinds(a.ab_format);
 #pragma unroll
-        for (int kind = 0; kind < 4; ++kind) {
-            unsigned char* dst = a.ops + ((((size_t)tile * a.B + f) * 4 + kind) * a.nchunks + ch) * (size_t)CHUNK_BYTES +
+        for (int kind = 0; kind < 8; ++kind) {
+            if (kind >= nk) break;
+            unsigned char* dst = a.ops + ((((size_t)tile * a.B + f) * nk + kind) * a.nchunks + ch) * (size_t)CHUNK_BYTES +
                                  (size_t)((m8 * cols + kc) * 8 + r) * 16;
-            *reinterpret_cast<uint4*>(dst) = pack_chunk(v[kind], per16, a.ab_format);
+            *reinterpret_cast<uint4*>(dst) = pack_chunk(v[kind & 3], per16, a.ab_format, kind >= 4);
         }
     }
 }
@@ -849,16 +887,19 @@ __global__ void k_pack_operands(PackArgs a) {
 // bin, node) writes that element of all four kinds; slots outside the window hold zeros.
 __device__ __forceinline__ void put_elem(unsigned char* ops, const PackArgs& a, int tile, int f, int kind, int m,
                                          int k, float v) {
-    const int esize = a.ab_format == 2 ? 4 : 2;
+    const int esize = a.ab_format >= 2 ? 4 : 2;
     const int per16 = 16 / esize;
     const int chunk = k / (8 * per16), kc = (k / per16) % 8, e16 = k % per16;
     const int cols = chunk_cols(a.last_kc, chunk, a.nchunks);  // kc < cols for every stored k
-    unsigned char* dst = ops + ((((size_t)tile * a.B + f) * 4 + kind) * a.nchunks + chunk) * (size_t)CHUNK_BYTES +
+    const int nk = op_kinds(a.ab_format);
+    unsigned char* dst = ops + ((((size_t)tile * a.B + f) * nk + kind) * a.nchunks + chunk) * (size_t)CHUNK_BYTES +
                          (size_t)((m / 8) * cols + kc) * 128 + (m % 8) * 16 + e16 * esize;
-    if (a.ab_format == 2) {
-        uint32_t t;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
-        *reinterpret_cast<uint32_t*>(dst) = t;
+    if (a.ab_format == 3) {  // split TF32: the high part here, the low part in kind + 4
+        *reinterpret_cast<uint32_t*>(dst) = tf32_bits(v);
+        unsigned char* dl = dst + (size_t)4 * a.nchunks * CHUNK_BYTES;
+        *reinterpret_cast<uint32_t*>(dl) = tf32_bits(tf32_low(v));
+    } else if (a.ab_format == 2) {
+        *reinterpret_cast<uint32_t*>(dst) = tf32_bits(v);
     } else if (a.ab_format == 1) {
         *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
     } else {
@@ -927,7 +968,8 @@ cudaError_t launch_pack_operands(const PackArgs& a, cudaStream_t st) {
 
 cudaError_t launch_herk_tc(const HerkArgs& a, cudaStream_t st) {
     cudaError_t e;
-    if (a.seg_a && a.nchunks <= RC_MAX) {  // resident-operand form
+    if (a.seg_a && a.nchunks <= RC_MAX) {  // resident-operand form (never split TF32)
+        if (a.ab_format == 3) return cudaErrorInvalidValue;
         const int items = 2 * a.groups * a.nseg;
         const int ctas = items < a.grid_ctas ? items : a.grid_ctas;
         if (a.ab_format == 2) {
@@ -945,14 +987,21 @@ cudaError_t launch_herk_tc(const HerkArgs& a, cudaStream_t st) {
     if (a.last_kc >= 2 && a.last_kc < 8) return cudaErrorInvalidValue;
     const int units = a.ntp * a.groups;
     const int ctas = units < a.grid_ctas ? units : a.grid_ctas;
-    if (a.ab_format == 2) {
-        e = cudaFuncSetAttribute(k_herk_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (a.ab_format == 3) {
+        constexpr int sm = HerkStages<true>::SMEM;
+        e = cudaFuncSetAttribute(k_herk_tc<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return e;
-        k_herk_tc<1><<<ctas, THREADS, SMEM_BYTES, st>>>(a);
+        k_herk_tc<1, true><<<ctas, THREADS, sm, st>>>(a);
+    } else if (a.ab_format == 2) {
+        constexpr int sm = HerkStages<false>::SMEM;
+        e = cudaFuncSetAttribute(k_herk_tc<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e != cudaSuccess) return e;
+        k_herk_tc<1, false><<<ctas, THREADS, sm, st>>>(a);
     } else {
-        e = cudaFuncSetAttribute(k_herk_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        constexpr int sm = HerkStages<false>::SMEM;
+        e = cudaFuncSetAttribute(k_herk_tc<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return e;
-        k_herk_tc<0><<<ctas, THREADS, SMEM_BYTES, st>>>(a);
+        k_herk_tc<0, false><<<ctas, THREADS, sm, st>>>(a);
     }
     return cudaGetLastError();
 }

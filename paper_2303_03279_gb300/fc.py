@@ -35,7 +35,7 @@ METRIC_BITS = {"COR": FC_COR, "XCOR": FC_XCOR, "COH": FC_COH, "IMAGCOHY": FC_IMA
 
 FC_TAPER_NONE, FC_TAPER_HANN, FC_TAPER_HANN_SYM = 0, 1, 2
 TAPERS = {"none": 0, "hann": 1, "hann_sym": 2}
-FC_PREC_FP32, FC_PREC_TF32, FC_PREC_BF16, FC_PREC_FP16 = 0, 1, 2, 3
+FC_PREC_FP32, FC_PREC_TF32, FC_PREC_BF16, FC_PREC_FP16, FC_PREC_TF32X3 = 0, 1, 2, 3, 4
 FC_MODE_STREAM, FC_MODE_FULL = 0, 1
 FC_SPECTRUM_AUTO, FC_SPECTRUM_DFT, FC_SPECTRUM_FFT = 0, 1, 2
 

@@ -28,7 +28,7 @@ from paper_2303_03279_gb300 import fc  # noqa: E402
 
 SPECTRAL = ("COH", "IMAGCOHY", "PLV", "PLI", "USPLI", "WPLI", "DSWPLI")
 TENSOR = ("COH", "PLV")
-PRECISIONS = {"bf16": fc.FC_PREC_BF16, "tf32": fc.FC_PREC_TF32}
+PRECISIONS = {"bf16": fc.FC_PREC_BF16, "tf32": fc.FC_PREC_TF32, "tf32x3": fc.FC_PREC_TF32X3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -38,12 +38,15 @@ def _need_gpu():
     fc.load()
 
 
-def _check(nets, X, K, B, what):
+def _check(nets, X, K, B, what, prec="bf16"):
     ref = oracle_spectral(X.astype(np.complex128))
     errs = {}
     for m in SPECTRAL:
         got = nets[m].astype(np.float64)
-        if m in TENSOR:
+        if m in TENSOR and prec == "tf32x3":  # split TF32: FP32-class products
+            assert_close(got, ref[m], what=f"{what} {m}")
+            errs[m] = float(np.nanmax(np.abs(got - ref[m])))
+        elif m in TENSOR:
             err = np.nanmax(np.abs(got - ref[m]))
             assert err <= 5e-3, (what, m, err)
             errs[m] = err
@@ -70,8 +73,20 @@ def test_mixed_stream_against_oracle(prec):
             s.push(x[t])
             if t in (W, W + 5, T - 1):
                 nets = {m: s.network(m, packed=True)[0] for m in SPECTRAL}
-                errs = _check(nets, window_spectra(s, W), W, B, f"{prec} push {t}")
+                errs = _check(nets, window_spectra(s, W), W, B, f"{prec} push {t}", prec)
         print(f"[{prec}] max |gpu - oracle| of the tensor-core metrics:", {k: f"{v:.1e}" for k, v in errs.items()})
+
+
+def test_split_tf32_is_a_streaming_precision():
+    """Split TF32 serves the drift re-sum of a sliding streaming window; a full-window session
+    asking for it is refused."""
+    with pytest.raises(fc.FcError) as e:
+        fc.Session(40, 64, 128.0, (4.0, 40.0, 64), "hann", fc.FC_SPECTRAL_METRICS, 4,
+                   mode=fc.FC_MODE_FULL, precision=fc.FC_PREC_TF32X3)
+    assert e.value.status == fc.FC_ERR_UNSUPPORTED
+    with fc.Session(40, 64, 128.0, (4.0, 40.0, 64), "hann", fc.FC_SPECTRAL_METRICS, 4,
+                    mode=fc.FC_MODE_STREAM, precision=fc.FC_PREC_TF32X3) as s:
+        assert s.info().precision == fc.FC_PREC_TF32X3
 
 
 def test_mixed_stream_odd_nodes_shortest_window():

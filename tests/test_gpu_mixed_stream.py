@@ -137,8 +137,8 @@ SHAPES = [  # n, N, fs, band, W, trials
 ]
 
 
-def _serve(which, xs, launch_blocks=0):
-    sv = fc.fc_server_create(precision=fc.FC_PREC_BF16, launch_blocks=launch_blocks)
+def _serve(which, xs, launch_blocks=0, precision=fc.FC_PREC_BF16):
+    sv = fc.fc_server_create(precision=precision, launch_blocks=launch_blocks)
     try:
         ids = {k: fc.fc_server_open(sv, n, N, fs, band, "hann", fc.FC_SPECTRAL_METRICS, W)
                for k, (n, N, fs, band, W, _) in ((k, SHAPES[k]) for k in which)}
@@ -162,26 +162,27 @@ def _serve(which, xs, launch_blocks=0):
         fc.fc_server_destroy(sv)
 
 
-def test_served_mixed_precision_sessions():
+@pytest.mark.parametrize("prec", ["bf16", "tf32x3"])
+def test_served_mixed_precision_sessions(prec):
     """A server whose sessions run the mixed-precision streaming form: each session's
     networks are bit-identical alone and in the mix (with pushes split over launches), and
-    match the oracle on the window's GPU spectra within the mixed-precision tolerances."""
+    match the oracle on the window's GPU spectra within the precision's tolerances."""
     xs = [white_trials(80 + k, T, n, N) for k, (n, N, fs, band, W, T) in enumerate(SHAPES)]
-    mixed, res = _serve([0, 1], xs, launch_blocks=50)
+    mixed, res = _serve([0, 1], xs, launch_blocks=50, precision=PRECISIONS[prec])
     assert max(r[5] for r in res) > 1
     for k, (n, N, fs, band, W, T) in enumerate(SHAPES):
-        alone, _ = _serve([k], xs)
+        alone, _ = _serve([k], xs, precision=PRECISIONS[prec])
         for m in SPECTRAL:
             assert np.array_equal(alone[k][m], mixed[k][m], equal_nan=True), (k, m)
         with fc.Session(n, N, fs, band, "hann", fc.FC_SPECTRAL_METRICS, W, mode=fc.FC_MODE_STREAM,
-                        precision=fc.FC_PREC_BF16) as s:
+                        precision=PRECISIONS[prec]) as s:
             for t in range(T):
                 s.push(xs[k][t])
             X = window_spectra(s, W)
             B = s.B
             for m in SPECTRAL:  # the standalone session runs the same kernels in the same order
                 assert np.array_equal(s.network(m, packed=True)[0], mixed[k][m], equal_nan=True), (k, m)
-        _check(mixed[k], X, W, B, f"served cfg {k}")
+        _check(mixed[k], X, W, B, f"served cfg {k}", prec)
 
 
 def test_mixed_stream_tiny_nodes_exact_signs():

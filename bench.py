@@ -354,6 +354,9 @@ CASES = {
     "window_5124_bf16": dict(n=5124, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=100, prec="bf16", pushes=1,
                              desc="5124 nodes, W = 100, 40 bins, BF16 tensor-core full window (about 1.5 GB on the "
                                   "device): bulk fill + 1 push"),
+    "window_5124_tf32x3": dict(n=5124, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=100, prec="tf32x3", pushes=1,
+                               desc="5124 nodes, W = 100, 40 bins, split-TF32 tensor-core full window (FP32-class "
+                                    "linear metrics; about 4 GB on the device): bulk fill + 1 push"),
     "xcor_meg_window": dict(n=306, N=1000, fs=1000.0, band=(1.0, 100.0, 1024), W=100, prec="fp32", pushes=2,
                             metrics="XCOR",
                             desc="XCOR only, 306 MEG-sized channels, W = 100 trials x 1000 samples (2048-point "
@@ -518,7 +521,7 @@ def run_case(args):
     else:
         x = white_trials(5, W + c["pushes"], n, N)
     x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
-    prec = {"fp32": fc.FC_PREC_FP32, "bf16": fc.FC_PREC_BF16}[c["prec"]]
+    prec = {"fp32": fc.FC_PREC_FP32, "bf16": fc.FC_PREC_BF16, "tf32x3": fc.FC_PREC_TF32X3}[c["prec"]]
     mask = {"COR": fc.FC_COR, "XCOR": fc.FC_XCOR}.get(c.get("metrics"), fc.FC_SPECTRAL_METRICS)
     with fc.Session(n, N, c["fs"], c["band"], "hann", mask, W, mode=fc.FC_MODE_FULL, precision=prec) as s:
         fc.fc_push_trials(s.handle, x[:W].contiguous(), W)

@@ -93,11 +93,11 @@ typedef enum {
                          rounding; IMAGCOHY, PLI, USPLI, WPLI, DSWPLI stay exact-term sums) */
     FC_PREC_BF16 = 2, /* same with BF16 operands */
     FC_PREC_FP16 = 3, /* same with FP16 operands */
-    FC_PREC_TF32X3 = 4 /* FC_MODE_STREAM only (FC_ERR_UNSUPPORTED in full mode): the drift
-                          re-sum's linear sums from split TF32 operands, each a TF32 high part
-                          plus a TF32 low part, three products per step (hi hi + hi lo + lo hi):
-                          FP32-class products, so COH and PLV keep about 1e-6 of their value
-                          after a re-sum instead of the single-operand rounding */
+    FC_PREC_TF32X3 = 4 /* split TF32: each operand a TF32 high part plus a TF32 low part, three
+                          products per step (hi hi + hi lo + lo hi), FP32-class products; in
+                          FC_MODE_FULL the linear metrics then match FP32 sessions to about
+                          1e-6, in FC_MODE_STREAM COH and PLV keep that accuracy after a
+                          re-sum instead of the single-operand rounding */
 } fc_precision;
 
 typedef enum {

@@ -1098,8 +1098,6 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
     if (cfg.mode != FC_MODE_STREAM && cfg.mode != FC_MODE_FULL) return fail(FC_ERR_INVALID_ARG, "bad mode");
     if (cfg.mode == FC_MODE_FULL && window < 1) return fail(FC_ERR_INVALID_ARG, "full mode needs window >= 1");
     if (cfg.precision < FC_PREC_FP32 || cfg.precision > FC_PREC_TF32X3) return fail(FC_ERR_INVALID_ARG, "bad precision");
-    if (cfg.precision == FC_PREC_TF32X3 && cfg.mode == FC_MODE_FULL)
-        return fail(FC_ERR_UNSUPPORTED, "split TF32 applies to the drift re-sum of a streaming session");
     if (cfg.spectrum < FC_SPECTRUM_AUTO || cfg.spectrum > FC_SPECTRUM_FFT) return fail(FC_ERR_INVALID_ARG, "bad spectrum method");
     if (cfg.spectrum == FC_SPECTRUM_FFT && !fc_fft_size_ok(band.nfft))
         return fail(FC_ERR_UNSUPPORTED,
@@ -1285,8 +1283,10 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
             TRY(alloc_zero(s, (size_t)s->resum_scratch_tp * B * FC_BLOCK_WORDS, &s->resum_scratch));
         }
         if (cfg.precision != FC_PREC_FP32 && cfg.mode == FC_MODE_FULL) {
-            s->ab_format = cfg.precision == FC_PREC_BF16 ? 1 : (cfg.precision == FC_PREC_FP16 ? 0 : 2);
-            const int per_chunk = s->ab_format == 2 ? 32 : 64;  // inner elements per 128-byte K-chunk
+            s->ab_format = cfg.precision == FC_PREC_BF16 ? 1
+                           : cfg.precision == FC_PREC_FP16 ? 0
+                           : cfg.precision == FC_PREC_TF32X3 ? 3 : 2;
+            const int per_chunk = s->ab_format >= 2 ? 32 : 64;  // inner elements per 128-byte K-chunk
             s->nchunks = (2 * window + per_chunk - 1) / per_chunk;
             s->nt128 = (n_nodes + 127) / 128;
             s->ntp128 = s->nt128 * (s->nt128 + 1) / 2;
@@ -1300,10 +1300,13 @@ fc_status fc_session_create(int n_nodes, int n_samples, double fs, fc_band band,
             TRY(alloc_zero(s, tb.size(), &s->tile_b128));
             TRY(upload(s, s->tile_a128, ta.data(), ta.size() * sizeof(unsigned short)));
             TRY(upload(s, s->tile_b128, tb.data(), tb.size() * sizeof(unsigned short)));
-            TRY(alloc_zero(s, (size_t)s->nt128 * B * 4 * s->nchunks * herk_chunk_bytes(), &s->ops));
+            const size_t kinds = s->ab_format == 3 ? 8 : 4;  // split TF32: high and low parts
+            TRY(alloc_zero(s, (size_t)s->nt128 * B * kinds * s->nchunks * herk_chunk_bytes(), &s->ops));
             TRY(alloc_zero(s, (size_t)B * n_nodes, &s->tiny_flags));
             int gb;
-            if (s->nchunks <= herk_resident_max_chunks()) {
+            // (split TF32 takes the streaming-operand form: both parts of a row tile would not
+            // stay resident)
+            if (s->nchunks <= herk_resident_max_chunks() && s->ab_format != 3) {
                 // resident-operand form: each row tile a with its column tiles b >= a in balanced
                 // segments of at most kHerkSegTiles tiles. Its operands keep, in the last
                 // K-chunk, only the 16-byte columns up to the last K-step that holds inner

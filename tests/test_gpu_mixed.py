@@ -22,8 +22,9 @@ from paper_2303_03279_gb300 import fc  # noqa: E402
 
 LINEAR = ("COH", "IMAGCOHY", "PLV")
 NONLINEAR = ("PLI", "USPLI", "WPLI", "DSWPLI")
-PRECISIONS = {"bf16": fc.FC_PREC_BF16, "fp16": fc.FC_PREC_FP16, "tf32": fc.FC_PREC_TF32}
-TOL_TC = {"bf16": 5e-3, "fp16": 5e-3, "tf32": 5e-3}
+PRECISIONS = {"bf16": fc.FC_PREC_BF16, "fp16": fc.FC_PREC_FP16, "tf32": fc.FC_PREC_TF32,
+              "tf32x3": fc.FC_PREC_TF32X3}
+TOL_TC = {"bf16": 5e-3, "fp16": 5e-3, "tf32": 5e-3, "tf32x3": 1e-5}  # split TF32: FP32-class
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -77,18 +77,6 @@ def test_mixed_stream_against_oracle(prec):
         print(f"[{prec}] max |gpu - oracle| of the tensor-core metrics:", {k: f"{v:.1e}" for k, v in errs.items()})
 
 
-def test_split_tf32_is_a_streaming_precision():
-    """Split TF32 serves the drift re-sum of a sliding streaming window; a full-window session
-    asking for it is refused."""
-    with pytest.raises(fc.FcError) as e:
-        fc.Session(40, 64, 128.0, (4.0, 40.0, 64), "hann", fc.FC_SPECTRAL_METRICS, 4,
-                   mode=fc.FC_MODE_FULL, precision=fc.FC_PREC_TF32X3)
-    assert e.value.status == fc.FC_ERR_UNSUPPORTED
-    with fc.Session(40, 64, 128.0, (4.0, 40.0, 64), "hann", fc.FC_SPECTRAL_METRICS, 4,
-                    mode=fc.FC_MODE_STREAM, precision=fc.FC_PREC_TF32X3) as s:
-        assert s.info().precision == fc.FC_PREC_TF32X3
-
-
 def test_mixed_stream_odd_nodes_shortest_window():
     """137 nodes (odd: the non-linear re-sum stages one node per copy; a ragged last 32-node
     and 128-node tile) with the shortest sliding window that re-sums, W = 2 (3 ring slots):

@@ -85,3 +85,22 @@ def test_argument_errors_are_reported_before_device_use():
     with pytest.raises(fc.FcError) as e:
         fc.fc_session_create(8, 16, 100.0, (1.0, 20.0, 16), "hann", fc.FC_COH, 4, cfg)
     assert e.value.status == fc.FC_ERR_INVALID_ARG
+    for prec in (-1, fc.FC_PREC_TF32X3 + 1):  # outside the precision enum
+        cfg = fc.fc_config_default()
+        cfg.precision = prec
+        with pytest.raises(fc.FcError) as e:
+            fc.fc_session_create(8, 16, 100.0, (1.0, 20.0, 16), "hann", fc.FC_COH, 4, cfg)
+        assert e.value.status == fc.FC_ERR_INVALID_ARG, prec
+
+
+def test_header_enum_values_match_the_binding():
+    """Every enumerator of include/fc.h written as NAME = <integer> has the same value in
+    the Python binding (where the binding names it)."""
+    text = open(os.path.join(ROOT, "include", "fc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    checked = 0
+    for name, value in re.findall(r"\b(FC_[A-Z0-9_]+)\s*=\s*(-?\d+)\s*[,}\n]", text):
+        if hasattr(fc, name):
+            assert getattr(fc, name) == int(value), name
+            checked += 1
+    assert checked >= 10 and fc.FC_PREC_TF32X3 == 4

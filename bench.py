@@ -354,6 +354,9 @@ CASES = {
     "window_5124_bf16": dict(n=5124, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=100, prec="bf16", pushes=1,
                              desc="5124 nodes, W = 100, 40 bins, BF16 tensor-core full window (about 1.5 GB on the "
                                   "device): bulk fill + 1 push"),
+    "window_1024_tf32x3": dict(n=1024, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=100, prec="tf32x3", pushes=3,
+                               desc="1024 nodes, W = 100, 40 bins, split-TF32 tensor-core full window: bulk fill + "
+                                    "3 pushes"),
     "window_5124_tf32x3": dict(n=5124, N=500, fs=1000.0, band=(4.0, 44.0, 1000), W=100, prec="tf32x3", pushes=1,
                                desc="5124 nodes, W = 100, 40 bins, split-TF32 tensor-core full window (FP32-class "
                                     "linear metrics; about 4 GB on the device): bulk fill + 1 push"),

@@ -8,7 +8,9 @@
 //   Re S_csd = A_r(rows i) A_r(rows j)^T,   Im S_csd = A_i(rows i) A_r(rows j)^T,
 // and the same with U for the phasor sums: four real GEMMs of 128 x 128 x 2K per
 // (128-node tile pair, bin), kind::f16 (BF16 or FP16 operands) or kind::tf32, FP32
-// accumulation. COH, IMAGCOHY and PLV of the bin are finalized from TMEM and added to the
+// accumulation; split TF32 (ab_format 3) stores each operand as a TF32 high part and a TF32
+// low part (operand kinds 4 .. 7) and forms every product as hi hi + hi lo + lo hi, which
+// keeps the sums FP32-class. COH, IMAGCOHY and PLV of the bin are finalized from TMEM and added to the
 // band sums of the unit's bin group (the first bin stores, the later ones add with
 // fire-and-forget reductions, red.global.add): one CTA walks all bins of a (tile pair, bin
 // group) unit in order and each sum has one owner thread, so the additions land in bin order
